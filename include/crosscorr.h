@@ -1,0 +1,208 @@
+/*
+ * crosscorr.h -- C ABI of the GB300 resampled cross-correlation (CrossCorr) library.
+ *
+ * The library computes, for a batch of binary-orbit templates (a_p, T_asc, P),
+ * the normalised cross-correlation statistic rho(f) of Meadors, Krishnan, Papa,
+ * Whelan & Zhang, "Resampling to accelerate cross-correlation searches for
+ * continuous gravitational waves from binary systems":
+ *
+ *   1. resample each detector's heterodyned complex series into the source
+ *      frame (Sec. III A: Eqs. t-ssb-equation, tau-equation, the windowed-sinc
+ *      formula shannon-interp-formula and resampled-time-series-q-eq) and weight
+ *      it by the antenna/noise functions (Eq. norm-a-eq);
+ *   2. take zero-padded FFTs segment by segment at the metric resolution and
+ *      keep the decimated output bins (Sec. III B 3-4);
+ *   3. sum the weighted cross-correlation over all detector/segment pairs with
+ *      lag up to T_max and normalise (Sec. III B 1 and Eq. final-formatted-rho).
+ *
+ * Conventions for every entry point
+ *   - Times are seconds.  cc_config.t0 is the GPS time of sample 0 and the
+ *     origin of the source-frame grid tau_r = t0 + r*dt; all table times in
+ *     cc_detector are relative to t0.  Template T_asc is absolute GPS.
+ *   - "host" pointers are read during the call only (the plan copies what it
+ *     keeps); "device" pointers are CUDA global memory owned by the caller and
+ *     must stay valid until the work queued on the stream has finished.
+ *   - Complex values are interleaved float pairs (re, im), 8 bytes each.
+ *   - Every call is asynchronous on the given stream (a cudaStream_t passed as
+ *     void*, NULL = legacy default stream) except crosscorr_plan,
+ *     crosscorr_plan_info, crosscorr_plan_destroy and crosscorr_rho_topk
+ *     (which waits for its host copy).
+ *   - Errors are returned, never raised or aborted on.  CC_ERR_INVALID for bad
+ *     arguments (checked before any work is queued), CC_ERR_OOM when device
+ *     memory cannot be allocated, CC_ERR_CUDA when a CUDA call fails,
+ *     CC_ERR_UNSUPPORTED for valid but unimplemented options.  The message of
+ *     the last failure on the calling thread is returned by
+ *     crosscorr_last_error().
+ *   - A plan is not thread-safe: use one plan per host thread / stream.
+ */
+#ifndef CROSSCORR_H
+#define CROSSCORR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CC_OK = 0,
+    CC_ERR_INVALID = 1,
+    CC_ERR_OOM = 2,
+    CC_ERR_CUDA = 3,
+    CC_ERR_TIMEOUT = 4,
+    CC_ERR_UNSUPPORTED = 5
+} cc_status;
+
+/* Pair sets (Sec. III B 1, pair selection for the resampled statistic). */
+enum {
+    CC_PAIRS_UNORDERED = 0,   /* each unordered pair once: X<Y with |K-L|<=R, and X=Y with
+                                 1<=L-K<=R (auto-correlation excluded) -- the default */
+    CC_PAIRS_CROSS_ONLY = 1,  /* X<Y with |K-L|<=R only (radiometer-like option) */
+    CC_PAIRS_ALL_ORDERED = 2  /* every ordered pair with |K-L|<=R incl. K=L, X=Y
+                                 (the F-statistic limit of Appendix A) */
+};
+
+enum { CC_INTERP_EXACT = 0, CC_INTERP_LEARNED = 1 };
+enum { CC_STORE_FP32 = 0, CC_STORE_BF16 = 1 };
+
+#define CC_MAX_DET 4
+
+/* Search set-up of one frequency band. */
+typedef struct {
+    double t0;        /* GPS time of sample 0 and origin of the source-frame grid */
+    double dt;        /* sampling interval dt' of the heterodyned series */
+    double f_h;       /* heterodyne frequency = band centre [Hz] */
+    double f_band;    /* searched band width [Hz] */
+    double T_sft;     /* noise-estimation block [s]; integer multiple of dt */
+    double T_short;   /* segment length [s]; 0 selects max(T_max, T_sft); integer multiple of dt */
+    double T_max;     /* maximum lag [s]; R = floor(T_max / T_short) */
+    double mu_f;      /* frequency mismatch for the metric spacing (0.1 typical) */
+    int32_t n_det;    /* Q, 1..CC_MAX_DET */
+    int32_t D;        /* windowed-sinc half width: 2D+1 taps, 1..32 */
+    int32_t interp;   /* CC_INTERP_EXACT (CC_INTERP_LEARNED reserved) */
+    int32_t store;    /* CC_STORE_FP32 or CC_STORE_BF16 for the resampled a_r, b_r series */
+    int32_t pair_mode;/* CC_PAIRS_* */
+    int32_t reserved;
+    int64_t n_samples;/* N_t samples per detector */
+} cc_config;
+
+/* Per-detector inputs (host memory; copied by crosscorr_plan). */
+typedef struct {
+    const double* ssb_delay; /* Roemer delay r(t).n/c = t_SSB - t [s] at eph_t0 + n*eph_dt,
+                                linearly interpolated (Eq. t-ssb-equation) */
+    double eph_t0, eph_dt;
+    int64_t n_eph;           /* >= 2 */
+    const double* a_tab;     /* antenna function a(t) at ab_t0 + n*ab_dt, linearly interpolated */
+    const double* b_tab;     /* antenna function b(t), same grid */
+    double ab_t0, ab_dt;     /* ab_t0 and ab_dt integer multiples of dt */
+    int64_t n_ab;            /* >= 2 */
+    const double* sigma;     /* noise std per T_sft block starting at t = 0; 0 marks a gap */
+    int64_t n_sigma;
+} cc_detector;
+
+/* One orbital template (circular orbit, Sec. II A 2). */
+typedef struct {
+    double a_p;    /* projected semi-major axis a sin i / c [s] */
+    double T_asc;  /* time of ascension, GPS [s] */
+    double P;      /* orbital period [s] */
+} cc_template;
+
+/* One top-k record. */
+typedef struct {
+    int64_t tmpl;  /* template index within the rho array */
+    int32_t bin;   /* output bin k, 0..N_f-1 */
+    int32_t pad;
+    double freq;   /* absolute frequency of the bin [Hz] */
+    float rho;
+    float pad2;
+} cc_hit;
+
+/* Plan quantities (Sec. III B 3-4), returned by crosscorr_plan_info. */
+typedef struct {
+    int64_t N_s;      /* samples per T_short segment */
+    int64_t M;        /* number of segments, floor(N_t / N_s) */
+    int64_t R;        /* T_max / T_short */
+    int64_t N_tau;    /* M * N_s resampled samples per detector */
+    int64_t N_FFT;    /* 2^ceil(log2 N_FFT0) */
+    int64_t N_f;      /* output bins, floor(f_band / delta-lambda_f) */
+    int64_t k0;       /* FFT bin of f_h - f_band/2 (FFT indexed from f_FFT) */
+    int64_t L;        /* coset FFT length used on chip */
+    int64_t C;        /* number of cosets, N_FFT / L */
+    double T_coh, dlf, N_FFT0, T_FFT, nu_R, f_r, f_FFT;
+    size_t ws_bytes;  /* device workspace currently held by the plan */
+} cc_plan_info;
+
+typedef struct cc_plan cc_plan;
+
+/* Build a plan: validates cfg, derives T_short, T_coh, delta-lambda_f, N_FFT,
+ * nu_R, f_r*, k0 and the output bins k-bar(k) = k0 + floor(nu_R k) (Sec. III B 3-4
+ * with the readings listed in the design notes), copies the detector tables
+ * to the device.  dets: host array of cfg->n_det detectors.  *out receives a
+ * plan owned by the caller and released with crosscorr_plan_destroy. */
+cc_status crosscorr_plan(const cc_config* cfg, const cc_detector* dets, cc_plan** out);
+
+/* Plan quantities; freqs_host (nullable, N_f doubles) receives the absolute
+ * output frequencies f_FFT + k-bar/T_FFT, kbar_host (nullable, N_f int64) the bins. */
+cc_status crosscorr_plan_info(const cc_plan* plan, cc_plan_info* info, double* freqs_host,
+                              int64_t* kbar_host);
+
+/* Stage 1, resample and weight (Eqs. tau-equation, resampled-time-series-q-eq,
+ * norm-a-eq): for template t and detector X writes
+ *   ab[((t*Q + X)*2 + 0)*N_tau + r] = a_r = alpha_r x'_r exp(-2 pi i f_r* tau_r)
+ *   ab[((t*Q + X)*2 + 1)*N_tau + r] = b_r = beta_r  x'_r exp(-2 pi i f_r* tau_r)
+ * with x'_r the heterodyne-corrected windowed-sinc interpolation at t(tau_r) and
+ * alpha = a/sigma^2, beta = b/sigma^2 at that detector time (0 in gaps), and
+ *   norm[((t*Q + X)*M + K)*4 + {0,1,2}] = sum over segment K of
+ *   alpha^2 sigma^2, beta^2 sigma^2, alpha beta sigma^2   (hat-A, hat-B, hat-C).
+ * x_dev: host array of Q device pointers to complex64[N_t].  t_dev: device
+ * cc_template[n_t].  ab_dev: device complex64 (store = FP32) or bf16 pairs
+ * (store = BF16) [n_t][Q][2][N_tau].  norm_dev: device float[n_t][Q][M][4]. */
+cc_status crosscorr_resample(cc_plan* plan, const void* const* x_dev, const cc_template* t_dev,
+                             int64_t n_t, void* ab_dev, float* norm_dev, void* stream);
+
+/* Stage 2, segment spectra (Eqs. fft-inklings to the F-bar definitions): for each
+ * template, detector X, segment K and weight w in {a, b}
+ *   F[(((t*Q + X)*M + K)*2 + w)*N_f + k] = sum_{r in segment K} w_r exp(-2 pi i (k-bar_k - N_FFT/2) r / N_FFT)
+ * i.e. the zero-padded N_FFT-point transform at the selected bins with the
+ * segment-start phase Phi_in included.  ab_dev as written by stage 1; F_dev:
+ * device complex64[n_t][Q][M][2][N_f]. */
+cc_status crosscorr_segment_fft(cc_plan* plan, const void* ab_dev, int64_t n_t, void* F_dev,
+                                void* stream);
+
+/* Stage 3, pair sum and normalisation (Sec. III B 1, Eq. final-formatted-rho):
+ *   rho[t*N_f + k] = sqrt(2) Re sum_P [conj(F_a,XK) F_a,YL + conj(F_b,XK) F_b,YL]
+ *                    / sqrt(sum_P (A_XK A_YL + B_XK B_YL + 2 C_XK C_YL))
+ * over the pair set of cfg.pair_mode, accumulated in compensated FP32.
+ * F_dev, norm_dev as written by stages 1-2; rho_dev: device float[n_t][N_f]. */
+cc_status crosscorr_pair_accumulate(cc_plan* plan, const void* F_dev, const float* norm_dev,
+                                    int64_t n_t, float* rho_dev, void* stream);
+
+/* Whole path fused on chip: the same rho as stages 1-3 without materialising
+ * a_r, b_r or F.  Inputs and output as for stages 1 and 3. */
+cc_status crosscorr_search(cc_plan* plan, const void* const* x_dev, const cc_template* t_dev,
+                           int64_t n_t, float* rho_dev, void* stream);
+
+/* The k largest rho over (template, bin) of a device float[n_t][N_f] array,
+ * descending, ties by (template, bin) ascending; hits_host receives
+ * min(k, n_t*N_f) records.  Synchronises the stream.  1 <= k <= 4096. */
+cc_status crosscorr_rho_topk(cc_plan* plan, const float* rho_dev, int64_t n_t, int k,
+                             cc_hit* hits_host, void* stream);
+
+/* Release the plan and everything it owns (NULL is ignored). */
+void crosscorr_plan_destroy(cc_plan* plan);
+
+const char* crosscorr_status_string(cc_status s);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* crosscorr_last_error(void);
+
+/* Number of CUDA kernels this library has launched in the process so far (a
+ * diagnostic counter, incremented on the host at every launch). */
+uint64_t crosscorr_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CROSSCORR_H */

@@ -1,0 +1,208 @@
+"""GB300 resampled cross-correlation (CrossCorr) search: Python binding.
+
+A thin marshalling layer over the C ABI of ``include/crosscorr.h``: every step
+of the statistic (timing, resampling, weighting, segment FFTs, pair sums,
+normalisation, top-k) runs in the CUDA library.  PyTorch supplies device
+memory and streams only.  Calls fail loudly when the compiled library is
+missing; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+from ctypes import POINTER, byref, c_double, c_int64, c_void_p
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _lib
+from ._lib import CcConfig, CcDetector, CcHit, CcPlanInfo, CrossCorrError, check
+
+__all__ = ["CrossCorrPlan", "CrossCorrError", "PAIR_UNORDERED", "PAIR_CROSS_ONLY",
+           "PAIR_ALL_ORDERED", "STORE_FP32", "STORE_BF16", "build", "load"]
+
+PAIR_UNORDERED, PAIR_CROSS_ONLY, PAIR_ALL_ORDERED = 0, 1, 2
+STORE_FP32, STORE_BF16 = 0, 1
+INTERP_EXACT, INTERP_LEARNED = 0, 1
+
+build = _lib.build
+load = _lib.load
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _dptr(t) -> int:
+    return int(t.data_ptr())
+
+
+def _check_tensor(name, t, dtype, device_required=True):
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if device_required and not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+class CrossCorrPlan:
+    """A plan for one band: derived FFT/bin layout plus device copies of the tables.
+
+    ``cfg`` needs the attributes t0, dt, n_samples, f_h, f_band, T_sft, T_max,
+    T_short, mu_f, D, n_det, pair_mode; each detector in ``dets`` needs eph_t0,
+    eph_dt, ssb_delay, ab_t0, ab_dt, a_tab, b_tab, sigma (numpy arrays for the
+    tables; times relative to t0).
+    """
+
+    def __init__(self, cfg, dets: Sequence, store: int = STORE_FP32, interp: int = INTERP_EXACT,
+                 pair_mode: Optional[int] = None):
+        self._lib = _lib.load()
+        c = CcConfig()
+        c.t0, c.dt, c.f_h, c.f_band = cfg.t0, cfg.dt, cfg.f_h, cfg.f_band
+        c.T_sft, c.T_short, c.T_max, c.mu_f = cfg.T_sft, cfg.T_short, cfg.T_max, cfg.mu_f
+        c.n_det, c.D, c.interp, c.store = len(dets), cfg.D, interp, store
+        c.pair_mode = cfg.pair_mode if pair_mode is None else pair_mode
+        c.n_samples = cfg.n_samples
+        self.cfg = c
+        keep = []
+        arr = (CcDetector * len(dets))()
+        for i, d in enumerate(dets):
+            ssb = np.ascontiguousarray(d.ssb_delay, np.float64)
+            a = np.ascontiguousarray(d.a_tab, np.float64)
+            b = np.ascontiguousarray(d.b_tab, np.float64)
+            s = np.ascontiguousarray(d.sigma, np.float64)
+            keep += [ssb, a, b, s]
+            arr[i].ssb_delay = ssb.ctypes.data_as(POINTER(c_double))
+            arr[i].eph_t0, arr[i].eph_dt, arr[i].n_eph = d.eph_t0, d.eph_dt, ssb.size
+            arr[i].a_tab = a.ctypes.data_as(POINTER(c_double))
+            arr[i].b_tab = b.ctypes.data_as(POINTER(c_double))
+            arr[i].ab_t0, arr[i].ab_dt, arr[i].n_ab = d.ab_t0, d.ab_dt, a.size
+            arr[i].sigma = s.ctypes.data_as(POINTER(c_double))
+            arr[i].n_sigma = s.size
+        h = c_void_p()
+        check("crosscorr_plan", self._lib.crosscorr_plan(byref(c), arr, byref(h)))
+        self._h = h
+        info = CcPlanInfo()
+        self.freqs = np.empty(0)
+        check("crosscorr_plan_info", self._lib.crosscorr_plan_info(h, byref(info), None, None))
+        self.freqs = np.empty(info.N_f, np.float64)
+        self.kbar = np.empty(info.N_f, np.int64)
+        check("crosscorr_plan_info", self._lib.crosscorr_plan_info(
+            h, byref(info), self.freqs.ctypes.data_as(POINTER(c_double)),
+            self.kbar.ctypes.data_as(POINTER(c_int64))))
+        self.info = {name: getattr(info, name) for name, _ in CcPlanInfo._fields_}
+        self.Q = len(dets)
+        self.N_f = info.N_f
+        self.M = info.M
+        self.N_tau = info.N_tau
+        self.store = store
+
+    # -- helpers ---------------------------------------------------------------
+    def _xptrs(self, x):
+        import torch
+        if isinstance(x, torch.Tensor):
+            xs = [x[i] for i in range(x.shape[0])]
+        else:
+            xs = list(x)
+        if len(xs) != self.Q:
+            raise ValueError(f"need {self.Q} detector series, got {len(xs)}")
+        for i, xi in enumerate(xs):
+            _check_tensor(f"x[{i}]", xi, torch.complex64)
+            if xi.numel() != self.cfg.n_samples:
+                raise ValueError(f"x[{i}] must hold n_samples = {self.cfg.n_samples} values")
+        arr = (c_void_p * self.Q)(*[_dptr(xi) for xi in xs])
+        return arr, xs
+
+    def _templates(self, templates):
+        import torch
+        _check_tensor("templates", templates, torch.float64)
+        if templates.dim() != 2 or templates.shape[1] != 3:
+            raise ValueError("templates must be [n_t, 3] (a_p, T_asc, P)")
+        return templates.shape[0]
+
+    # -- the C ABI calls -------------------------------------------------------
+    def resample(self, x, templates, ab=None, norm=None, stream=None):
+        """Stage 1: a_r, b_r series [n_t, Q, 2, N_tau] and segment norms [n_t, Q, M, 4]."""
+        import torch
+        n_t = self._templates(templates)
+        xp, _ = self._xptrs(x)
+        dev = templates.device
+        if ab is None:
+            if self.store == STORE_BF16:
+                ab = torch.empty((n_t, self.Q, 2, self.N_tau, 2), dtype=torch.bfloat16, device=dev)
+            else:
+                ab = torch.empty((n_t, self.Q, 2, self.N_tau), dtype=torch.complex64, device=dev)
+        if norm is None:
+            norm = torch.empty((n_t, self.Q, self.M, 4), dtype=torch.float32, device=dev)
+        check("crosscorr_resample", self._lib.crosscorr_resample(
+            self._h, xp, _dptr(templates), n_t, _dptr(ab), _dptr(norm), _stream_handle(stream)))
+        return ab, norm
+
+    def segment_fft(self, ab, n_t, F=None, stream=None):
+        """Stage 2: spectra [n_t, Q, M, 2, N_f] complex64."""
+        import torch
+        if F is None:
+            F = torch.empty((n_t, self.Q, self.M, 2, self.N_f), dtype=torch.complex64, device=ab.device)
+        check("crosscorr_segment_fft", self._lib.crosscorr_segment_fft(
+            self._h, _dptr(ab), n_t, _dptr(F), _stream_handle(stream)))
+        return F
+
+    def pair_accumulate(self, F, norm, n_t, rho=None, stream=None):
+        """Stage 3: rho [n_t, N_f] float32."""
+        import torch
+        if rho is None:
+            rho = torch.empty((n_t, self.N_f), dtype=torch.float32, device=F.device)
+        check("crosscorr_pair_accumulate", self._lib.crosscorr_pair_accumulate(
+            self._h, _dptr(F), _dptr(norm), n_t, _dptr(rho), _stream_handle(stream)))
+        return rho
+
+    def search(self, x, templates, rho=None, stream=None):
+        """The whole path: rho [n_t, N_f] float32."""
+        import torch
+        n_t = self._templates(templates)
+        xp, _ = self._xptrs(x)
+        if rho is None:
+            rho = torch.empty((n_t, self.N_f), dtype=torch.float32, device=templates.device)
+        else:
+            _check_tensor("rho", rho, torch.float32)
+        check("crosscorr_search", self._lib.crosscorr_search(
+            self._h, xp, _dptr(templates), n_t, _dptr(rho), _stream_handle(stream)))
+        return rho
+
+    def topk(self, rho, k, stream=None):
+        """k best (template, bin, freq, rho), descending, ties by (template, bin)."""
+        import torch
+        _check_tensor("rho", rho, torch.float32)
+        n_t = rho.numel() // self.N_f
+        n = min(k, n_t * self.N_f)
+        hits = (CcHit * max(n, 1))()
+        check("crosscorr_rho_topk", self._lib.crosscorr_rho_topk(
+            self._h, _dptr(rho), n_t, k, hits, _stream_handle(stream)))
+        out = np.zeros(n, dtype=[("tmpl", np.int64), ("bin", np.int32), ("freq", np.float64),
+                                 ("rho", np.float32)])
+        for i in range(n):
+            out[i] = (hits[i].tmpl, hits[i].bin, hits[i].freq, hits[i].rho)
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.crosscorr_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,304 @@
+// Internal definitions shared by the CUDA translation units of the crosscorr library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "crosscorr.h"
+
+namespace cc {
+
+// Samples between FP64 timing knots.  Between knots the delay d(tau) = tau - t(tau)
+// is a cubic through four knots; its error for the Sco X-1 orbit is
+// a_p Omega^4 KNOT^4 / 24 * 0.56 ~ 7e-10 s at KNOT = 128.
+constexpr int KNOT = 128;
+constexpr int MAX_D = 32;
+constexpr int MAX_TAPS = 2 * MAX_D + 1;
+constexpr int N_BIN_ITER = 6;   // fixed-point steps of u = tau + a_p sin(Omega (u - T_asc))
+constexpr int N_SSB_ITER = 5;   // fixed-point steps of t = u - Delta(t)
+constexpr int MAX_L = 8192;     // largest on-chip coset FFT
+
+// Timing record of one knot, built from four FP64 knot delays.
+struct __align__(16) KnotRec {
+    int N;        // floor(d_k / dt)
+    float f;      // d_k / dt - N, in [0, 1)
+    float psi;    // frac(-f_h d_k - f_r* tau_k), cycles
+    float dm1;    // (d_{k-1} - d_k) / dt
+    float dp1;    // (d_{k+1} - d_k) / dt
+    float dp2;    // (d_{k+2} - d_k) / dt
+    float pad0, pad1;
+};
+
+// Everything a kernel needs, passed by value.
+struct DevParams {
+    int Q, D, pair_mode, store;
+    int L, C, log2L, nsft;
+    int n_ab_step, pad_;
+    int64_t N_t, N_s, M, R, N_tau, N_FFT, N_f;
+    int64_t b0;      // (k0 - N_FFT/2) mod N_FFT: FFT bin of output k = 0
+    int64_t ab_j0;   // ab_t0 / dt
+    double dt, t0, f_h, f_r;
+    float f_h_dt, f_r_dt;
+    const float2* x[CC_MAX_DET];
+    const double* ssb[CC_MAX_DET];
+    double eph_t0[CC_MAX_DET], eph_dt[CC_MAX_DET];
+    int64_t n_eph[CC_MAX_DET];
+    const float* atab[CC_MAX_DET];
+    const float* btab[CC_MAX_DET];
+    int64_t n_ab[CC_MAX_DET];
+    const float* sig2[CC_MAX_DET];   // sigma^2 per T_sft block, 0 in gaps
+    int64_t n_sig[CC_MAX_DET];
+    const int* coset_off;            // [C+1]
+    const int* coset_k;              // [N_f] output index k, grouped by coset
+    const int* coset_m;              // [N_f] position in the coset's L-point transform
+    const float2* twL;               // exp(-2 pi i j / L), j < L
+    float ham[MAX_TAPS];             // Hamming window, 2D+1 taps
+};
+
+}  // namespace cc
+
+// The opaque plan of the C ABI.
+struct cc_plan {
+    cc_config cfg;
+    int Q;
+    // plan quantities (host, FP64)
+    int64_t N_s, M, R, N_tau, N_FFT, N_f, k0, L, C;
+    double T_short, T_coh, dlf, N_FFT0, T_FFT, nu_R, f_r, f_FFT;
+    std::vector<int64_t> kbar;
+    std::vector<double> freq;
+    cc::DevParams dp;
+    // device allocations owned by the plan
+    std::vector<void*> dev_allocs;
+    // workspace (grown on demand by staged/fused paths)
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+};
+
+namespace cc {
+
+// ---------------------------------------------------------------------------
+// Host helpers (plan.cu)
+// ---------------------------------------------------------------------------
+cc_status fail(cc_status s, const std::string& msg);
+cc_status cuda_fail(cudaError_t e, const char* what);
+cc_status ensure_workspace(cc_plan* p, size_t bytes);
+int launch_blocks_for(int64_t n, int threads);
+void count_launch(uint64_t n = 1);
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// Re(conj(a) b)
+__device__ __forceinline__ float redot(float2 a, float2 b) { return fmaf(a.x, b.x, a.y * b.y); }
+__device__ __forceinline__ float2 mul_negi(float2 a) { return make_float2(a.y, -a.x); }
+
+// Kahan-compensated accumulation.
+__device__ __forceinline__ void kahan_add(float& sum, float& comp, float v) {
+    float y = v - comp;
+    float t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+}
+
+__device__ __forceinline__ int64_t floor_div(int64_t a, int64_t b) {
+    int64_t q = a / b;
+    return (q * b > a) ? q - 1 : q;
+}
+
+// Linear interpolation of an FP64 table at time t (end intervals extrapolate).
+__device__ __forceinline__ double table_lerp(const double* tab, double t0, double dt, int64_t n,
+                                             double t) {
+    double u = (t - t0) / dt;
+    double fi = floor(u);
+    int64_t i = (int64_t)fi;
+    i = i < 0 ? 0 : (i > n - 2 ? n - 2 : i);
+    double f = u - (double)i;
+    double v0 = __ldg(tab + i), v1 = __ldg(tab + i + 1);
+    return v0 + f * (v1 - v0);
+}
+
+// d(tau) = tau - t(tau) for detector X and one template (all times relative to t0).
+// tau(t) = t_SSB - a_p sin(Omega (t_SSB - T_asc)), t_SSB = t + Delta_X(t); the two
+// fixed points are iterated on the small quantities b = t_SSB - tau and
+// Delta = t_SSB - t so that d = Delta - b keeps FP64 precision.
+__device__ __forceinline__ double knot_delay(const DevParams& p, int X, double a_p,
+                                             double tasc_rel, double invP, double tau) {
+    double b = 0.0;
+#pragma unroll 1
+    for (int it = 0; it < N_BIN_ITER; ++it)
+        b = a_p * sinpi(2.0 * (((tau + b) - tasc_rel) * invP));
+    const double* tab = p.ssb[X];
+    double t0 = p.eph_t0[X], edt = p.eph_dt[X];
+    int64_t n = p.n_eph[X];
+    double dl = table_lerp(tab, t0, edt, n, tau);
+#pragma unroll 1
+    for (int it = 0; it < N_SSB_ITER; ++it) dl = table_lerp(tab, t0, edt, n, (tau + b) - dl);
+    return dl - b;
+}
+
+// Knot record from the delays at knots k-1, k, k+1, k+2 (seconds) of a knot at
+// source time tau_k.
+__device__ __forceinline__ KnotRec make_knot(const DevParams& p, double dm1, double d0,
+                                             double dp1, double dp2, double tau_k) {
+    KnotRec r;
+    double e = d0 / p.dt;
+    double fl = floor(e);
+    r.N = (int)fl;
+    r.f = (float)(e - fl);
+    r.dm1 = (float)((dm1 - d0) / p.dt);
+    r.dp1 = (float)((dp1 - d0) / p.dt);
+    r.dp2 = (float)((dp2 - d0) / p.dt);
+    double c = -p.f_h * d0 - p.f_r * tau_k;
+    r.psi = (float)(c - floor(c));
+    r.pad0 = r.pad1 = 0.f;
+    return r;
+}
+
+// Per-sample timing from the knot record: stencil centre j*, offset delta in
+// [-1/2, 1/2) and heterodyne + f_r* phase (cycles, reduced to [-1/2, 1/2)).
+struct SampleTiming {
+    int64_t jstar;
+    float delta;
+    float psi;
+};
+
+__device__ __forceinline__ SampleTiming sample_timing(const DevParams& p, const KnotRec& kr,
+                                                      int64_t r, int64_t rk) {
+    float h = (float)(r - rk) * (1.0f / KNOT);
+    float hm1 = h - 1.0f, hm2 = h - 2.0f, hp1 = h + 1.0f;
+    float Lm1 = -h * hm1 * hm2 * (1.0f / 6.0f);
+    float L1 = -hp1 * h * hm2 * 0.5f;
+    float L2 = hp1 * h * hm1 * (1.0f / 6.0f);
+    float pp = fmaf(Lm1, kr.dm1, fmaf(L1, kr.dp1, L2 * kr.dp2));
+    float v = kr.f + pp;
+    float g = 0.5f - v;
+    float fl = floorf(g);
+    SampleTiming s;
+    s.jstar = r - (int64_t)kr.N + (int64_t)fl;
+    s.delta = (g - 0.5f) - fl;
+    float psi = kr.psi - p.f_h_dt * pp - p.f_r_dt * (float)(r - rk);
+    s.psi = psi - rintf(psi);
+    return s;
+}
+
+// Windowed-sinc interpolation (2D+1 taps) at t/dt = j* + delta of a complex series.
+__device__ __forceinline__ float2 interp_sinc(const DevParams& p, const float2* __restrict__ x,
+                                              int64_t jstar, float delta) {
+    const int64_t N = p.N_t;
+    if (delta == 0.0f) {
+        return (jstar >= 0 && jstar < N) ? __ldg(x + jstar) : make_float2(0.f, 0.f);
+    }
+    const int D = p.D;
+    float s = sinpif(delta) * 0.318309886183790672f;   // sin(pi delta)/pi
+    float2 acc = make_float2(0.f, 0.f);
+    int64_t j0 = jstar - D;
+    for (int n = 0; n <= 2 * D; ++n) {
+        int64_t j = j0 + n;
+        if (j < 0 || j >= N) continue;
+        float dj = delta - (float)(n - D);              // (t - t_j)/dt
+        float c = p.ham[n] * __fdividef(((n - D) & 1) ? -s : s, dj);
+        float2 xv = __ldg(x + j);
+        acc.x = fmaf(c, xv.x, acc.x);
+        acc.y = fmaf(c, xv.y, acc.y);
+    }
+    return acc;
+}
+
+// Weights at detector time t/dt = j* + delta: alpha = a/sigma^2, beta = b/sigma^2,
+// s2 = sigma^2 (all zero in gaps).
+struct SampleWeights {
+    float alpha, beta, s2;
+};
+
+__device__ __forceinline__ SampleWeights sample_weights(const DevParams& p, int X, int64_t jstar,
+                                                        float delta) {
+    SampleWeights w{0.f, 0.f, 0.f};
+    int64_t q = floor_div(jstar, p.nsft);
+    int64_t rem = jstar - q * p.nsft;
+    int64_t blk = (rem == 0 && delta < 0.f) ? q - 1 : q;
+    if (blk < 0 || blk >= p.n_sig[X]) return w;
+    float s2 = __ldg(p.sig2[X] + blk);
+    if (!(s2 > 0.f)) return w;
+    int64_t ja = jstar - p.ab_j0;
+    int64_t ia = floor_div(ja, p.n_ab_step);
+    int64_t nab = p.n_ab[X];
+    int64_t ic = ia < 0 ? 0 : (ia > nab - 2 ? nab - 2 : ia);
+    // the linear interpolant is continuous, so the interval chosen at a node does not matter
+    float fr = ((float)(ja - ic * p.n_ab_step) + delta) / (float)p.n_ab_step;
+    float a0 = __ldg(p.atab[X] + ic), a1 = __ldg(p.atab[X] + ic + 1);
+    float b0 = __ldg(p.btab[X] + ic), b1 = __ldg(p.btab[X] + ic + 1);
+    float a = fmaf(fr, a1 - a0, a0);
+    float b = fmaf(fr, b1 - b0, b0);
+    float inv = 1.0f / s2;
+    w.alpha = a * inv;
+    w.beta = b * inv;
+    w.s2 = s2;
+    return w;
+}
+
+// exp(-2 pi i j / N) for integer j in [0, N), N a power of two.
+__device__ __forceinline__ float2 twiddle_N(uint64_t j, uint64_t N) {
+    float s, c;
+    sincospif(-2.0f * (float)j / (float)N, &s, &c);
+    return make_float2(c, s);
+}
+
+// In-place-free Stockham FFT (forward, exp(-2 pi i m s / L)) of L = 2^log2L points in
+// shared memory, natural order in and out, radix 4 with one radix-2 pass when log2 L
+// is odd.  Input in a, scratch b; returns the buffer holding the result.  Must be
+// called by all threads of the block.
+__device__ __forceinline__ float2* fft_stockham(float2* a, float2* b, int L, int log2L,
+                                                const float2* __restrict__ twL) {
+    float2* in = a;
+    float2* out = b;
+    int Ns = 1;
+    const int quarter = L >> 2;
+    for (int ps = 0; ps < (log2L >> 1); ++ps) {
+        const int stride = L / (Ns * 4);
+        for (int j = threadIdx.x; j < quarter; j += blockDim.x) {
+            int k = j & (Ns - 1);
+            float2 v0 = in[j], v1 = in[j + quarter], v2 = in[j + 2 * quarter], v3 = in[j + 3 * quarter];
+            if (Ns > 1) {
+                v1 = cmul(v1, __ldg(twL + k * stride));
+                v2 = cmul(v2, __ldg(twL + 2 * k * stride));
+                v3 = cmul(v3, __ldg(twL + 3 * k * stride));
+            }
+            float2 a0 = cadd(v0, v2), a1 = csub(v0, v2), a2 = cadd(v1, v3), a3 = mul_negi(csub(v1, v3));
+            int idxD = ((j - k) << 2) + k;
+            out[idxD] = cadd(a0, a2);
+            out[idxD + Ns] = cadd(a1, a3);
+            out[idxD + 2 * Ns] = csub(a0, a2);
+            out[idxD + 3 * Ns] = csub(a1, a3);
+        }
+        __syncthreads();
+        float2* t = in; in = out; out = t;
+        Ns <<= 2;
+    }
+    if (log2L & 1) {
+        const int half = L >> 1;
+        const int stride = L / (Ns * 2);
+        for (int j = threadIdx.x; j < half; j += blockDim.x) {
+            int k = j & (Ns - 1);
+            float2 v0 = in[j], v1 = in[j + half];
+            if (Ns > 1) v1 = cmul(v1, __ldg(twL + k * stride));
+            int idxD = ((j - k) << 1) + k;
+            out[idxD] = cadd(v0, v1);
+            out[idxD + Ns] = csub(v0, v1);
+        }
+        __syncthreads();
+        float2* t = in; in = out; out = t;
+    }
+    return in;
+}
+
+}  // namespace cc

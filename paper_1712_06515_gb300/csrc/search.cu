@@ -1,0 +1,63 @@
+// crosscorr_search: the whole path for a batch of templates.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace cc {
+cc_status set_inputs(cc_plan* plan, const void* const* x_dev);
+cc_status launch_resample(cc_plan* plan, const cc_template* t_dev, int64_t n_t, void* ab, float* norm,
+                          cudaStream_t st);
+cc_status launch_segfft(cc_plan* plan, const void* ab, int64_t n_t, void* F, cudaStream_t st);
+cc_status launch_norm_pairs(cc_plan* plan, const void* F, const float* norm, int64_t n_t, double* Dws,
+                            float* rho, cudaStream_t st);
+
+constexpr size_t STAGED_WS_BUDGET = (size_t)6 << 30;
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Templates per batch and the workspace they need when the stages run back to back.
+static void staged_batch(const cc_plan* p, int64_t n_t, int64_t* batch, size_t* bytes) {
+    const size_t elem = p->cfg.store == CC_STORE_BF16 ? 4 : 8;
+    const size_t ab = (size_t)p->Q * 2 * p->N_tau * elem;
+    const size_t F = (size_t)p->Q * p->M * 2 * p->N_f * sizeof(float2);
+    const size_t nm = (size_t)p->Q * p->M * sizeof(float4);
+    const size_t per = align256(ab) + align256(F) + align256(nm) + 256;
+    int64_t b = (int64_t)std::max<size_t>(1, STAGED_WS_BUDGET / per);
+    b = std::min<int64_t>(b, n_t);
+    *batch = b;
+    *bytes = (align256(ab * b) + align256(F * b) + align256(nm * b) + align256(8 * b));
+}
+
+}  // namespace cc
+
+extern "C" cc_status crosscorr_search(cc_plan* plan, const void* const* x_dev, const cc_template* t_dev,
+                                      int64_t n_t, float* rho_dev, void* stream) {
+    using namespace cc;
+    if (!plan) return fail(CC_ERR_INVALID, "plan is null");
+    if (n_t < 0) return fail(CC_ERR_INVALID, "n_t must be >= 0");
+    if (n_t == 0) return CC_OK;
+    if (!t_dev || !rho_dev) return fail(CC_ERR_INVALID, "null device pointer");
+    cc_status s = set_inputs(plan, x_dev);
+    if (s != CC_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    int64_t batch;
+    size_t bytes;
+    staged_batch(plan, n_t, &batch, &bytes);
+    if ((s = ensure_workspace(plan, bytes)) != CC_OK) return s;
+    const size_t elem = plan->cfg.store == CC_STORE_BF16 ? 4 : 8;
+    char* w = (char*)plan->ws;
+    void* ab = w;
+    w += align256((size_t)plan->Q * 2 * plan->N_tau * elem * batch);
+    void* F = w;
+    w += align256((size_t)plan->Q * plan->M * 2 * plan->N_f * sizeof(float2) * batch);
+    float* nm = (float*)w;
+    w += align256((size_t)plan->Q * plan->M * sizeof(float4) * batch);
+    double* Dws = (double*)w;
+    for (int64_t t0 = 0; t0 < n_t; t0 += batch) {
+        const int64_t nb = std::min(batch, n_t - t0);
+        if ((s = launch_resample(plan, t_dev + t0, nb, ab, nm, st)) != CC_OK) return s;
+        if ((s = launch_segfft(plan, ab, nb, F, st)) != CC_OK) return s;
+        if ((s = launch_norm_pairs(plan, F, nm, nb, Dws, rho_dev + t0 * plan->N_f, st)) != CC_OK) return s;
+    }
+    return CC_OK;
+}

@@ -1,0 +1,318 @@
+// Staged path of the crosscorr C ABI: resample -> segment spectra -> pair sum, each
+// stage materialising its output in device memory.  Used for per-stage parity and
+// per-stage HBM measurement; the fused path (search.cu) shares the device helpers.
+#include <math.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace cc {
+
+constexpr int RS_THREADS = 256;
+constexpr int FFT_THREADS = 256;
+constexpr int PAIR_THREADS = 256;
+constexpr int64_t MAX_GRID_YZ = 65535;
+
+__device__ __forceinline__ float2 load_series(const void* base, int store, int64_t i) {
+    if (store == CC_STORE_BF16) {
+        __nv_bfloat162 v = ((const __nv_bfloat162*)base)[i];
+        return __bfloat1622float2(v);
+    }
+    return __ldg((const float2*)base + i);
+}
+
+__device__ __forceinline__ void store_series(void* base, int store, int64_t i, float2 v) {
+    if (store == CC_STORE_BF16)
+        ((__nv_bfloat162*)base)[i] = __float22bfloat162_rn(v);
+    else
+        ((float2*)base)[i] = v;
+}
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    T s = 0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    return s;
+}
+
+// Knots covering segment [seg0, seg0 + N_s): k in [kA, kB] with kA one below the
+// first knot and kB two above the last, so every sample has its four knots.
+__device__ __forceinline__ void segment_knot_range(const DevParams& p, int64_t seg0, int64_t* kA,
+                                                   int64_t* kB) {
+    *kA = floor_div(seg0, KNOT) - 1;
+    *kB = floor_div(seg0 + p.N_s - 1, KNOT) + 2;
+}
+
+// Stage 1: one block per (segment K, detector X, template t).
+__global__ void __launch_bounds__(RS_THREADS)
+resample_kernel(DevParams p, const cc_template* __restrict__ tm, int64_t t_base, void* ab,
+                float4* __restrict__ norm) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ float red[32];
+    const int64_t K = blockIdx.x;
+    const int X = blockIdx.y;
+    const int64_t t = t_base + blockIdx.z;
+    const int64_t seg0 = K * p.N_s;
+    int64_t kA, kB;
+    segment_knot_range(p, seg0, &kA, &kB);
+    const int nk = (int)(kB - kA + 1);
+    KnotRec* rec = (KnotRec*)smem;
+    double* dk = (double*)(smem + sizeof(KnotRec) * nk);
+
+    const cc_template T = tm[t];
+    const double tasc_rel = T.T_asc - p.t0;
+    const double invP = 1.0 / T.P;
+    for (int i = threadIdx.x; i < nk; i += blockDim.x)
+        dk[i] = knot_delay(p, X, T.a_p, tasc_rel, invP, (double)((kA + i) * KNOT) * p.dt);
+    __syncthreads();
+    for (int i = 1 + threadIdx.x; i < nk - 2; i += blockDim.x)
+        rec[i] = make_knot(p, dk[i - 1], dk[i], dk[i + 1], dk[i + 2], (double)((kA + i) * KNOT) * p.dt);
+    __syncthreads();
+
+    const float2* __restrict__ x = p.x[X];
+    const int64_t sa = ((t * p.Q + X) * 2 + 0) * p.N_tau;
+    const int64_t sb = sa + p.N_tau;
+    float A = 0.f, B = 0.f, Cn = 0.f;
+    for (int64_t i = threadIdx.x; i < p.N_s; i += blockDim.x) {
+        const int64_t r = seg0 + i;
+        const int64_t k = r / KNOT;
+        const KnotRec kr = rec[k - kA];
+        const SampleTiming st = sample_timing(p, kr, r, k * KNOT);
+        const float2 xv = interp_sinc(p, x, st.jstar, st.delta);
+        float sn, cs;
+        sincospif(2.0f * st.psi, &sn, &cs);
+        const float2 xr = cmul(xv, make_float2(cs, sn));
+        const SampleWeights w = sample_weights(p, X, st.jstar, st.delta);
+        store_series(ab, p.store, sa + r, cscale(xr, w.alpha));
+        store_series(ab, p.store, sb + r, cscale(xr, w.beta));
+        A = fmaf(w.alpha * w.alpha, w.s2, A);
+        B = fmaf(w.beta * w.beta, w.s2, B);
+        Cn = fmaf(w.alpha * w.beta, w.s2, Cn);
+    }
+    A = block_sum(A, red);
+    B = block_sum(B, red);
+    Cn = block_sum(Cn, red);
+    if (threadIdx.x == 0) norm[(t * p.Q + X) * p.M + K] = make_float4(A, B, Cn, 0.f);
+}
+
+// Stage 2: one block per (coset c, segment K, series s = (t*Q + X)*2 + w).
+__global__ void __launch_bounds__(FFT_THREADS)
+segfft_kernel(DevParams p, const void* ab, int64_t s_base, float2* __restrict__ F) {
+    extern __shared__ __align__(16) float2 buf[];
+    const int c = blockIdx.x;
+    const int64_t K = blockIdx.y;
+    const int64_t s = s_base + blockIdx.z;
+    const int64_t seg0 = K * p.N_s, seg1 = seg0 + p.N_s;
+    const uint64_t N = (uint64_t)p.N_FFT, mask = N - 1;
+    const uint64_t bc = ((uint64_t)p.b0 + (uint64_t)c) & mask;
+    const int64_t base = s * p.N_tau;
+    const int L = p.L;
+    for (int pos = threadIdx.x; pos < L; pos += blockDim.x) {
+        int64_t off = ((int64_t)pos - seg0) % L;
+        if (off < 0) off += L;
+        float2 acc = make_float2(0.f, 0.f);
+        for (int64_t r = seg0 + off; r < seg1; r += L) {
+            const float2 v = load_series(ab, p.store, base + r);
+            const uint64_t j = (bc * ((uint64_t)r & mask)) & mask;
+            acc = cadd(acc, cmul(v, twiddle_N(j, N)));
+        }
+        buf[pos] = acc;
+    }
+    __syncthreads();
+    const float2* res = fft_stockham(buf, buf + L, L, p.log2L, p.twL);
+    const int64_t tX = s >> 1;
+    const int w = (int)(s & 1);
+    float2* Fo = F + ((tX * p.M + K) * 2 + w) * p.N_f;
+    const int e = __ldg(p.coset_off + c + 1);
+    for (int i = __ldg(p.coset_off + c) + threadIdx.x; i < e; i += blockDim.x)
+        Fo[__ldg(p.coset_k + i)] = res[__ldg(p.coset_m + i)];
+}
+
+// Sum over the pair set of (A_i A_j + B_i B_j + 2 C_i C_j), one block per template.
+__device__ __forceinline__ double nn(float4 a, float4 b) {
+    return (double)a.x * b.x + (double)a.y * b.y + 2.0 * (double)a.z * b.z;
+}
+
+__global__ void norm_kernel(DevParams p, const float4* __restrict__ norm, int64_t t_base,
+                            double* __restrict__ Dout) {
+    __shared__ double red[32];
+    const int64_t t = t_base + blockIdx.x;
+    const float4* nt = norm + t * p.Q * p.M;
+    const int64_t M = p.M, R = p.R;
+    double acc = 0.0;
+    for (int64_t idx = threadIdx.x; idx < p.Q * M; idx += blockDim.x) {
+        const int Y = (int)(idx / M);
+        const int64_t K = idx - Y * M;
+        const float4 nY = nt[Y * M + K];
+        double s = 0.0;
+        for (int X = 0; X < Y; ++X) s += nn(nt[X * M + K], nY);
+        for (int64_t Lg = (K - R > 0 ? K - R : 0); Lg < K; ++Lg)
+            for (int X = 0; X < p.Q; ++X) {
+                if (p.pair_mode == CC_PAIRS_CROSS_ONLY && X == Y) continue;
+                s += nn(nt[X * M + Lg], nY);
+            }
+        if (p.pair_mode == CC_PAIRS_ALL_ORDERED) s = 2.0 * s + nn(nY, nY);
+        acc += s;
+    }
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) Dout[t] = acc;
+}
+
+// Stage 3: one thread per (template, bin); pairs whose later segment is K are
+// added at step K, so each unordered pair is visited once.
+__global__ void __launch_bounds__(PAIR_THREADS)
+pair_kernel(DevParams p, const float2* __restrict__ F, const double* __restrict__ Dn, int64_t t_base,
+            float* __restrict__ rho) {
+    const int64_t t = t_base + blockIdx.y;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= p.N_f) return;
+    const int Q = p.Q;
+    const int64_t M = p.M, R = p.R, Nf = p.N_f;
+    const int mode = p.pair_mode;
+    auto Fat = [&](int X, int64_t K, int w) -> float2 {
+        return __ldg(F + (((t * Q + X) * M + K) * 2 + w) * Nf + k);
+    };
+    float sum = 0.f, comp = 0.f;
+    for (int64_t K = 0; K < M; ++K) {
+        float term = 0.f;
+        for (int w = 0; w < 2; ++w) {
+            float2 fk[CC_MAX_DET], winx[CC_MAX_DET];
+            float2 win = make_float2(0.f, 0.f);
+            for (int X = 0; X < Q; ++X) {
+                fk[X] = Fat(X, K, w);
+                winx[X] = make_float2(0.f, 0.f);
+            }
+            for (int64_t Lg = (K - R > 0 ? K - R : 0); Lg < K; ++Lg)
+                for (int X = 0; X < Q; ++X) {
+                    const float2 f = Fat(X, Lg, w);
+                    win = cadd(win, f);
+                    winx[X] = cadd(winx[X], f);
+                }
+            float2 same = make_float2(0.f, 0.f);
+            for (int Y = 0; Y < Q; ++Y) {
+                float2 h = cadd(same, mode == CC_PAIRS_CROSS_ONLY ? csub(win, winx[Y]) : win);
+                float tY = redot(fk[Y], h);
+                if (mode == CC_PAIRS_ALL_ORDERED) tY = fmaf(2.f, tY, redot(fk[Y], fk[Y]));
+                term += tY;
+                same = cadd(same, fk[Y]);
+            }
+        }
+        kahan_add(sum, comp, term);
+    }
+    const double D = Dn[t];
+    rho[t * Nf + k] = D > 0.0 ? (float)(1.4142135623730951 * (double)sum / sqrt(D)) : 0.f;
+}
+
+size_t resample_smem_bytes(const DevParams& p) {
+    const int64_t nk = p.N_s / KNOT + 5;
+    return (size_t)nk * (sizeof(KnotRec) + sizeof(double));
+}
+
+cc_status launch_resample(cc_plan* plan, const cc_template* t_dev, int64_t n_t, void* ab,
+                          float* norm, cudaStream_t st) {
+    const DevParams& p = plan->dp;
+    const size_t sm = resample_smem_bytes(p);
+    if (sm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(resample_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sm);
+        if (e != cudaSuccess) return cuda_fail(e, "resample smem attribute");
+    }
+    for (int64_t t0 = 0; t0 < n_t; t0 += MAX_GRID_YZ) {
+        const int64_t nt = std::min<int64_t>(MAX_GRID_YZ, n_t - t0);
+        dim3 grid((unsigned)p.M, (unsigned)p.Q, (unsigned)nt);
+        resample_kernel<<<grid, RS_THREADS, sm, st>>>(p, t_dev, t0, ab, (float4*)norm);
+        count_launch();
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? CC_OK : cuda_fail(e, "resample launch");
+}
+
+cc_status launch_segfft(cc_plan* plan, const void* ab, int64_t n_t, void* F, cudaStream_t st) {
+    const DevParams& p = plan->dp;
+    const size_t sm = (size_t)2 * p.L * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(segfft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return cuda_fail(e, "segment fft smem attribute");
+    const int64_t ns = n_t * p.Q * 2;
+    for (int64_t s0 = 0; s0 < ns; s0 += MAX_GRID_YZ) {
+        const int64_t n = std::min<int64_t>(MAX_GRID_YZ, ns - s0);
+        dim3 grid((unsigned)p.C, (unsigned)p.M, (unsigned)n);
+        segfft_kernel<<<grid, FFT_THREADS, sm, st>>>(p, ab, s0, (float2*)F);
+        count_launch();
+    }
+    e = cudaGetLastError();
+    return e == cudaSuccess ? CC_OK : cuda_fail(e, "segment fft launch");
+}
+
+cc_status launch_norm_pairs(cc_plan* plan, const void* F, const float* norm, int64_t n_t,
+                            double* Dws, float* rho, cudaStream_t st) {
+    const DevParams& p = plan->dp;
+    for (int64_t t0 = 0; t0 < n_t; t0 += MAX_GRID_YZ) {
+        const int64_t nt = std::min<int64_t>(MAX_GRID_YZ, n_t - t0);
+        norm_kernel<<<(unsigned)nt, 256, 0, st>>>(p, (const float4*)norm, t0, Dws);
+        count_launch();
+        dim3 grid((unsigned)launch_blocks_for(p.N_f, PAIR_THREADS), (unsigned)nt);
+        pair_kernel<<<grid, PAIR_THREADS, 0, st>>>(p, (const float2*)F, Dws, t0, rho);
+        count_launch();
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? CC_OK : cuda_fail(e, "pair launch");
+}
+
+cc_status set_inputs(cc_plan* plan, const void* const* x_dev) {
+    if (!x_dev) return fail(CC_ERR_INVALID, "x_dev is null");
+    for (int q = 0; q < plan->Q; ++q) {
+        if (!x_dev[q]) return fail(CC_ERR_INVALID, "x_dev[" + std::to_string(q) + "] is null");
+        if (((uintptr_t)x_dev[q]) & 7) return fail(CC_ERR_INVALID, "x_dev entries must be 8-byte aligned");
+        plan->dp.x[q] = (const float2*)x_dev[q];
+    }
+    return CC_OK;
+}
+
+}  // namespace cc
+
+extern "C" {
+
+cc_status crosscorr_resample(cc_plan* plan, const void* const* x_dev, const cc_template* t_dev,
+                             int64_t n_t, void* ab_dev, float* norm_dev, void* stream) {
+    using namespace cc;
+    if (!plan) return fail(CC_ERR_INVALID, "plan is null");
+    if (n_t < 0) return fail(CC_ERR_INVALID, "n_t must be >= 0");
+    if (n_t == 0) return CC_OK;
+    if (!t_dev || !ab_dev || !norm_dev) return fail(CC_ERR_INVALID, "null device pointer");
+    cc_status s = set_inputs(plan, x_dev);
+    if (s != CC_OK) return s;
+    return launch_resample(plan, t_dev, n_t, ab_dev, norm_dev, (cudaStream_t)stream);
+}
+
+cc_status crosscorr_segment_fft(cc_plan* plan, const void* ab_dev, int64_t n_t, void* F_dev,
+                                void* stream) {
+    using namespace cc;
+    if (!plan) return fail(CC_ERR_INVALID, "plan is null");
+    if (n_t < 0) return fail(CC_ERR_INVALID, "n_t must be >= 0");
+    if (n_t == 0) return CC_OK;
+    if (!ab_dev || !F_dev) return fail(CC_ERR_INVALID, "null device pointer");
+    if (plan->M > MAX_GRID_YZ) return fail(CC_ERR_UNSUPPORTED, "more than 65535 segments");
+    return launch_segfft(plan, ab_dev, n_t, F_dev, (cudaStream_t)stream);
+}
+
+cc_status crosscorr_pair_accumulate(cc_plan* plan, const void* F_dev, const float* norm_dev,
+                                    int64_t n_t, float* rho_dev, void* stream) {
+    using namespace cc;
+    if (!plan) return fail(CC_ERR_INVALID, "plan is null");
+    if (n_t < 0) return fail(CC_ERR_INVALID, "n_t must be >= 0");
+    if (n_t == 0) return CC_OK;
+    if (!F_dev || !norm_dev || !rho_dev) return fail(CC_ERR_INVALID, "null device pointer");
+    cc_status s = ensure_workspace(plan, (size_t)n_t * sizeof(double));
+    if (s != CC_OK) return s;
+    return launch_norm_pairs(plan, F_dev, norm_dev, n_t, (double*)plan->ws, rho_dev,
+                             (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,295 @@
+"""Parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (per template, in units of rho's unit noise): |rho_gpu - rho_oracle|
+<= 1e-4 max(1, max|rho_oracle|) for the FP32 path, 1e-2 for BF16 storage.  Stage
+tests feed oracle inputs to one GPU stage and compare its output element by
+element.  Samples whose stencil centre or noise block is decided by a tie
+(|delta| within 1e-5 of 1/2, or of 0 on a block boundary) are excluded from the
+per-sample comparisons: the two sides round the same real number in different
+precision there.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from synth import Injection
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU hosts too
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1712_06515_gb300 as cc  # noqa: E402
+
+DEV = torch.device("cuda:0")
+TOL32 = 1e-4
+TOL16 = 1e-2
+
+
+def dev_inputs(ds):
+    return (torch.from_numpy(ds.x64).to(DEV), torch.from_numpy(ds.templates).to(DEV))
+
+
+def rho_tol(ref, tol=TOL32):
+    return tol * max(1.0, float(np.abs(ref).max()))
+
+
+def assert_rho_close(got, ref, tol=TOL32):
+    for t in range(ref.shape[0]):
+        err = float(np.abs(got[t] - ref[t]).max())
+        lim = rho_tol(ref[t], tol)
+        assert err <= lim, f"template {t}: max |drho| = {err:.3e} > {lim:.3e}"
+
+
+def oracle_ab(ds, plan, tmpl, q):
+    """Oracle a_r, b_r (with the f_r* rotation) and a mask of tie-free samples."""
+    xr, js, de = oracle.resample(ds.x[q], ds.dets[q], ds.cfg, plan, tmpl)
+    al, be, s2 = oracle.weights(ds.dets[q], ds.cfg, js, de)
+    r = np.arange(plan.M * plan.N_s)
+    rot = np.exp(-2j * np.pi * ((plan.f_r * r * plan.dt) % 1.0))
+    nsft = int(round(ds.cfg.T_sft / ds.cfg.dt))
+    tie = (np.abs(de + 0.5) < 1e-5) | ((np.abs(de) < 1e-5) & (js % nsft == 0))
+    return al * xr * rot, be * xr * rot, oracle.segment_norms(al, be, s2, plan), ~tie
+
+
+CASES = {
+    "default": dict(),
+    "T_max0": dict(T_max=0.0, T_short=64.0, f_band=0.3),
+    "R2": dict(T_max=256.0, T_short=128.0),
+    "fband_005": dict(f_band=0.05, T_max=256.0, T_short=256.0),
+    "Q1": dict(n_det=1),
+    "Q3": dict(n_det=3),
+    "cross_only": dict(pair_mode=1),
+    "all_ordered": dict(pair_mode=2),
+    "D16": dict(D=16),
+    "ragged": dict(n_samples=4096 + 77),
+    "short_series": dict(n_samples=300, T_sft=32.0, T_max=64.0, T_short=64.0),
+}
+
+
+def case_ds(name, seed=21, n_templates=3, **extra):
+    kw = dict(CASES[name])
+    kw.update(extra)
+    return synth.tiny(seed=seed, n_templates=n_templates, **kw)
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_search_parity(name):
+    ds = case_ds(name)
+    ref = oracle.rho(ds)
+    with cc.CrossCorrPlan(ds.cfg, ds.dets) as plan:
+        x, tm = dev_inputs(ds)
+        got = plan.search(x, tm).cpu().numpy().astype(np.float64)
+    assert got.shape == ref.shape
+    assert_rho_close(got, ref)
+
+
+def test_plan_bins_match_oracle():
+    for name in ("default", "fband_005", "T_max0"):
+        ds = case_ds(name)
+        p = oracle.make_plan(ds.cfg)
+        with cc.CrossCorrPlan(ds.cfg, ds.dets) as plan:
+            assert np.array_equal(plan.kbar, p.kbar)
+            np.testing.assert_allclose(plan.freqs, p.freq, rtol=0, atol=1e-12)
+            for key, val in (("N_FFT", p.N_FFT), ("N_f", p.N_f), ("M", p.M), ("R", p.R),
+                             ("N_s", p.N_s), ("k0", p.k0)):
+                assert plan.info[key] == val, key
+            assert plan.info["nu_R"] == p.nu_R and plan.info["f_r"] == p.f_r
+
+
+@pytest.mark.parametrize("name", ["default", "fband_005", "ragged", "Q3"])
+def test_resample_stage_parity(name):
+    ds = case_ds(name)
+    p = oracle.make_plan(ds.cfg)
+    with cc.CrossCorrPlan(ds.cfg, ds.dets) as plan:
+        x, tm = dev_inputs(ds)
+        ab, nrm = plan.resample(x, tm)
+        ab = ab.cpu().numpy()
+        nrm = nrm.cpu().numpy()
+    for t, tmpl in enumerate(ds.templates):
+        for q in range(ds.cfg.n_det):
+            a, b, norms, ok = oracle_ab(ds, p, tmpl, q)
+            scale = max(np.abs(a).max(), np.abs(b).max())
+            assert ok.mean() > 0.999
+            assert np.abs(ab[t, q, 0] - a)[ok].max() <= 2e-5 * scale
+            assert np.abs(ab[t, q, 1] - b)[ok].max() <= 2e-5 * scale
+            for i in range(3):
+                np.testing.assert_allclose(nrm[t, q, :, i], norms[i], rtol=2e-5,
+                                           atol=2e-5 * max(1e-30, np.abs(norms[i]).max()))
+
+
+@pytest.mark.parametrize("name", ["default", "fband_005", "T_max0"])
+def test_segment_fft_stage_parity(name):
+    """Oracle a_r, b_r in, GPU spectra out, against the oracle's FFT route."""
+    ds = case_ds(name, n_templates=2)
+    p = oracle.make_plan(ds.cfg)
+    Q = ds.cfg.n_det
+    ab = np.zeros((2, Q, 2, p.M * p.N_s), np.complex64)
+    Fref = np.zeros((2, Q, p.M, 2, p.N_f), np.complex128)
+    for t, tmpl in enumerate(ds.templates):
+        for q in range(Q):
+            a, b, _, _ = oracle_ab(ds, p, tmpl, q)
+            ab[t, q, 0], ab[t, q, 1] = a, b
+            Fref[t, q, :, 0] = oracle.spectra_fft(ab[t, q, 0].astype(np.complex128), p)
+            Fref[t, q, :, 1] = oracle.spectra_fft(ab[t, q, 1].astype(np.complex128), p)
+    with cc.CrossCorrPlan(ds.cfg, ds.dets) as plan:
+        F = plan.segment_fft(torch.from_numpy(ab).to(DEV), 2).cpu().numpy()
+    err = np.abs(F - Fref).max()
+    assert err <= 1e-5 * np.abs(Fref).max(), err
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_pair_stage_parity(mode):
+    """Oracle spectra and norms in, GPU rho out, against the oracle's pair sum."""
+    ds = case_ds("R2", n_templates=2, n_det=3, pair_mode=mode)
+    p = oracle.make_plan(ds.cfg)
+    Q = ds.cfg.n_det
+    F = np.zeros((2, Q, p.M, 2, p.N_f), np.complex64)
+    nrm = np.zeros((2, Q, p.M, 4), np.float32)
+    ref = np.zeros((2, p.N_f))
+    rng = np.random.default_rng(5)
+    for t in range(2):
+        Fa = [(rng.standard_normal((p.M, p.N_f)) + 1j * rng.standard_normal((p.M, p.N_f))).astype(np.complex64)
+              for _ in range(Q)]
+        Fb = [(rng.standard_normal((p.M, p.N_f)) + 1j * rng.standard_normal((p.M, p.N_f))).astype(np.complex64)
+              for _ in range(Q)]
+        norms = [tuple(rng.uniform(0.5, 2.0, p.M).astype(np.float32) for _ in range(3)) for _ in range(Q)]
+        for q in range(Q):
+            F[t, q, :, 0], F[t, q, :, 1] = Fa[q], Fb[q]
+            nrm[t, q, :, :3] = np.stack(norms[q], axis=1)
+        Dn = oracle.normalization([tuple(n.astype(np.float64) for n in nq) for nq in norms], p, mode)
+        raw = oracle.pair_sum([f.astype(np.complex128) for f in Fa], [f.astype(np.complex128) for f in Fb], p, mode)
+        ref[t] = math.sqrt(2.0) * raw / math.sqrt(Dn)
+    with cc.CrossCorrPlan(ds.cfg, ds.dets) as plan:
+        rho = plan.pair_accumulate(torch.from_numpy(F).to(DEV), torch.from_numpy(nrm).to(DEV), 2)
+    assert_rho_close(rho.cpu().numpy().astype(np.float64), ref)
+
+
+def test_staged_equals_search():
+    ds = case_ds("default")
+    with cc.CrossCorrPlan(ds.cfg, ds.dets) as plan:
+        x, tm = dev_inputs(ds)
+        ab, nrm = plan.resample(x, tm)
+        F = plan.segment_fft(ab, tm.shape[0])
+        staged = plan.pair_accumulate(F, nrm, tm.shape[0]).cpu().numpy()
+        fused = plan.search(x, tm).cpu().numpy()
+    assert_rho_close(fused.astype(np.float64), staged.astype(np.float64))
+
+
+def test_bf16_storage_parity():
+    ds = case_ds("default")
+    ref = oracle.rho(ds)
+    with cc.CrossCorrPlan(ds.cfg, ds.dets, store=cc.STORE_BF16) as plan:
+        x, tm = dev_inputs(ds)
+        got = plan.search(x, tm).cpu().numpy().astype(np.float64)
+    assert_rho_close(got, ref, TOL16)
+
+
+def test_empty_and_degenerate_inputs():
+    ds = case_ds("default")
+    with cc.CrossCorrPlan(ds.cfg, ds.dets) as plan:
+        x, tm = dev_inputs(ds)
+        out = plan.search(x, tm[:0])
+        assert out.shape == (0, plan.N_f)
+        # a detector entirely in gaps contributes nothing; both in gaps gives rho = 0
+        for d in ds.dets:
+            d.sigma[:] = 0.0
+        ds.x[:] = 0.0
+    with cc.CrossCorrPlan(ds.cfg, ds.dets) as plan:
+        x, tm = dev_inputs(ds)
+        got = plan.search(x, tm).cpu().numpy()
+    assert np.all(got == 0.0)
+    np.testing.assert_array_equal(oracle.rho(ds), 0.0)
+
+
+def test_bad_arguments_raise():
+    ds = case_ds("default")
+    with cc.CrossCorrPlan(ds.cfg, ds.dets) as plan:
+        x, tm = dev_inputs(ds)
+        with pytest.raises(ValueError):
+            plan.search(x[:1], tm)
+        with pytest.raises(ValueError):
+            plan.search(x, tm.float())
+        with pytest.raises(ValueError):
+            plan.search(x.cpu(), tm)
+
+
+def test_topk_matches_oracle_on_loud_injection():
+    probe = synth.tiny(seed=31, noise=False)
+    p = oracle.make_plan(probe.cfg)
+    tasc = synth.T_ASC_O1 + 12.0
+    inj = Injection(h0=0.6, f0=p.freq[150], a_p=1.44, T_asc=tasc, P=synth.SCO_X1_P, cosi=0.5)
+    tm = np.array([[1.40, tasc, synth.SCO_X1_P], [1.44, tasc, synth.SCO_X1_P],
+                   [1.44, tasc + 200.0, synth.SCO_X1_P], [1.48, tasc - 100, synth.SCO_X1_P]])
+    ds = synth.tiny(seed=31, injection=inj, templates=tm)
+    ref = oracle.rho(ds)
+    with cc.CrossCorrPlan(ds.cfg, ds.dets) as plan:
+        x, t = dev_inputs(ds)
+        rho = plan.search(x, t)
+        hits = plan.topk(rho, 10)
+    assert_rho_close(rho.cpu().numpy().astype(np.float64), ref)
+    ti, bi, vi = oracle.topk(ref, 10)
+    assert (hits["tmpl"][0], hits["bin"][0]) == (1, 150)
+    assert list(zip(hits["tmpl"][:3], hits["bin"][:3])) == list(zip(ti[:3], bi[:3]))
+    np.testing.assert_allclose(hits["rho"], vi, atol=rho_tol(ref))
+
+
+def test_topk_ordering_and_ties():
+    ds = case_ds("default")
+    with cc.CrossCorrPlan(ds.cfg, ds.dets) as plan:
+        vals = np.random.default_rng(3).standard_normal((7, plan.N_f)).astype(np.float32)
+        vals[2, 5] = vals[0, 9] = vals[4, 1] = 9.0     # three-way tie at the top
+        vals[6, 0] = np.nan                           # NaN never ranks
+        rho = torch.from_numpy(vals).to(DEV)
+        hits = plan.topk(rho, 20)
+        ti, bi, vi = oracle.topk(np.nan_to_num(vals.astype(np.float64), nan=-np.inf), 20)
+    assert list(zip(hits["tmpl"], hits["bin"])) == list(zip(ti, bi))
+    assert list(zip(hits["tmpl"][:3], hits["bin"][:3])) == [(0, 9), (2, 5), (4, 1)]
+    np.testing.assert_array_equal(hits["rho"], vi.astype(np.float32))
+    assert np.allclose(hits["freq"], plan.freqs[hits["bin"]])
+
+
+def test_plain_day_all_templates():
+    """One day, 1 Hz band at 100 Hz, 20% gaps, T_max = 0, the 4x4x4 grid (64 templates)."""
+    ds = synth.plain_day()
+    ref = oracle.rho(ds)
+    with cc.CrossCorrPlan(ds.cfg, ds.dets) as plan:
+        x, tm = dev_inputs(ds)
+        got = plan.search(x, tm).cpu().numpy().astype(np.float64)
+    assert_rho_close(got, ref)
+
+
+def test_plain_day_loud_injection_topk():
+    probe = synth.plain_day(noise=False)
+    p = oracle.make_plan(probe.cfg)
+    ds = synth.plain_day(loudness=10.0, f0=p.freq[300])
+    tm = ds.templates
+    inj_t = int(np.argmin(np.abs(tm[:, 0] - 1.44) + np.abs(tm[:, 1] - ds.injection.T_asc)
+                          + np.abs(tm[:, 2] - synth.SCO_X1_P)))
+    sub = tm[[inj_t, 0, 21, 42, 63]]
+    ref = oracle.rho(ds, templates=sub)
+    with cc.CrossCorrPlan(ds.cfg, ds.dets) as plan:
+        x = torch.from_numpy(ds.x64).to(DEV)
+        rho = plan.search(x, torch.from_numpy(sub).to(DEV))
+        hits = plan.topk(rho, 5)
+    assert_rho_close(rho.cpu().numpy().astype(np.float64), ref)
+    ti, bi, _ = oracle.topk(ref, 5)
+    assert (ti[0], bi[0]) == (0, 300)
+    assert list(zip(hits["tmpl"], hits["bin"])) == list(zip(ti, bi))
+
+
+def test_o1_band_full_size_injected_template():
+    """120 days, 60% duty, 0.5 Hz at 150 Hz, T_max = T_short = 3600 s: the full-size
+    workload, checked on the injected template and one far template."""
+    ds = synth.o1_band(n_ap=1, n_tasc=1)
+    inj = ds.injection
+    tm = np.array([[inj.a_p, inj.T_asc, inj.P], [1.52, inj.T_asc + 300.0, inj.P]])
+    ref = oracle.rho(ds, templates=tm)
+    with cc.CrossCorrPlan(ds.cfg, ds.dets) as plan:
+        x = torch.from_numpy(ds.x64).to(DEV)
+        got = plan.search(x, torch.from_numpy(tm).to(DEV)).cpu().numpy().astype(np.float64)
+    assert_rho_close(got, ref)
