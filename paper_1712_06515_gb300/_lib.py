@@ -20,7 +20,7 @@ BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "lib")
 LIBPATH = os.path.join(LIBDIR, "libcrosscorr.so")
 
-SOURCES = ["plan.cu", "stages.cu", "search.cu", "topk.cu"]
+SOURCES = ["plan.cu", "stages.cu", "search.cu", "topk.cu", "fused.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 

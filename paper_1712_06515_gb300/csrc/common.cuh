@@ -56,7 +56,35 @@ struct DevParams {
     const int* coset_k;              // [N_f] output index k, grouped by coset
     const int* coset_m;              // [N_f] position in the coset's L-point transform
     const float2* twL;               // exp(-2 pi i j / L), j < L
+    const float2* twc;               // [C][N_s]: exp(-2 pi i ((b0 + c) s mod N_FFT) / N_FFT)
     float ham[MAX_TAPS];             // Hamming window, 2D+1 taps
+};
+
+constexpr int FUSED_THREADS = 256;
+constexpr int FUSED_WARPS = FUSED_THREADS / 32;
+constexpr int MAX_CLUSTER = 8;
+
+// Shared-memory layout and work split of the fused kernel (byte offsets).
+struct FusedLayout {
+    int CL;            // CTAs per cluster, sharing each segment
+    int S;             // samples per CTA slice, ceil(N_s / CL)
+    int nb;            // max output bins held by one CTA
+    int nkseg;         // max knots per segment (incl. the cubic's neighbours)
+    int nrec;          // max knot records per slice
+    int ring_q;        // detectors kept per ring slot (1: summed; Q: cross-only mode)
+    int64_t chunk_len; // segments per chunk
+    int n_chunks;
+    size_t off_slice, slice_bytes;   // [2][Q][2][S] float2
+    size_t off_fft;                  // [2][L] float2
+    size_t off_ring;                 // [R+1][ring_q][2][nb] float2 (slot K mod (R+1) is written)
+    size_t off_same;                 // [2][nb] float2
+    size_t off_rho;                  // [nb] float, then [nb] float compensation
+    size_t off_dk;                   // [2][Q][nkseg] double
+    size_t off_rec;                  // [2][Q][nrec] KnotRec
+    size_t off_wpart;                // [2][FUSED_WARPS][Q][4] float
+    size_t off_nring;                // [R+1][Q] float4 (rank 0)
+    size_t off_bins;                 // [nb] int2 (m, k) and [ncos+1] int starts
+    size_t bytes;
 };
 
 }  // namespace cc
@@ -70,6 +98,7 @@ struct cc_plan {
     double T_short, T_coh, dlf, N_FFT0, T_FFT, nu_R, f_r, f_FFT;
     std::vector<int64_t> kbar;
     std::vector<double> freq;
+    std::vector<int> coset_off;      // host copy of the coset list offsets [C+1]
     cc::DevParams dp;
     // device allocations owned by the plan
     std::vector<void*> dev_allocs;
@@ -87,6 +116,9 @@ cc_status fail(cc_status s, const std::string& msg);
 cc_status cuda_fail(cudaError_t e, const char* what);
 cc_status ensure_workspace(cc_plan* p, size_t bytes);
 int launch_blocks_for(int64_t n, int threads);
+bool fused_layout(const cc_plan* plan, int64_t n_t, FusedLayout* lay);
+cc_status launch_fused(cc_plan* plan, const cc_template* t_dev, int64_t n_t, float* rho,
+                       const FusedLayout& lay, float* raw, double* dpart, cudaStream_t st);
 void count_launch(uint64_t n = 1);
 
 // ---------------------------------------------------------------------------
@@ -109,6 +141,9 @@ __device__ __forceinline__ void kahan_add(float& sum, float& comp, float v) {
     comp = (t - sum) - y;
     sum = t;
 }
+
+__host__ __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
+__host__ __device__ __forceinline__ int64_t imax64(int64_t a, int64_t b) { return a > b ? a : b; }
 
 __device__ __forceinline__ int64_t floor_div(int64_t a, int64_t b) {
     int64_t q = a / b;

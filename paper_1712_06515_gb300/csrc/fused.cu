@@ -1,0 +1,404 @@
+// Fused resample -> segment spectra -> pair sum, without materialising a_r, b_r or F.
+//
+// One thread-block cluster of CL CTAs handles one (template, chunk of segments).
+// For every segment K:
+//   * each CTA computes the FP64 timing knots it owns (knot index = rank mod CL) for
+//     segment K+1 and resamples its 1/CL slice of segment K (windowed-sinc, heterodyne
+//     and f_r* phase, antenna/noise weights) into shared memory;
+//   * after one cluster barrier every CTA gathers the whole segment from its peers'
+//     shared memory (distributed shared memory), applies the coset twiddle and places
+//     sample r at position r mod L of an L-point buffer (the segment-start phase Phi_in
+//     then falls out of the transform), and runs the L-point FFT of each of its cosets;
+//   * the coset's output bins update the pair sum held on chip: a running sum over
+//     detectors of the current segment and a ring of the R previous segments' sums.
+// Slices, knot delays and norm partials are double-buffered, so one cluster barrier
+// per segment suffices.  Chunks start R segments early to fill the ring; their partial
+// sums and normalisations are combined by finalize_kernel.
+#include <cooperative_groups.h>
+#include <math.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace cc {
+
+
+
+__device__ __forceinline__ const float2* slice_ptr(const FusedLayout& lay, unsigned char* base, int buf,
+                                                   int Q, int X, int w) {
+    return (const float2*)(base + lay.off_slice) + (((size_t)buf * Q + X) * 2 + w) * lay.S;
+}
+
+template <bool CLUSTER>
+__global__ void __launch_bounds__(FUSED_THREADS, 1)
+fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, int64_t t_base,
+             float* __restrict__ raw_out, double* __restrict__ dpart_out) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int CL = lay.CL;
+    const int rank = CLUSTER ? (int)cg::this_cluster().block_rank() : 0;
+    const int chunk = blockIdx.y;
+    const int64_t t = t_base + blockIdx.z;
+    const int Q = p.Q, L = p.L, S = lay.S, nb = lay.nb;
+    const int64_t N_s = p.N_s, R = p.R;
+    const int64_t Ka = (int64_t)chunk * lay.chunk_len;
+    const int64_t Kb = imin64(p.M, Ka + lay.chunk_len);
+    const int64_t Kl = imax64(0, Ka - R);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ncos = (p.C + CL - 1 - rank) / CL;   // cosets c = rank, rank + CL, ...
+
+    float2* fftb = (float2*)(sm + lay.off_fft);
+    float2* ring = (float2*)(sm + lay.off_ring);
+    float2* same = (float2*)(sm + lay.off_same);
+    float* rho = (float*)(sm + lay.off_rho);
+    float* comp = rho + nb;
+    double* dkb = (double*)(sm + lay.off_dk);
+    KnotRec* recb = (KnotRec*)(sm + lay.off_rec);
+    float* wpart = (float*)(sm + lay.off_wpart);
+    float4* nring = (float4*)(sm + lay.off_nring);
+    int2* bins = (int2*)(sm + lay.off_bins);
+    int* cstart = (int*)(bins + nb);
+
+    const cc_template T = tm[t];
+    const double tasc_rel = T.T_asc - p.t0;
+    const double invP = 1.0 / T.P;
+
+    // this CTA's bins: cosets rank, rank+CL, ... concatenated
+    if (tid == 0) {
+        int acc = 0;
+        for (int j = 0; j < ncos; ++j) {
+            cstart[j] = acc;
+            const int c = rank + j * CL;
+            acc += __ldg(p.coset_off + c + 1) - __ldg(p.coset_off + c);
+        }
+        cstart[ncos] = acc;
+    }
+    __syncthreads();
+    const int nmine = cstart[ncos];
+    for (int j = 0; j < ncos; ++j) {
+        const int c = rank + j * CL;
+        const int o = __ldg(p.coset_off + c), n = __ldg(p.coset_off + c + 1) - o;
+        for (int i = tid; i < n; i += FUSED_THREADS)
+            bins[cstart[j] + i] = make_int2(__ldg(p.coset_m + o + i), __ldg(p.coset_k + o + i));
+    }
+    const int64_t R1 = R + 1;
+    const int ringn = R > 0 ? (int)R1 * lay.ring_q * 2 * nb : 0;
+    for (int i = tid; i < ringn; i += FUSED_THREADS) ring[i] = make_float2(0.f, 0.f);
+    for (int i = tid; i < nb; i += FUSED_THREADS) rho[i] = comp[i] = 0.f;
+    if (tid < (int)(R + 1) * Q) nring[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+    double Dacc = 0.0;
+
+    auto knot_range = [&](int64_t K, int64_t* kA) {
+        const int64_t seg0 = K * N_s;
+        *kA = floor_div(seg0, KNOT) - 1;
+        return (int)(floor_div(seg0 + N_s - 1, KNOT) + 2 - *kA + 1);
+    };
+    // FP64 knot delays owned by this CTA for segment K into buffer `buf`
+    auto compute_knots = [&](int64_t K, int buf) {
+        int64_t kA;
+        const int nk = knot_range(K, &kA);
+        const int nown = (nk - rank + CL - 1) / CL;
+        for (int j = tid; j < nown * Q; j += FUSED_THREADS) {
+            const int X = j / nown, i = rank + (j % nown) * CL;
+            dkb[((size_t)buf * Q + X) * lay.nkseg + i] =
+                knot_delay(p, X, T.a_p, tasc_rel, invP, (double)((kA + i) * KNOT) * p.dt);
+        }
+    };
+    auto remote_dk = [&](int buf, int X, int i) -> double {
+        const double* b = dkb + ((size_t)buf * Q + X) * lay.nkseg + i;
+        if (CLUSTER) {
+            cg::cluster_group cl = cg::this_cluster();
+            return *cl.map_shared_rank(b, i % CL);
+        }
+        return *b;
+    };
+    // knot records of this CTA's slice of segment K from the cluster's knot delays
+    auto build_records = [&](int64_t K, int buf) {
+        int64_t kA;
+        knot_range(K, &kA);
+        const int64_t s0 = K * N_s + (int64_t)rank * S;
+        const int64_t s1 = imin64(K * N_s + N_s, s0 + S);
+        if (s1 <= s0) return;
+        const int64_t kr0 = floor_div(s0, KNOT), kr1 = floor_div(s1 - 1, KNOT);
+        const int n = (int)(kr1 - kr0 + 1);
+        for (int j = tid; j < n * Q; j += FUSED_THREADS) {
+            const int X = j / n, jj = j % n;
+            const int i = (int)(kr0 + jj - kA);
+            recb[((size_t)buf * Q + X) * lay.nrec + jj] =
+                make_knot(p, remote_dk(buf, X, i - 1), remote_dk(buf, X, i), remote_dk(buf, X, i + 1),
+                          remote_dk(buf, X, i + 2), (double)((kr0 + jj) * KNOT) * p.dt);
+        }
+    };
+    auto cluster_sync = [&]() {
+        if (CLUSTER)
+            cg::this_cluster().sync();
+        else
+            __syncthreads();
+    };
+
+    // prologue: knots and records of the first segment
+    compute_knots(Kl, 0);
+    cluster_sync();
+    build_records(Kl, 0);
+    __syncthreads();
+
+    for (int64_t K = Kl; K < Kb; ++K) {
+        const int b = (int)((K - Kl) & 1);
+        const int64_t seg0 = K * N_s;
+        // (1) knot delays of the next segment (FP64, a few threads)
+        if (K + 1 < Kb) compute_knots(K + 1, b ^ 1);
+        // (2) resample this CTA's slice of segment K for every detector
+        {
+            const int64_t s0 = seg0 + (int64_t)rank * S;
+            const int64_t s1 = imin64(seg0 + N_s, s0 + S);
+            const int64_t kr0 = floor_div(s0, KNOT);
+            for (int X = 0; X < Q; ++X) {
+                float A = 0.f, B = 0.f, Cn = 0.f;
+                const float2* __restrict__ x = p.x[X];
+                float2* sa = (float2*)slice_ptr(lay, sm, b, Q, X, 0);
+                float2* sb = (float2*)slice_ptr(lay, sm, b, Q, X, 1);
+                const KnotRec* rec = recb + ((size_t)b * Q + X) * lay.nrec;
+                for (int64_t r = s0 + tid; r < s1; r += FUSED_THREADS) {
+                    const int64_t k = r / KNOT;
+                    const KnotRec kr = rec[k - kr0];
+                    const SampleTiming st = sample_timing(p, kr, r, k * KNOT);
+                    const float2 xv = interp_sinc(p, x, st.jstar, st.delta);
+                    float sn, cs;
+                    sincospif(2.0f * st.psi, &sn, &cs);
+                    const float2 xr = cmul(xv, make_float2(cs, sn));
+                    const SampleWeights wt = sample_weights(p, X, st.jstar, st.delta);
+                    sa[r - s0] = cscale(xr, wt.alpha);
+                    sb[r - s0] = cscale(xr, wt.beta);
+                    A = fmaf(wt.alpha * wt.alpha, wt.s2, A);
+                    B = fmaf(wt.beta * wt.beta, wt.s2, B);
+                    Cn = fmaf(wt.alpha * wt.beta, wt.s2, Cn);
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    A += __shfl_xor_sync(0xffffffffu, A, o);
+                    B += __shfl_xor_sync(0xffffffffu, B, o);
+                    Cn += __shfl_xor_sync(0xffffffffu, Cn, o);
+                }
+                if (lane == 0) {
+                    float* wp = wpart + (((size_t)b * FUSED_WARPS + warp) * Q + X) * 4;
+                    wp[0] = A;
+                    wp[1] = B;
+                    wp[2] = Cn;
+                }
+            }
+        }
+        cluster_sync();
+        // (3) knot records of the next segment's slice
+        if (K + 1 < Kb) build_records(K + 1, b ^ 1);
+        // (4) segment norms and the normalisation (rank 0 holds D)
+        if (rank == 0 && tid == 0) {
+            float4 nK[CC_MAX_DET];
+            for (int X = 0; X < Q; ++X) {
+                float s[3] = {0.f, 0.f, 0.f};
+                for (int rr = 0; rr < CL; ++rr) {
+                    const float* wp = wpart + (size_t)b * FUSED_WARPS * Q * 4;
+                    if (CLUSTER) wp = cg::this_cluster().map_shared_rank(wp, rr);
+                    for (int wv = 0; wv < FUSED_WARPS; ++wv)
+                        for (int i = 0; i < 3; ++i) s[i] += wp[(wv * Q + X) * 4 + i];
+                }
+                nK[X] = make_float4(s[0], s[1], s[2], 0.f);
+            }
+            if (K >= Ka) {
+                for (int Y = 0; Y < Q; ++Y) {
+                    double sY = 0.0;
+                    for (int X = 0; X < Y; ++X)
+                        sY += (double)nK[X].x * nK[Y].x + (double)nK[X].y * nK[Y].y +
+                              2.0 * (double)nK[X].z * nK[Y].z;
+                    for (int64_t Lg = imax64(0, K - R); Lg < K; ++Lg)
+                        for (int X = 0; X < Q; ++X) {
+                            if (p.pair_mode == CC_PAIRS_CROSS_ONLY && X == Y) continue;
+                            const float4 nl = nring[(Lg % R) * Q + X];
+                            sY += (double)nl.x * nK[Y].x + (double)nl.y * nK[Y].y + 2.0 * (double)nl.z * nK[Y].z;
+                        }
+                    if (p.pair_mode == CC_PAIRS_ALL_ORDERED)
+                        sY = 2.0 * sY + (double)nK[Y].x * nK[Y].x + (double)nK[Y].y * nK[Y].y +
+                             2.0 * (double)nK[Y].z * nK[Y].z;
+                    Dacc += sY;
+                }
+            }
+            if (R > 0)
+                for (int X = 0; X < Q; ++X) nring[(K % R) * Q + X] = nK[X];
+        }
+        // (5) spectra of this CTA's cosets and the pair sum
+        const int64_t cur = R > 0 ? K % R1 : 0;
+        for (int j = 0; j < ncos; ++j) {
+            const int c = rank + j * CL;
+            const uint64_t N = (uint64_t)p.N_FFT, mask = N - 1;
+            const uint64_t bc = ((uint64_t)p.b0 + (uint64_t)c) & mask;
+            const float2 wseg = twiddle_N((bc * ((uint64_t)seg0 & mask)) & mask, N);
+            const float2* __restrict__ twr = p.twc + (size_t)c * N_s;
+            const int i0 = cstart[j], i1 = cstart[j + 1];
+            const int64_t off0 = ((int64_t)(-seg0) % L + L) % L;   // position of r - seg0 = 0 is (seg0 mod L)
+            for (int w = 0; w < 2; ++w) {
+                for (int X = 0; X < Q; ++X) {
+                    for (int pos = tid; pos < L; pos += FUSED_THREADS) {
+                        float2 acc = make_float2(0.f, 0.f);
+                        for (int64_t rr = (pos + off0) % L; rr < N_s; rr += L) {
+                            const int owner = (int)(rr / S);
+                            const float2* sp = slice_ptr(lay, sm, b, Q, X, w) + (rr - (int64_t)owner * S);
+                            float2 v;
+                            if (CLUSTER)
+                                v = *cg::this_cluster().map_shared_rank(sp, owner);
+                            else
+                                v = *sp;
+                            acc = cadd(acc, cmul(v, __ldg(twr + rr)));
+                        }
+                        fftb[pos] = acc;
+                    }
+                    __syncthreads();
+                    const float2* res = fft_stockham(fftb, fftb + L, L, p.log2L, p.twL);
+                    const bool last = (X == Q - 1);
+                    for (int i = i0 + tid; i < i1; i += FUSED_THREADS) {
+                        const float2 F = cmul(res[bins[i].x], wseg);
+                        float2 h = X == 0 ? make_float2(0.f, 0.f) : same[w * nb + i];
+                        // window: the R slots other than the current segment's
+                        for (int s = 0; s < (int)R1 && R > 0; ++s) {
+                            if (s == (int)cur) continue;
+                            if (lay.ring_q == 1) {
+                                h = cadd(h, ring[((size_t)s * 2 + w) * nb + i]);
+                            } else {
+                                for (int X2 = 0; X2 < Q; ++X2)
+                                    if (X2 != X) h = cadd(h, ring[(((size_t)s * Q + X2) * 2 + w) * nb + i]);
+                            }
+                        }
+                        float term = redot(F, h);
+                        if (p.pair_mode == CC_PAIRS_ALL_ORDERED) term = fmaf(2.f, term, redot(F, F));
+                        if (K >= Ka) kahan_add(rho[i], comp[i], term);
+                        const float2 sn = X == 0 ? F : cadd(same[w * nb + i], F);
+                        same[w * nb + i] = sn;
+                        if (R > 0) {
+                            if (lay.ring_q > 1)
+                                ring[(((size_t)cur * Q + X) * 2 + w) * nb + i] = F;
+                            else if (last)
+                                ring[((size_t)cur * 2 + w) * nb + i] = sn;
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+        }
+    }
+    // every peer may still read this CTA's shared memory until the cluster is done
+    cluster_sync();
+    float* outp = raw_out + ((size_t)t * lay.n_chunks + chunk) * p.N_f;
+    for (int i = tid; i < nmine; i += FUSED_THREADS) outp[bins[i].y] = rho[i];
+    if (rank == 0 && tid == 0) dpart_out[(size_t)t * lay.n_chunks + chunk] = Dacc;
+}
+
+// rho = sqrt(2) sum_chunks raw / sqrt(sum_chunks D), in place on the first chunk's row
+__global__ void finalize_kernel(const float* __restrict__ raw, const double* __restrict__ dpart,
+                                int64_t N_f, int n_chunks, int64_t t_base, float* __restrict__ rho) {
+    const int64_t t = t_base + blockIdx.y;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N_f) return;
+    double D = 0.0;
+    for (int c = 0; c < n_chunks; ++c) D += dpart[(size_t)t * n_chunks + c];
+    float s = 0.f, comp = 0.f;
+    for (int c = 0; c < n_chunks; ++c) kahan_add(s, comp, raw[((size_t)t * n_chunks + c) * N_f + k]);
+    rho[(size_t)t * N_f + k] = D > 0.0 ? (float)(1.4142135623730951 * (double)s / sqrt(D)) : 0.f;
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static size_t al16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+bool fused_layout(const cc_plan* plan, int64_t n_t, FusedLayout* lay) {
+    const DevParams& p = plan->dp;
+    const int C = p.C;
+    int CL = 1;
+    while (CL * 2 <= std::min(C, MAX_CLUSTER)) CL *= 2;
+    if (C % CL) return false;
+    lay->CL = CL;
+    lay->S = (int)((p.N_s + CL - 1) / CL);
+    // bins per CTA: max over ranks of the sum of its cosets' list lengths
+    int nb = 0;
+    const std::vector<int>& off = plan->coset_off;
+    for (int r = 0; r < CL; ++r) {
+        int s = 0;
+        for (int c = r; c < C; c += CL) s += off[c + 1] - off[c];
+        nb = std::max(nb, s);
+    }
+    lay->nb = std::max(nb, 1);
+    lay->nkseg = (int)(p.N_s / KNOT + 5);
+    lay->nrec = lay->S / KNOT + 3;
+    lay->ring_q = p.pair_mode == CC_PAIRS_CROSS_ONLY ? p.Q : 1;
+    const int ncos_max = (C + CL - 1) / CL;
+    size_t o = 0;
+    lay->off_slice = o;
+    lay->slice_bytes = (size_t)2 * p.Q * 2 * lay->S * sizeof(float2);
+    o = al16(o + lay->slice_bytes);
+    lay->off_fft = o;
+    o = al16(o + (size_t)2 * p.L * sizeof(float2));
+    lay->off_ring = o;
+    o = al16(o + (size_t)(p.R > 0 ? p.R + 1 : 0) * lay->ring_q * 2 * lay->nb * sizeof(float2));
+    lay->off_same = o;
+    o = al16(o + (size_t)2 * lay->nb * sizeof(float2));
+    lay->off_rho = o;
+    o = al16(o + (size_t)2 * lay->nb * sizeof(float));
+    lay->off_dk = o;
+    o = al16(o + (size_t)2 * p.Q * lay->nkseg * sizeof(double));
+    lay->off_rec = o;
+    o = al16(o + (size_t)2 * p.Q * lay->nrec * sizeof(KnotRec));
+    lay->off_wpart = o;
+    o = al16(o + (size_t)2 * FUSED_WARPS * p.Q * 4 * sizeof(float));
+    lay->off_nring = o;
+    o = al16(o + (size_t)(p.R + 1) * p.Q * sizeof(float4));
+    lay->off_bins = o;
+    o = al16(o + (size_t)lay->nb * sizeof(int2) + (ncos_max + 1) * sizeof(int));
+    lay->bytes = o;
+    if (lay->bytes > 227 * 1024) return false;
+    if ((int64_t)(p.R + 1) * p.Q > FUSED_THREADS) return false;
+    // chunks: enough CTAs to fill the GPU, each chunk at least 4R + 1 segments
+    int64_t ctas = (int64_t)C / (C / CL) * n_t;   // = CL * n_t clusters' CTAs
+    int64_t want = std::max<int64_t>(1, (4 * 152 + ctas - 1) / std::max<int64_t>(ctas, 1));
+    int64_t maxch = std::max<int64_t>(1, p.M / (4 * p.R + 1));
+    int64_t nch = std::min(want, maxch);
+    lay->chunk_len = (p.M + nch - 1) / nch;
+    lay->n_chunks = (int)((p.M + lay->chunk_len - 1) / lay->chunk_len);
+    return true;
+}
+
+cc_status launch_fused(cc_plan* plan, const cc_template* t_dev, int64_t n_t, float* rho,
+                       const FusedLayout& lay, float* raw, double* dpart, cudaStream_t st) {
+    const DevParams& p = plan->dp;
+    const bool cluster = lay.CL > 1;
+    const void* fn = cluster ? (const void*)fused_kernel<true> : (const void*)fused_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "fused smem attribute");
+    const int64_t MAXZ = 65535;
+    for (int64_t t0 = 0; t0 < n_t; t0 += MAXZ) {
+        const int64_t nt = std::min(MAXZ, n_t - t0);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)lay.CL, (unsigned)lay.n_chunks, (unsigned)nt);
+        cfg.blockDim = dim3(FUSED_THREADS);
+        cfg.dynamicSmemBytes = lay.bytes;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = lay.CL;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        if (cluster)
+            e = cudaLaunchKernelEx(&cfg, fused_kernel<true>, p, lay, t_dev, t0, raw, dpart);
+        else
+            e = cudaLaunchKernelEx(&cfg, fused_kernel<false>, p, lay, t_dev, t0, raw, dpart);
+        count_launch();
+        if (e != cudaSuccess) return cuda_fail(e, "fused launch");
+        dim3 g2((unsigned)launch_blocks_for(p.N_f, 256), (unsigned)nt);
+        finalize_kernel<<<g2, 256, 0, st>>>(raw, dpart, p.N_f, lay.n_chunks, t0, rho);
+        count_launch();
+    }
+    e = cudaGetLastError();
+    return e == cudaSuccess ? CC_OK : cuda_fail(e, "fused launch");
+}
+
+}  // namespace cc

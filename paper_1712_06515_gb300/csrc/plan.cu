@@ -285,8 +285,21 @@ cc_status crosscorr_plan(const cc_config* cfg, const cc_detector* dets, cc_plan*
         double ang = -2.0 * M_PI * (double)j / (double)L;
         tw[j] = make_float2((float)cos(ang), (float)sin(ang));
     }
+    p->coset_off = off;
+    // per-coset twiddles of the segment-local sample index (FP64 phase, exact integer index)
+    const int64_t b0 = ((p->k0 - N / 2) % N + N) % N;
+    std::vector<float2> twc((size_t)C * p->N_s);
+    for (int64_t c2 = 0; c2 < C; ++c2) {
+        const uint64_t bc = (uint64_t)((b0 + c2) % N);
+        for (int64_t r = 0; r < p->N_s; ++r) {
+            const uint64_t j = (bc * (uint64_t)r) % (uint64_t)N;
+            const double ang = -2.0 * M_PI * (double)j / (double)N;
+            twc[(size_t)c2 * p->N_s + r] = make_float2((float)cos(ang), (float)sin(ang));
+        }
+    }
     cc_status st;
-    if ((st = upload(p, off.data(), off.size(), &dp.coset_off)) != CC_OK ||
+    if ((st = upload(p, twc.data(), twc.size(), &dp.twc)) != CC_OK ||
+        (st = upload(p, off.data(), off.size(), &dp.coset_off)) != CC_OK ||
         (st = upload(p, ck.data(), ck.size(), &dp.coset_k)) != CC_OK ||
         (st = upload(p, cm.data(), cm.size(), &dp.coset_m)) != CC_OK ||
         (st = upload(p, tw.data(), tw.size(), &dp.twL)) != CC_OK) {

@@ -40,6 +40,16 @@ extern "C" cc_status crosscorr_search(cc_plan* plan, const void* const* x_dev, c
     cc_status s = set_inputs(plan, x_dev);
     if (s != CC_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
+    FusedLayout lay;
+    if (plan->cfg.store == CC_STORE_FP32 && fused_layout(plan, n_t, &lay)) {
+        // raw partial sums go straight into rho when there is one chunk per template
+        const size_t dbytes = align256((size_t)n_t * lay.n_chunks * sizeof(double));
+        const size_t rbytes = lay.n_chunks > 1 ? (size_t)n_t * lay.n_chunks * plan->N_f * sizeof(float) : 0;
+        if ((s = ensure_workspace(plan, dbytes + rbytes)) != CC_OK) return s;
+        double* dpart = (double*)plan->ws;
+        float* raw = lay.n_chunks > 1 ? (float*)((char*)plan->ws + dbytes) : rho_dev;
+        return launch_fused(plan, t_dev, n_t, rho_dev, lay, raw, dpart, st);
+    }
     int64_t batch;
     size_t bytes;
     staged_batch(plan, n_t, &batch, &bytes);

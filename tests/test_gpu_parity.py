@@ -45,12 +45,13 @@ def assert_rho_close(got, ref, tol=TOL32):
         assert err <= lim, f"template {t}: max |drho| = {err:.3e} > {lim:.3e}"
 
 
-def oracle_ab(ds, plan, tmpl, q):
-    """Oracle a_r, b_r (with the f_r* rotation) and a mask of tie-free samples."""
+def oracle_ab(ds, plan, tmpl, q, rotate=True):
+    """Oracle a_r, b_r (with the f_r* rotation exp(-2 pi i f_r* tau_r) that stage 1
+    applies, unless rotate=False), segment norms, and a mask of tie-free samples."""
     xr, js, de = oracle.resample(ds.x[q], ds.dets[q], ds.cfg, plan, tmpl)
     al, be, s2 = oracle.weights(ds.dets[q], ds.cfg, js, de)
     r = np.arange(plan.M * plan.N_s)
-    rot = np.exp(-2j * np.pi * ((plan.f_r * r * plan.dt) % 1.0))
+    rot = np.exp(-2j * np.pi * ((plan.f_r * r * plan.dt) % 1.0)) if rotate else 1.0
     nsft = int(round(ds.cfg.T_sft / ds.cfg.dt))
     tie = (np.abs(de + 0.5) < 1e-5) | ((np.abs(de) < 1e-5) & (js % nsft == 0))
     return al * xr * rot, be * xr * rot, oracle.segment_norms(al, be, s2, plan), ~tie
@@ -124,7 +125,8 @@ def test_resample_stage_parity(name):
 
 @pytest.mark.parametrize("name", ["default", "fband_005", "T_max0"])
 def test_segment_fft_stage_parity(name):
-    """Oracle a_r, b_r in, GPU spectra out, against the oracle's FFT route."""
+    """Oracle a_r, b_r in, GPU spectra out, against the oracle's FFT route (which
+    applies the f_r* rotation itself, so it gets the unrotated series)."""
     ds = case_ds(name, n_templates=2)
     p = oracle.make_plan(ds.cfg)
     Q = ds.cfg.n_det
@@ -134,8 +136,9 @@ def test_segment_fft_stage_parity(name):
         for q in range(Q):
             a, b, _, _ = oracle_ab(ds, p, tmpl, q)
             ab[t, q, 0], ab[t, q, 1] = a, b
-            Fref[t, q, :, 0] = oracle.spectra_fft(ab[t, q, 0].astype(np.complex128), p)
-            Fref[t, q, :, 1] = oracle.spectra_fft(ab[t, q, 1].astype(np.complex128), p)
+            a0, b0, _, _ = oracle_ab(ds, p, tmpl, q, rotate=False)
+            Fref[t, q, :, 0] = oracle.spectra_fft(a0, p)
+            Fref[t, q, :, 1] = oracle.spectra_fft(b0, p)
     with cc.CrossCorrPlan(ds.cfg, ds.dets) as plan:
         F = plan.segment_fft(torch.from_numpy(ab).to(DEV), 2).cpu().numpy()
     err = np.abs(F - Fref).max()
