@@ -18,8 +18,8 @@ namespace cc {
 constexpr int KNOT = 128;
 constexpr int MAX_D = 32;
 constexpr int MAX_TAPS = 2 * MAX_D + 1;
-constexpr int N_BIN_ITER = 6;   // fixed-point steps of u = tau + a_p sin(Omega (u - T_asc))
-constexpr int N_SSB_ITER = 5;   // fixed-point steps of t = u - Delta(t)
+constexpr int N_BIN_ITER = 4;   // fixed-point steps of the binary delay b = a_p sin(Omega (tau + b - T_asc))
+constexpr int N_SSB_ITER = 4;   // fixed-point steps of t = u - Delta(t)
 constexpr int MAX_L = 8192;     // largest on-chip coset FFT
 
 // Timing record of one knot, built from four FP64 knot delays.
@@ -41,11 +41,11 @@ struct DevParams {
     int64_t N_t, N_s, M, R, N_tau, N_FFT, N_f;
     int64_t b0;      // (k0 - N_FFT/2) mod N_FFT: FFT bin of output k = 0
     int64_t ab_j0;   // ab_t0 / dt
-    double dt, t0, f_h, f_r;
+    double dt, inv_dt, t0, f_h, f_r;
     float f_h_dt, f_r_dt;
     const float2* x[CC_MAX_DET];
     const double* ssb[CC_MAX_DET];
-    double eph_t0[CC_MAX_DET], eph_dt[CC_MAX_DET];
+    double eph_t0[CC_MAX_DET], eph_dt[CC_MAX_DET], inv_eph_dt[CC_MAX_DET];
     int64_t n_eph[CC_MAX_DET];
     const float* atab[CC_MAX_DET];
     const float* btab[CC_MAX_DET];
@@ -150,10 +150,11 @@ __device__ __forceinline__ int64_t floor_div(int64_t a, int64_t b) {
     return (q * b > a) ? q - 1 : q;
 }
 
-// Linear interpolation of an FP64 table at time t (end intervals extrapolate).
-__device__ __forceinline__ double table_lerp(const double* tab, double t0, double dt, int64_t n,
+// Linear interpolation of an FP64 table at time t (end intervals extrapolate);
+// inv_dt = 1 / table spacing.
+__device__ __forceinline__ double table_lerp(const double* tab, double t0, double inv_dt, int64_t n,
                                              double t) {
-    double u = (t - t0) / dt;
+    double u = (t - t0) * inv_dt;
     double fi = floor(u);
     int64_t i = (int64_t)fi;
     i = i < 0 ? 0 : (i > n - 2 ? n - 2 : i);
@@ -163,21 +164,35 @@ __device__ __forceinline__ double table_lerp(const double* tab, double t0, doubl
 }
 
 // d(tau) = tau - t(tau) for detector X and one template (all times relative to t0).
-// tau(t) = t_SSB - a_p sin(Omega (t_SSB - T_asc)), t_SSB = t + Delta_X(t); the two
-// fixed points are iterated on the small quantities b = t_SSB - tau and
-// Delta = t_SSB - t so that d = Delta - b keeps FP64 precision.
+// tau(t) = t_SSB - a_p sin(Omega (t_SSB - T_asc)), t_SSB = t + Delta_X(t).
+// Binary part: b = a_p sin(theta0 + Omega b) with theta0 = Omega (tau - T_asc); one
+// FP64 sincospi at theta0, then fixed-point steps through the angle-addition formula
+// with sin/cos of the small angle Omega b (|Omega b| <= 1.4e-4 rad) from their series
+// (remainders below 1e-26); the contraction a_p Omega ~ 1.3e-4 per step leaves
+// < 1e-15 s after N_BIN_ITER steps.  SSB part: t = u - Delta(t), u = tau + b, iterated
+// on Delta from Delta(u) (contraction |Delta'| <= 1e-4).  Both work on the small
+// quantities b and Delta so d = Delta - b keeps FP64 precision.
 __device__ __forceinline__ double knot_delay(const DevParams& p, int X, double a_p,
                                              double tasc_rel, double invP, double tau) {
-    double b = 0.0;
-#pragma unroll 1
-    for (int it = 0; it < N_BIN_ITER; ++it)
-        b = a_p * sinpi(2.0 * (((tau + b) - tasc_rel) * invP));
+    const double x0 = (tau - tasc_rel) * invP;            // orbital phase in cycles
+    double s0, c0;
+    sincospi(2.0 * x0, &s0, &c0);
+    const double om = 6.283185307179586 * invP;           // Omega
+    double b = a_p * s0;
+#pragma unroll
+    for (int it = 0; it < N_BIN_ITER; ++it) {
+        const double dl = om * b, d2 = dl * dl;
+        const double sd = dl * (1.0 - d2 * (1.0 / 6.0) * (1.0 - d2 * (1.0 / 20.0)));
+        const double cd = 1.0 - d2 * 0.5 * (1.0 - d2 * (1.0 / 12.0));
+        b = a_p * fma(s0, cd, c0 * sd);
+    }
     const double* tab = p.ssb[X];
-    double t0 = p.eph_t0[X], edt = p.eph_dt[X];
-    int64_t n = p.n_eph[X];
-    double dl = table_lerp(tab, t0, edt, n, tau);
-#pragma unroll 1
-    for (int it = 0; it < N_SSB_ITER; ++it) dl = table_lerp(tab, t0, edt, n, (tau + b) - dl);
+    const double t0 = p.eph_t0[X], inv = p.inv_eph_dt[X];
+    const int64_t n = p.n_eph[X];
+    const double u = tau + b;
+    double dl = table_lerp(tab, t0, inv, n, u);
+#pragma unroll
+    for (int it = 0; it < N_SSB_ITER; ++it) dl = table_lerp(tab, t0, inv, n, u - dl);
     return dl - b;
 }
 
@@ -186,13 +201,13 @@ __device__ __forceinline__ double knot_delay(const DevParams& p, int X, double a
 __device__ __forceinline__ KnotRec make_knot(const DevParams& p, double dm1, double d0,
                                              double dp1, double dp2, double tau_k) {
     KnotRec r;
-    double e = d0 / p.dt;
+    double e = d0 * p.inv_dt;
     double fl = floor(e);
     r.N = (int)fl;
     r.f = (float)(e - fl);
-    r.dm1 = (float)((dm1 - d0) / p.dt);
-    r.dp1 = (float)((dp1 - d0) / p.dt);
-    r.dp2 = (float)((dp2 - d0) / p.dt);
+    r.dm1 = (float)((dm1 - d0) * p.inv_dt);
+    r.dp1 = (float)((dp1 - d0) * p.inv_dt);
+    r.dp2 = (float)((dp2 - d0) * p.inv_dt);
     double c = -p.f_h * d0 - p.f_r * tau_k;
     r.psi = (float)(c - floor(c));
     r.pad0 = r.pad1 = 0.f;

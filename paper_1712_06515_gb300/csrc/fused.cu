@@ -100,7 +100,9 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
         int64_t kA;
         const int nk = knot_range(K, &kA);
         const int nown = (nk - rank + CL - 1) / CL;
-        for (int j = tid; j < nown * Q; j += FUSED_THREADS) {
+        // the block's last threads carry the lightest resampling share, so the FP64
+        // chains start there and overlap the others' FP32 work
+        for (int j = FUSED_THREADS - 1 - tid; j < nown * Q && j >= 0; j += FUSED_THREADS) {
             const int X = j / nown, i = rank + (j % nown) * CL;
             dkb[((size_t)buf * Q + X) * lay.nkseg + i] =
                 knot_delay(p, X, T.a_p, tasc_rel, invP, (double)((kA + i) * KNOT) * p.dt);
@@ -191,39 +193,53 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
         cluster_sync();
         // (3) knot records of the next segment's slice
         if (K + 1 < Kb) build_records(K + 1, b ^ 1);
-        // (4) segment norms and the normalisation (rank 0 holds D)
-        if (rank == 0 && tid == 0) {
-            float4 nK[CC_MAX_DET];
-            for (int X = 0; X < Q; ++X) {
-                float s[3] = {0.f, 0.f, 0.f};
-                for (int rr = 0; rr < CL; ++rr) {
-                    const float* wp = wpart + (size_t)b * FUSED_WARPS * Q * 4;
-                    if (CLUSTER) wp = cg::this_cluster().map_shared_rank(wp, rr);
-                    for (int wv = 0; wv < FUSED_WARPS; ++wv)
-                        for (int i = 0; i < 3; ++i) s[i] += wp[(wv * Q + X) * 4 + i];
-                }
-                nK[X] = make_float4(s[0], s[1], s[2], 0.f);
+        // (4) segment norms and the normalisation (rank 0 holds D): one thread per
+        //     (peer, detector, component) sums that peer's warp partials
+        if (rank == 0) {
+            float* nsum = wpart + (size_t)2 * FUSED_WARPS * Q * 4;   // [CL][Q][3] scratch
+            if (tid < CL * Q * 3) {
+                const int rr = tid / (Q * 3), X = (tid / 3) % Q, i = tid % 3;
+                const float* wp = wpart + (size_t)b * FUSED_WARPS * Q * 4;
+                if (CLUSTER) wp = cg::this_cluster().map_shared_rank(wp, rr);
+                float v[FUSED_WARPS];
+#pragma unroll
+                for (int wv = 0; wv < FUSED_WARPS; ++wv) v[wv] = wp[(wv * Q + X) * 4 + i];
+                float sacc = 0.f;
+#pragma unroll
+                for (int wv = 0; wv < FUSED_WARPS; ++wv) sacc += v[wv];
+                nsum[tid] = sacc;
             }
-            if (K >= Ka) {
-                for (int Y = 0; Y < Q; ++Y) {
-                    double sY = 0.0;
-                    for (int X = 0; X < Y; ++X)
-                        sY += (double)nK[X].x * nK[Y].x + (double)nK[X].y * nK[Y].y +
-                              2.0 * (double)nK[X].z * nK[Y].z;
-                    for (int64_t Lg = imax64(0, K - R); Lg < K; ++Lg)
-                        for (int X = 0; X < Q; ++X) {
-                            if (p.pair_mode == CC_PAIRS_CROSS_ONLY && X == Y) continue;
-                            const float4 nl = nring[(Lg % R) * Q + X];
-                            sY += (double)nl.x * nK[Y].x + (double)nl.y * nK[Y].y + 2.0 * (double)nl.z * nK[Y].z;
-                        }
-                    if (p.pair_mode == CC_PAIRS_ALL_ORDERED)
-                        sY = 2.0 * sY + (double)nK[Y].x * nK[Y].x + (double)nK[Y].y * nK[Y].y +
-                             2.0 * (double)nK[Y].z * nK[Y].z;
-                    Dacc += sY;
+            __syncthreads();
+            if (tid == 0) {
+                float4 nK[CC_MAX_DET];
+                for (int X = 0; X < Q; ++X) {
+                    float sv[3] = {0.f, 0.f, 0.f};
+                    for (int rr = 0; rr < CL; ++rr)
+                        for (int i = 0; i < 3; ++i) sv[i] += nsum[(rr * Q + X) * 3 + i];
+                    nK[X] = make_float4(sv[0], sv[1], sv[2], 0.f);
                 }
+                if (K >= Ka) {
+                    for (int Y = 0; Y < Q; ++Y) {
+                        double sY = 0.0;
+                        for (int X = 0; X < Y; ++X)
+                            sY += (double)nK[X].x * nK[Y].x + (double)nK[X].y * nK[Y].y +
+                                  2.0 * (double)nK[X].z * nK[Y].z;
+                        for (int64_t Lg = imax64(0, K - R); Lg < K; ++Lg)
+                            for (int X = 0; X < Q; ++X) {
+                                if (p.pair_mode == CC_PAIRS_CROSS_ONLY && X == Y) continue;
+                                const float4 nl = nring[(Lg % R) * Q + X];
+                                sY += (double)nl.x * nK[Y].x + (double)nl.y * nK[Y].y +
+                                      2.0 * (double)nl.z * nK[Y].z;
+                            }
+                        if (p.pair_mode == CC_PAIRS_ALL_ORDERED)
+                            sY = 2.0 * sY + (double)nK[Y].x * nK[Y].x + (double)nK[Y].y * nK[Y].y +
+                                 2.0 * (double)nK[Y].z * nK[Y].z;
+                        Dacc += sY;
+                    }
+                }
+                if (R > 0)
+                    for (int X = 0; X < Q; ++X) nring[(K % R) * Q + X] = nK[X];
             }
-            if (R > 0)
-                for (int X = 0; X < Q; ++X) nring[(K % R) * Q + X] = nK[X];
         }
         // (5) spectra of this CTA's cosets and the pair sum
         const int64_t cur = R > 0 ? K % R1 : 0;
@@ -237,19 +253,44 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
             const int64_t off0 = ((int64_t)(-seg0) % L + L) % L;   // position of r - seg0 = 0 is (seg0 mod L)
             for (int w = 0; w < 2; ++w) {
                 for (int X = 0; X < Q; ++X) {
-                    for (int pos = tid; pos < L; pos += FUSED_THREADS) {
-                        float2 acc = make_float2(0.f, 0.f);
-                        for (int64_t rr = (pos + off0) % L; rr < N_s; rr += L) {
-                            const int owner = (int)(rr / S);
-                            const float2* sp = slice_ptr(lay, sm, b, Q, X, w) + (rr - (int64_t)owner * S);
-                            float2 v;
-                            if (CLUSTER)
-                                v = *cg::this_cluster().map_shared_rank(sp, owner);
-                            else
-                                v = *sp;
-                            acc = cadd(acc, cmul(v, __ldg(twr + rr)));
+                    if (N_s <= L) {
+                        // one sample per position: zero the padding, then gather with
+                        // four independent peer loads in flight per thread
+                        const int offp = (int)(seg0 & (L - 1));
+                        for (int rr = (int)N_s + tid; rr < L; rr += FUSED_THREADS)
+                            fftb[(offp + rr) & (L - 1)] = make_float2(0.f, 0.f);
+                        for (int rr0 = tid; rr0 < (int)N_s; rr0 += 4 * FUSED_THREADS) {
+                            float2 v[4], tw[4];
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                const int rr = rr0 + u * FUSED_THREADS;
+                                v[u] = make_float2(0.f, 0.f);
+                                tw[u] = make_float2(0.f, 0.f);
+                                if (rr < (int)N_s) {
+                                    const int owner = rr / S;
+                                    const float2* sp = slice_ptr(lay, sm, b, Q, X, w) + (rr - owner * S);
+                                    v[u] = CLUSTER ? *cg::this_cluster().map_shared_rank(sp, owner) : *sp;
+                                    tw[u] = __ldg(twr + rr);
+                                }
+                            }
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                const int rr = rr0 + u * FUSED_THREADS;
+                                if (rr < (int)N_s) fftb[(offp + rr) & (L - 1)] = cmul(v[u], tw[u]);
+                            }
                         }
-                        fftb[pos] = acc;
+                    } else {
+                        // folded: several samples per position, summed in index order
+                        for (int pos = tid; pos < L; pos += FUSED_THREADS) {
+                            float2 acc = make_float2(0.f, 0.f);
+                            for (int64_t rr = (pos + off0) % L; rr < N_s; rr += L) {
+                                const int owner = (int)(rr / S);
+                                const float2* sp = slice_ptr(lay, sm, b, Q, X, w) + (rr - (int64_t)owner * S);
+                                const float2 v = CLUSTER ? *cg::this_cluster().map_shared_rank(sp, owner) : *sp;
+                                acc = cadd(acc, cmul(v, __ldg(twr + rr)));
+                            }
+                            fftb[pos] = acc;
+                        }
                     }
                     __syncthreads();
                     const float2* res = fft_stockham(fftb, fftb + L, L, p.log2L, p.twL);
@@ -347,7 +388,7 @@ bool fused_layout(const cc_plan* plan, int64_t n_t, FusedLayout* lay) {
     lay->off_rec = o;
     o = al16(o + (size_t)2 * p.Q * lay->nrec * sizeof(KnotRec));
     lay->off_wpart = o;
-    o = al16(o + (size_t)2 * FUSED_WARPS * p.Q * 4 * sizeof(float));
+    o = al16(o + ((size_t)2 * FUSED_WARPS * p.Q * 4 + (size_t)MAX_CLUSTER * p.Q * 3) * sizeof(float));
     lay->off_nring = o;
     o = al16(o + (size_t)(p.R + 1) * p.Q * sizeof(float4));
     lay->off_bins = o;

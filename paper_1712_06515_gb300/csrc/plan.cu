@@ -262,6 +262,7 @@ cc_status crosscorr_plan(const cc_config* cfg, const cc_detector* dets, cc_plan*
         }
         dp.eph_t0[q] = d.eph_t0;
         dp.eph_dt[q] = d.eph_dt;
+        dp.inv_eph_dt[q] = 1.0 / d.eph_dt;
         dp.n_eph[q] = d.n_eph;
         dp.n_ab[q] = d.n_ab;
         dp.n_sig[q] = d.n_sigma;
@@ -324,6 +325,7 @@ cc_status crosscorr_plan(const cc_config* cfg, const cc_detector* dets, cc_plan*
     dp.N_f = p->N_f;
     dp.b0 = ((p->k0 - N / 2) % N + N) % N;
     dp.dt = dt;
+    dp.inv_dt = 1.0 / dt;
     dp.t0 = c.t0;
     dp.f_h = c.f_h;
     dp.f_r = p->f_r;
