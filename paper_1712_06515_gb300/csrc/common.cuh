@@ -60,7 +60,7 @@ struct DevParams {
     float ham[MAX_TAPS];             // Hamming window, 2D+1 taps
 };
 
-constexpr int FUSED_THREADS = 256;
+constexpr int FUSED_THREADS = 512;
 constexpr int FUSED_WARPS = FUSED_THREADS / 32;
 constexpr int MAX_CLUSTER = 8;
 
@@ -72,12 +72,13 @@ struct FusedLayout {
     int nkseg;         // max knots per segment (incl. the cubic's neighbours)
     int nrec;          // max knot records per slice
     int ring_q;        // detectors kept per ring slot (1: summed; Q: cross-only mode)
+    float invS;        // 1 / S
     int64_t chunk_len; // segments per chunk
     int n_chunks;
     size_t off_slice, slice_bytes;   // [2][Q][2][S] float2
-    size_t off_fft;                  // [2][L] float2
-    size_t off_ring;                 // [R+1][ring_q][2][nb] float2 (slot K mod (R+1) is written)
-    size_t off_same;                 // [2][nb] float2
+    size_t off_fft;                  // [2 halves][padded L] float2
+    size_t off_ring;                 // [slots][ring_q][2][nb] float2; slots = R (summed) or R+1
+    size_t off_same;                 // [nb] float2: running detector sum across rounds
     size_t off_rho;                  // [nb] float, then [nb] float compensation
     size_t off_dk;                   // [2][Q][nkseg] double
     size_t off_rec;                  // [2][Q][nrec] KnotRec

@@ -1,0 +1,179 @@
+// Register-resident radix-16/8/4/2 DFT kernels and a Stockham pass for L-point FFTs
+// (L = 2^n <= 4096) done by 256 threads with one butterfly per thread per pass.
+//
+// Shared-memory layout: element p of the L-point buffer lives at padi(p) = p + p/16,
+// which makes every pass's 8-byte loads and stores bank-conflict free (radix-16
+// Stockham writes with stride 16 elements become stride 17).
+#pragma once
+
+#include "common.cuh"
+
+namespace cc {
+
+__device__ __forceinline__ int padi(int p) { return p + (p >> 4); }
+__host__ __device__ constexpr int padded_len(int L) { return L + L / 16; }
+
+// cos(pi/8), sin(pi/8), sqrt(1/2)
+constexpr float kC8 = 0.923879532511286756f;
+constexpr float kS8 = 0.382683432365089772f;
+constexpr float kR2 = 0.707106781186547524f;
+
+__device__ __forceinline__ void dft2(float2& a, float2& b) {
+    const float2 t = a;
+    a = cadd(t, b);
+    b = csub(t, b);
+}
+
+// forward 4-point DFT in place, natural order
+__device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
+    const float2 s0 = cadd(a0, a2), d0 = csub(a0, a2), s1 = cadd(a1, a3), d1 = mul_negi(csub(a1, a3));
+    a0 = cadd(s0, s1);
+    a2 = csub(s0, s1);
+    a1 = cadd(d0, d1);
+    a3 = csub(d0, d1);
+}
+
+// multiplication by exp(-2 pi i e / 16) for the constant exponents of the 4x4 split
+template <int E>
+__device__ __forceinline__ float2 w16(float2 a) {
+    if constexpr (E == 0) return a;
+    else if constexpr (E == 1) return cmul(a, make_float2(kC8, -kS8));
+    else if constexpr (E == 2) return make_float2(kR2 * (a.x + a.y), kR2 * (a.y - a.x));
+    else if constexpr (E == 3) return cmul(a, make_float2(kS8, -kC8));
+    else if constexpr (E == 4) return mul_negi(a);
+    else if constexpr (E == 6) return make_float2(kR2 * (a.y - a.x), -kR2 * (a.x + a.y));
+    else return cmul(a, make_float2(-kC8, kS8));   // E == 9
+}
+
+// 16-point DFT: n = 4 n1 + n2, k = k1 + 4 k2; inner 4-point DFTs over n1, twiddles
+// W16^(n2 k1), outer 4-point DFTs over n2.  Result in natural order.
+__device__ __forceinline__ void dft16(float2 (&v)[16]) {
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft4(v[n2], v[n2 + 4], v[n2 + 8], v[n2 + 12]);
+    // v[n2 + 4 k1] = Y[n2][k1]
+    v[5] = w16<1>(v[5]);
+    v[9] = w16<2>(v[9]);
+    v[13] = w16<3>(v[13]);
+    v[6] = w16<2>(v[6]);
+    v[10] = w16<4>(v[10]);
+    v[14] = w16<6>(v[14]);
+    v[7] = w16<3>(v[7]);
+    v[11] = w16<6>(v[11]);
+    v[15] = w16<9>(v[15]);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft4(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+    // v[4 k1 + k2] = X[k1 + 4 k2]: transpose to natural order
+    float2 t[16];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) t[k1 + 4 * k2] = v[4 * k1 + k2];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = t[i];
+}
+
+// 8-point DFT: n = 4 n1 + n2 (n1 < 2), k = k1 + 2 k2.
+__device__ __forceinline__ void dft8(float2 (&v)[16]) {
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft2(v[n2], v[n2 + 4]);
+    v[5] = w16<2>(v[5]);   // W8^1
+    v[6] = w16<4>(v[6]);   // W8^2
+    v[7] = w16<6>(v[7]);   // W8^3
+    dft4(v[0], v[1], v[2], v[3]);
+    dft4(v[4], v[5], v[6], v[7]);
+    float2 t[8];
+#pragma unroll
+    for (int k1 = 0; k1 < 2; ++k1)
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) t[k1 + 2 * k2] = v[4 * k1 + k2];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = t[i];
+}
+
+template <int R>
+__device__ __forceinline__ void dft_r(float2 (&v)[16]) {
+    if constexpr (R == 16) dft16(v);
+    else if constexpr (R == 8) dft8(v);
+    else if constexpr (R == 4) dft4(v[0], v[1], v[2], v[3]);
+    else if constexpr (R == 2) dft2(v[0], v[1]);
+}
+
+// v[r] *= W_L^(step r) for r = 1..R-1, from the L-point table: W^step, W^2step,
+// W^4step, W^8step are loaded and the rest formed by at most three products.
+template <int R>
+__device__ __forceinline__ void apply_twiddles(float2 (&v)[16], const float2* __restrict__ twL, int step,
+                                               int mask) {
+    if constexpr (R == 2) {
+        v[1] = cmul(v[1], __ldg(twL + step));
+    } else {
+        const float2 w1 = __ldg(twL + step);
+        const float2 w2 = __ldg(twL + ((2 * step) & mask));
+        const float2 w3 = cmul(w2, w1);
+        v[1] = cmul(v[1], w1);
+        v[2] = cmul(v[2], w2);
+        v[3] = cmul(v[3], w3);
+        if constexpr (R >= 8) {
+            const float2 w4 = __ldg(twL + ((4 * step) & mask));
+            v[4] = cmul(v[4], w4);
+            v[5] = cmul(v[5], cmul(w4, w1));
+            v[6] = cmul(v[6], cmul(w4, w2));
+            v[7] = cmul(v[7], cmul(w4, w3));
+            if constexpr (R == 16) {
+                const float2 w8 = __ldg(twL + ((8 * step) & mask));
+                v[8] = cmul(v[8], w8);
+#pragma unroll
+                for (int r = 9; r < 16; ++r) {
+                    const int lo = r - 8;
+                    const float2 wl = lo == 1 ? w1 : lo == 2 ? w2 : lo == 3 ? w3 : lo == 4 ? w4
+                                    : lo == 5 ? cmul(w4, w1) : lo == 6 ? cmul(w4, w2) : cmul(w4, w3);
+                    v[r] = cmul(v[r], cmul(w8, wl));
+                }
+            }
+        }
+    }
+}
+
+// One Stockham pass of radix R over an L-point buffer in padded shared memory, done
+// in place: loads, twiddles and the DFT in registers, barrier, stores.  `j` is this
+// thread's butterfly (active if j < L/R); `sync` is the barrier of the threads that
+// share the buffer.  Ns is the product of the radices of the earlier passes.
+template <int R, typename Sync>
+__device__ __forceinline__ void stockham_pass(float2* buf, int L, int Ns, int j,
+                                              const float2* __restrict__ twL, Sync sync) {
+    const int B = L / R;
+    float2 v[16];
+    const bool act = j < B;
+    const int k = j & (Ns - 1);
+    if (act) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = buf[padi(j + r * B)];
+        if (Ns > 1) apply_twiddles<R>(v, twL, k * (L / (Ns * R)), L - 1);
+        dft_r<R>(v);
+    }
+    sync();
+    if (act) {
+        const int idxD = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[padi(idxD + r * Ns)] = v[r];
+    }
+    sync();
+}
+
+// Stockham passes after the first one (which the caller runs on gathered registers):
+// radix-16 passes while at least 16 remain, then one pass of the leftover radix.
+template <typename Sync>
+__device__ __forceinline__ void stockham_rest(float2* buf, int L, int log2L, int Ns, int j,
+                                              const float2* __restrict__ twL, Sync sync) {
+    int rem = log2L;
+    for (int n = Ns; n > 1; n >>= 1) --rem;   // bits already transformed
+    while (rem >= 4) {
+        stockham_pass<16>(buf, L, Ns, j, twL, sync);
+        Ns <<= 4;
+        rem -= 4;
+    }
+    if (rem == 3) stockham_pass<8>(buf, L, Ns, j, twL, sync);
+    else if (rem == 2) stockham_pass<4>(buf, L, Ns, j, twL, sync);
+    else if (rem == 1) stockham_pass<2>(buf, L, Ns, j, twL, sync);
+}
+
+}  // namespace cc

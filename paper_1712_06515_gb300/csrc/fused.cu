@@ -7,8 +7,10 @@
 //     and f_r* phase, antenna/noise weights) into shared memory;
 //   * after one cluster barrier every CTA gathers the whole segment from its peers'
 //     shared memory (distributed shared memory), applies the coset twiddle and places
-//     sample r at position r mod L of an L-point buffer (the segment-start phase Phi_in
-//     then falls out of the transform), and runs the L-point FFT of each of its cosets;
+//     sample r at position r mod L of an L-point transform (the segment-start phase
+//     Phi_in then falls out of the transform).  The two halves of the CTA (256 threads
+//     each) transform two detectors at once: the gather lands in the registers of the
+//     first radix-16 Stockham pass, later passes go through a padded buffer per half;
 //   * the coset's output bins update the pair sum held on chip: a running sum over
 //     detectors of the current segment and a ring of the R previous segments' sums.
 // Slices, knot delays and norm partials are double-buffered, so one cluster barrier
@@ -20,6 +22,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "fft_reg.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -31,6 +34,14 @@ __device__ __forceinline__ const float2* slice_ptr(const FusedLayout& lay, unsig
                                                    int Q, int X, int w) {
     return (const float2*)(base + lay.off_slice) + (((size_t)buf * Q + X) * 2 + w) * lay.S;
 }
+
+// barrier of one 256-thread half of the CTA (named barrier 1 or 2)
+struct HalfSync {
+    int id;
+    __device__ __forceinline__ void operator()() const {
+        asm volatile("bar.sync %0, 256;" ::"r"(id) : "memory");
+    }
+};
 
 template <bool CLUSTER>
 __global__ void __launch_bounds__(FUSED_THREADS, 1)
@@ -83,8 +94,8 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
         for (int i = tid; i < n; i += FUSED_THREADS)
             bins[cstart[j] + i] = make_int2(__ldg(p.coset_m + o + i), __ldg(p.coset_k + o + i));
     }
-    const int64_t R1 = R + 1;
-    const int ringn = R > 0 ? (int)R1 * lay.ring_q * 2 * nb : 0;
+    const int64_t nslot = lay.ring_q > 1 ? R + 1 : R;   // per-detector rings keep one spare slot
+    const int ringn = R > 0 ? (int)nslot * lay.ring_q * 2 * nb : 0;
     for (int i = tid; i < ringn; i += FUSED_THREADS) ring[i] = make_float2(0.f, 0.f);
     for (int i = tid; i < nb; i += FUSED_THREADS) rho[i] = comp[i] = 0.f;
     if (tid < (int)(R + 1) * Q) nring[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -241,8 +252,17 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
                     for (int X = 0; X < Q; ++X) nring[(K % R) * Q + X] = nK[X];
             }
         }
-        // (5) spectra of this CTA's cosets and the pair sum
-        const int64_t cur = R > 0 ? K % R1 : 0;
+        // (5) spectra of this CTA's cosets and the pair sum.  Rounds of two detectors:
+        //     half h of the CTA transforms detector 2g + h of round g.
+        const int half = tid >> 8, lt = tid & 255;
+        const HalfSync hsync{1 + half};
+        const int PL = padded_len(L);
+        float2* hbuf = fftb + (size_t)half * PL;
+        const int R1 = L >= 16 ? 16 : L;      // radix of the first pass
+        const int B1 = L / R1;
+        const int offn = (int)((-seg0) & (int64_t)(L - 1));   // position p holds r - seg0 = (p + offn) mod L
+        const int64_t cur = R > 0 ? K % nslot : 0;
+        const int nround = (Q + 1) / 2;
         for (int j = 0; j < ncos; ++j) {
             const int c = rank + j * CL;
             const uint64_t N = (uint64_t)p.N_FFT, mask = N - 1;
@@ -250,75 +270,88 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
             const float2 wseg = twiddle_N((bc * ((uint64_t)seg0 & mask)) & mask, N);
             const float2* __restrict__ twr = p.twc + (size_t)c * N_s;
             const int i0 = cstart[j], i1 = cstart[j + 1];
-            const int64_t off0 = ((int64_t)(-seg0) % L + L) % L;   // position of r - seg0 = 0 is (seg0 mod L)
             for (int w = 0; w < 2; ++w) {
-                for (int X = 0; X < Q; ++X) {
-                    if (N_s <= L) {
-                        // one sample per position: zero the padding, then gather with
-                        // four independent peer loads in flight per thread
-                        const int offp = (int)(seg0 & (L - 1));
-                        for (int rr = (int)N_s + tid; rr < L; rr += FUSED_THREADS)
-                            fftb[(offp + rr) & (L - 1)] = make_float2(0.f, 0.f);
-                        for (int rr0 = tid; rr0 < (int)N_s; rr0 += 4 * FUSED_THREADS) {
-                            float2 v[4], tw[4];
+                for (int g = 0; g < nround; ++g) {
+                    const int X = 2 * g + half;
+                    if (X < Q) {
+                        const float2* sbase = slice_ptr(lay, sm, b, Q, X, w);
+                        float2 v[16];
+                        if (lt < B1) {
+                            if (N_s <= L) {
+                                float2 vv[16], tw[16];
 #pragma unroll
-                            for (int u = 0; u < 4; ++u) {
-                                const int rr = rr0 + u * FUSED_THREADS;
-                                v[u] = make_float2(0.f, 0.f);
-                                tw[u] = make_float2(0.f, 0.f);
-                                if (rr < (int)N_s) {
-                                    const int owner = rr / S;
-                                    const float2* sp = slice_ptr(lay, sm, b, Q, X, w) + (rr - owner * S);
-                                    v[u] = CLUSTER ? *cg::this_cluster().map_shared_rank(sp, owner) : *sp;
-                                    tw[u] = __ldg(twr + rr);
+                                for (int r = 0; r < 16; ++r) {
+                                    vv[r] = tw[r] = make_float2(0.f, 0.f);
+                                    const int rr = (lt + r * B1 + offn) & (L - 1);
+                                    if (r < R1 && rr < (int)N_s) {
+                                        int owner = (int)((float)rr * lay.invS);
+                                        owner -= (owner * S > rr);
+                                        owner += ((owner + 1) * S <= rr);
+                                        const float2* sp = sbase + (rr - owner * S);
+                                        vv[r] = CLUSTER ? *cg::this_cluster().map_shared_rank(sp, owner) : *sp;
+                                        tw[r] = __ldg(twr + rr);
+                                    }
+                                }
+#pragma unroll
+                                for (int r = 0; r < 16; ++r) v[r] = cmul(vv[r], tw[r]);
+                            } else {
+#pragma unroll
+                                for (int r = 0; r < 16; ++r) {
+                                    float2 acc = make_float2(0.f, 0.f);
+                                    if (r < R1) {
+                                        for (int64_t rr = (lt + r * B1 + offn) & (L - 1); rr < N_s; rr += L) {
+                                            const int owner = (int)(rr / S);
+                                            const float2* sp = sbase + (rr - (int64_t)owner * S);
+                                            const float2 vr = CLUSTER ? *cg::this_cluster().map_shared_rank(sp, owner) : *sp;
+                                            acc = cadd(acc, cmul(vr, __ldg(twr + rr)));
+                                        }
+                                    }
+                                    v[r] = acc;
                                 }
                             }
+                            if (R1 == 16) dft16(v);
+                            else if (R1 == 8) dft8(v);
+                            else if (R1 == 4) dft4(v[0], v[1], v[2], v[3]);
+                            else if (R1 == 2) dft2(v[0], v[1]);
 #pragma unroll
-                            for (int u = 0; u < 4; ++u) {
-                                const int rr = rr0 + u * FUSED_THREADS;
-                                if (rr < (int)N_s) fftb[(offp + rr) & (L - 1)] = cmul(v[u], tw[u]);
-                            }
+                            for (int r = 0; r < 16; ++r)
+                                if (r < R1) hbuf[padi(lt * R1 + r)] = v[r];
                         }
-                    } else {
-                        // folded: several samples per position, summed in index order
-                        for (int pos = tid; pos < L; pos += FUSED_THREADS) {
-                            float2 acc = make_float2(0.f, 0.f);
-                            for (int64_t rr = (pos + off0) % L; rr < N_s; rr += L) {
-                                const int owner = (int)(rr / S);
-                                const float2* sp = slice_ptr(lay, sm, b, Q, X, w) + (rr - (int64_t)owner * S);
-                                const float2 v = CLUSTER ? *cg::this_cluster().map_shared_rank(sp, owner) : *sp;
-                                acc = cadd(acc, cmul(v, __ldg(twr + rr)));
-                            }
-                            fftb[pos] = acc;
-                        }
+                        hsync();
+                        stockham_rest(hbuf, L, p.log2L, R1, lt, p.twL, hsync);
                     }
                     __syncthreads();
-                    const float2* res = fft_stockham(fftb, fftb + L, L, p.log2L, p.twL);
-                    const bool last = (X == Q - 1);
+                    // pair sum for this round's detectors
+                    const bool lastg = (g == nround - 1);
                     for (int i = i0 + tid; i < i1; i += FUSED_THREADS) {
-                        const float2 F = cmul(res[bins[i].x], wseg);
-                        float2 h = X == 0 ? make_float2(0.f, 0.f) : same[w * nb + i];
-                        // window: the R slots other than the current segment's
-                        for (int s = 0; s < (int)R1 && R > 0; ++s) {
-                            if (s == (int)cur) continue;
-                            if (lay.ring_q == 1) {
-                                h = cadd(h, ring[((size_t)s * 2 + w) * nb + i]);
-                            } else {
-                                for (int X2 = 0; X2 < Q; ++X2)
-                                    if (X2 != X) h = cadd(h, ring[(((size_t)s * Q + X2) * 2 + w) * nb + i]);
+                        const int m = bins[i].x;
+                        float2 sacc = g == 0 ? make_float2(0.f, 0.f) : same[i];
+                        float term = 0.f;
+                        for (int hh = 0; hh < 2; ++hh) {
+                            const int Xh = 2 * g + hh;
+                            if (Xh >= Q) break;
+                            const float2 F = cmul(fftb[(size_t)hh * PL + padi(m)], wseg);
+                            float2 hv = sacc;
+                            if (R > 0) {
+                                if (lay.ring_q == 1) {
+                                    for (int sl = 0; sl < (int)R; ++sl) hv = cadd(hv, ring[((size_t)sl * 2 + w) * nb + i]);
+                                } else {
+                                    for (int sl = 0; sl < (int)nslot; ++sl) {
+                                        if (sl == (int)cur) continue;
+                                        for (int X2 = 0; X2 < Q; ++X2)
+                                            if (X2 != Xh) hv = cadd(hv, ring[(((size_t)sl * Q + X2) * 2 + w) * nb + i]);
+                                    }
+                                    ring[(((size_t)cur * Q + Xh) * 2 + w) * nb + i] = F;
+                                }
                             }
+                            float tX = redot(F, hv);
+                            if (p.pair_mode == CC_PAIRS_ALL_ORDERED) tX = fmaf(2.f, tX, redot(F, F));
+                            term += tX;
+                            sacc = cadd(sacc, F);
                         }
-                        float term = redot(F, h);
-                        if (p.pair_mode == CC_PAIRS_ALL_ORDERED) term = fmaf(2.f, term, redot(F, F));
                         if (K >= Ka) kahan_add(rho[i], comp[i], term);
-                        const float2 sn = X == 0 ? F : cadd(same[w * nb + i], F);
-                        same[w * nb + i] = sn;
-                        if (R > 0) {
-                            if (lay.ring_q > 1)
-                                ring[(((size_t)cur * Q + X) * 2 + w) * nb + i] = F;
-                            else if (last)
-                                ring[((size_t)cur * 2 + w) * nb + i] = sn;
-                        }
+                        if (!lastg) same[i] = sacc;
+                        else if (R > 0 && lay.ring_q == 1) ring[((size_t)cur * 2 + w) * nb + i] = sacc;
                     }
                     __syncthreads();
                 }
@@ -369,6 +402,7 @@ bool fused_layout(const cc_plan* plan, int64_t n_t, FusedLayout* lay) {
     lay->nb = std::max(nb, 1);
     lay->nkseg = (int)(p.N_s / KNOT + 5);
     lay->nrec = lay->S / KNOT + 3;
+    lay->invS = 1.0f / (float)lay->S;
     lay->ring_q = p.pair_mode == CC_PAIRS_CROSS_ONLY ? p.Q : 1;
     const int ncos_max = (C + CL - 1) / CL;
     size_t o = 0;
@@ -376,11 +410,12 @@ bool fused_layout(const cc_plan* plan, int64_t n_t, FusedLayout* lay) {
     lay->slice_bytes = (size_t)2 * p.Q * 2 * lay->S * sizeof(float2);
     o = al16(o + lay->slice_bytes);
     lay->off_fft = o;
-    o = al16(o + (size_t)2 * p.L * sizeof(float2));
+    o = al16(o + (size_t)2 * padded_len(p.L) * sizeof(float2));
     lay->off_ring = o;
-    o = al16(o + (size_t)(p.R > 0 ? p.R + 1 : 0) * lay->ring_q * 2 * lay->nb * sizeof(float2));
+    const int64_t nslot = lay->ring_q > 1 ? p.R + 1 : p.R;
+    o = al16(o + (size_t)nslot * lay->ring_q * 2 * lay->nb * sizeof(float2));
     lay->off_same = o;
-    o = al16(o + (size_t)2 * lay->nb * sizeof(float2));
+    o = al16(o + (size_t)lay->nb * sizeof(float2));
     lay->off_rho = o;
     o = al16(o + (size_t)2 * lay->nb * sizeof(float));
     lay->off_dk = o;
@@ -395,6 +430,7 @@ bool fused_layout(const cc_plan* plan, int64_t n_t, FusedLayout* lay) {
     o = al16(o + (size_t)lay->nb * sizeof(int2) + (ncos_max + 1) * sizeof(int));
     lay->bytes = o;
     if (lay->bytes > 227 * 1024) return false;
+    if (p.L > 4096 || p.L < 16) return false;   // one radix-16 butterfly per thread per pass
     if ((int64_t)(p.R + 1) * p.Q > FUSED_THREADS) return false;
     // chunks: enough CTAs to fill the GPU, each chunk at least 4R + 1 segments
     int64_t ctas = (int64_t)C / (C / CL) * n_t;   // = CL * n_t clusters' CTAs
