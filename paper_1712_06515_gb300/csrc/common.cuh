@@ -67,12 +67,12 @@ constexpr int MAX_CLUSTER = 8;
 // Shared-memory layout and work split of the fused kernel (byte offsets).
 struct FusedLayout {
     int CL;            // CTAs per cluster, sharing each segment
-    int S;             // samples per CTA slice, ceil(N_s / CL)
+    int S;             // local samples per CTA: its KNOT-sample blocks (block q -> CTA q mod CL)
     int nb;            // max output bins held by one CTA
     int nkseg;         // max knots per segment (incl. the cubic's neighbours)
-    int nrec;          // max knot records per slice
+    int nrec;          // knot records per CTA: two per owned block
     int ring_q;        // detectors kept per ring slot (1: summed; Q: cross-only mode)
-    float invS;        // 1 / S
+    int log2CL;        // CL is a power of two
     int64_t chunk_len; // segments per chunk
     int n_chunks;
     size_t off_slice, slice_bytes;   // [2][Q][2][S] float2
@@ -146,6 +146,11 @@ __device__ __forceinline__ void kahan_add(float& sum, float& comp, float v) {
 __host__ __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
 __host__ __device__ __forceinline__ int64_t imax64(int64_t a, int64_t b) { return a > b ? a : b; }
 
+__device__ __forceinline__ int floor_div32(int a, int b) {
+    int q = a / b;
+    return (q * b > a) ? q - 1 : q;
+}
+
 __device__ __forceinline__ int64_t floor_div(int64_t a, int64_t b) {
     int64_t q = a / b;
     return (q * b > a) ? q - 1 : q;
@@ -218,13 +223,13 @@ __device__ __forceinline__ KnotRec make_knot(const DevParams& p, double dm1, dou
 // Per-sample timing from the knot record: stencil centre j*, offset delta in
 // [-1/2, 1/2) and heterodyne + f_r* phase (cycles, reduced to [-1/2, 1/2)).
 struct SampleTiming {
-    int64_t jstar;
+    int jstar;      // sample index of the stencil centre (series fit in 32-bit indices)
     float delta;
     float psi;
 };
 
 __device__ __forceinline__ SampleTiming sample_timing(const DevParams& p, const KnotRec& kr,
-                                                      int64_t r, int64_t rk) {
+                                                      int r, int rk) {
     float h = (float)(r - rk) * (1.0f / KNOT);
     float hm1 = h - 1.0f, hm2 = h - 2.0f, hp1 = h + 1.0f;
     float Lm1 = -h * hm1 * hm2 * (1.0f / 6.0f);
@@ -235,7 +240,7 @@ __device__ __forceinline__ SampleTiming sample_timing(const DevParams& p, const 
     float g = 0.5f - v;
     float fl = floorf(g);
     SampleTiming s;
-    s.jstar = r - (int64_t)kr.N + (int64_t)fl;
+    s.jstar = r - kr.N + (int)fl;
     s.delta = (g - 0.5f) - fl;
     float psi = kr.psi - p.f_h_dt * pp - p.f_r_dt * (float)(r - rk);
     s.psi = psi - rintf(psi);
@@ -244,23 +249,34 @@ __device__ __forceinline__ SampleTiming sample_timing(const DevParams& p, const 
 
 // Windowed-sinc interpolation (2D+1 taps) at t/dt = j* + delta of a complex series.
 __device__ __forceinline__ float2 interp_sinc(const DevParams& p, const float2* __restrict__ x,
-                                              int64_t jstar, float delta) {
-    const int64_t N = p.N_t;
+                                              int jstar, float delta) {
+    const int N = (int)p.N_t;
     if (delta == 0.0f) {
         return (jstar >= 0 && jstar < N) ? __ldg(x + jstar) : make_float2(0.f, 0.f);
     }
     const int D = p.D;
     float s = sinpif(delta) * 0.318309886183790672f;   // sin(pi delta)/pi
     float2 acc = make_float2(0.f, 0.f);
-    int64_t j0 = jstar - D;
-    for (int n = 0; n <= 2 * D; ++n) {
-        int64_t j = j0 + n;
-        if (j < 0 || j >= N) continue;
-        float dj = delta - (float)(n - D);              // (t - t_j)/dt
-        float c = p.ham[n] * __fdividef(((n - D) & 1) ? -s : s, dj);
-        float2 xv = __ldg(x + j);
-        acc.x = fmaf(c, xv.x, acc.x);
-        acc.y = fmaf(c, xv.y, acc.y);
+    const int j0 = jstar - D;
+    const float2* __restrict__ xp = x + j0;
+    if (j0 >= 0 && j0 + 2 * D < N) {
+        for (int n = 0; n <= 2 * D; ++n) {
+            float dj = delta - (float)(n - D);              // (t - t_j)/dt
+            float c = p.ham[n] * __fdividef(((n - D) & 1) ? -s : s, dj);
+            float2 xv = __ldg(xp + n);
+            acc.x = fmaf(c, xv.x, acc.x);
+            acc.y = fmaf(c, xv.y, acc.y);
+        }
+    } else {
+        for (int n = 0; n <= 2 * D; ++n) {
+            const int j = j0 + n;
+            if (j < 0 || j >= N) continue;
+            float dj = delta - (float)(n - D);
+            float c = p.ham[n] * __fdividef(((n - D) & 1) ? -s : s, dj);
+            float2 xv = __ldg(x + j);
+            acc.x = fmaf(c, xv.x, acc.x);
+            acc.y = fmaf(c, xv.y, acc.y);
+        }
     }
     return acc;
 }
@@ -271,26 +287,26 @@ struct SampleWeights {
     float alpha, beta, s2;
 };
 
-__device__ __forceinline__ SampleWeights sample_weights(const DevParams& p, int X, int64_t jstar,
+__device__ __forceinline__ SampleWeights sample_weights(const DevParams& p, int X, int jstar,
                                                         float delta) {
     SampleWeights w{0.f, 0.f, 0.f};
-    int64_t q = floor_div(jstar, p.nsft);
-    int64_t rem = jstar - q * p.nsft;
-    int64_t blk = (rem == 0 && delta < 0.f) ? q - 1 : q;
-    if (blk < 0 || blk >= p.n_sig[X]) return w;
-    float s2 = __ldg(p.sig2[X] + blk);
+    const int q = floor_div32(jstar, p.nsft);
+    const int rem = jstar - q * p.nsft;
+    const int blk = (rem == 0 && delta < 0.f) ? q - 1 : q;
+    if (blk < 0 || blk >= (int)p.n_sig[X]) return w;
+    const float s2 = __ldg(p.sig2[X] + blk);
     if (!(s2 > 0.f)) return w;
-    int64_t ja = jstar - p.ab_j0;
-    int64_t ia = floor_div(ja, p.n_ab_step);
-    int64_t nab = p.n_ab[X];
-    int64_t ic = ia < 0 ? 0 : (ia > nab - 2 ? nab - 2 : ia);
+    const int ja = jstar - (int)p.ab_j0;
+    const int ia = floor_div32(ja, p.n_ab_step);
+    const int nab = (int)p.n_ab[X];
+    const int ic = ia < 0 ? 0 : (ia > nab - 2 ? nab - 2 : ia);
     // the linear interpolant is continuous, so the interval chosen at a node does not matter
-    float fr = ((float)(ja - ic * p.n_ab_step) + delta) / (float)p.n_ab_step;
-    float a0 = __ldg(p.atab[X] + ic), a1 = __ldg(p.atab[X] + ic + 1);
-    float b0 = __ldg(p.btab[X] + ic), b1 = __ldg(p.btab[X] + ic + 1);
-    float a = fmaf(fr, a1 - a0, a0);
-    float b = fmaf(fr, b1 - b0, b0);
-    float inv = 1.0f / s2;
+    const float fr = ((float)(ja - ic * p.n_ab_step) + delta) / (float)p.n_ab_step;
+    const float a0 = __ldg(p.atab[X] + ic), a1 = __ldg(p.atab[X] + ic + 1);
+    const float b0 = __ldg(p.btab[X] + ic), b1 = __ldg(p.btab[X] + ic + 1);
+    const float a = fmaf(fr, a1 - a0, a0);
+    const float b = fmaf(fr, b1 - b0, b0);
+    const float inv = 1.0f / s2;
     w.alpha = a * inv;
     w.beta = b * inv;
     w.s2 = s2;

@@ -35,6 +35,8 @@ __device__ __forceinline__ const float2* slice_ptr(const FusedLayout& lay, unsig
     return (const float2*)(base + lay.off_slice) + (((size_t)buf * Q + X) * 2 + w) * lay.S;
 }
 
+static_assert(KNOT == 128, "slice blocks and knot indices use shifts by 7");
+
 // barrier of one 256-thread half of the CTA (named barrier 1 or 2)
 struct HalfSync {
     int id;
@@ -52,7 +54,7 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
     const int rank = CLUSTER ? (int)cg::this_cluster().block_rank() : 0;
     const int chunk = blockIdx.y;
     const int64_t t = t_base + blockIdx.z;
-    const int Q = p.Q, L = p.L, S = lay.S, nb = lay.nb;
+    const int Q = p.Q, L = p.L, nb = lay.nb;
     const int64_t N_s = p.N_s, R = p.R;
     const int64_t Ka = (int64_t)chunk * lay.chunk_len;
     const int64_t Kb = imin64(p.M, Ka + lay.chunk_len);
@@ -127,21 +129,26 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
         }
         return *b;
     };
-    // knot records of this CTA's slice of segment K from the cluster's knot delays
+    // Slices are dealt in blocks of KNOT samples: segment-local block q belongs to CTA
+    // q mod CL and sits at local block q / CL.  A block spans at most two knots.
+    const int nblk = (int)((N_s + KNOT - 1) / KNOT);
+    const int nmyb = (nblk - rank + CL - 1) / CL;
+    // knot records of this CTA's blocks of segment K from the cluster's knot delays
     auto build_records = [&](int64_t K, int buf) {
         int64_t kA;
         knot_range(K, &kA);
-        const int64_t s0 = K * N_s + (int64_t)rank * S;
-        const int64_t s1 = imin64(K * N_s + N_s, s0 + S);
-        if (s1 <= s0) return;
-        const int64_t kr0 = floor_div(s0, KNOT), kr1 = floor_div(s1 - 1, KNOT);
-        const int n = (int)(kr1 - kr0 + 1);
-        for (int j = tid; j < n * Q; j += FUSED_THREADS) {
-            const int X = j / n, jj = j % n;
-            const int i = (int)(kr0 + jj - kA);
+        const int64_t seg0 = K * N_s, seg1 = seg0 + N_s;
+        for (int j = tid; j < 2 * nmyb * Q; j += FUSED_THREADS) {
+            const int X = j / (2 * nmyb), jj = j % (2 * nmyb);
+            const int qi = jj >> 1, e = jj & 1;
+            const int64_t r0 = seg0 + (int64_t)(qi * CL + rank) * KNOT;
+            const int64_t r1 = imin64(r0 + KNOT, seg1);
+            const int64_t k = (r0 >> 7) + e;
+            if (k > ((r1 - 1) >> 7)) continue;
+            const int i = (int)(k - kA);
             recb[((size_t)buf * Q + X) * lay.nrec + jj] =
                 make_knot(p, remote_dk(buf, X, i - 1), remote_dk(buf, X, i), remote_dk(buf, X, i + 1),
-                          remote_dk(buf, X, i + 2), (double)((kr0 + jj) * KNOT) * p.dt);
+                          remote_dk(buf, X, i + 2), (double)(k * KNOT) * p.dt);
         }
     };
     auto cluster_sync = [&]() {
@@ -162,28 +169,31 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
         const int64_t seg0 = K * N_s;
         // (1) knot delays of the next segment (FP64, a few threads)
         if (K + 1 < Kb) compute_knots(K + 1, b ^ 1);
-        // (2) resample this CTA's slice of segment K for every detector
+        // (2) resample this CTA's blocks of segment K for every detector
         {
-            const int64_t s0 = seg0 + (int64_t)rank * S;
-            const int64_t s1 = imin64(seg0 + N_s, s0 + S);
-            const int64_t kr0 = floor_div(s0, KNOT);
+            const int nloc = nmyb * KNOT;
             for (int X = 0; X < Q; ++X) {
                 float A = 0.f, B = 0.f, Cn = 0.f;
                 const float2* __restrict__ x = p.x[X];
                 float2* sa = (float2*)slice_ptr(lay, sm, b, Q, X, 0);
                 float2* sb = (float2*)slice_ptr(lay, sm, b, Q, X, 1);
                 const KnotRec* rec = recb + ((size_t)b * Q + X) * lay.nrec;
-                for (int64_t r = s0 + tid; r < s1; r += FUSED_THREADS) {
-                    const int64_t k = r / KNOT;
-                    const KnotRec kr = rec[k - kr0];
+                for (int li = tid; li < nloc; li += FUSED_THREADS) {
+                    const int qi = li >> 7;
+                    const int rr = (qi * CL + rank) * KNOT + (li & (KNOT - 1));
+                    if (rr >= (int)N_s) continue;
+                    const int r = (int)seg0 + rr;
+                    const int k = r >> 7;
+                    const int r0 = (int)seg0 + (qi * CL + rank) * KNOT;
+                    const KnotRec kr = rec[2 * qi + (k - (r0 >> 7))];
                     const SampleTiming st = sample_timing(p, kr, r, k * KNOT);
                     const float2 xv = interp_sinc(p, x, st.jstar, st.delta);
                     float sn, cs;
                     sincospif(2.0f * st.psi, &sn, &cs);
                     const float2 xr = cmul(xv, make_float2(cs, sn));
                     const SampleWeights wt = sample_weights(p, X, st.jstar, st.delta);
-                    sa[r - s0] = cscale(xr, wt.alpha);
-                    sb[r - s0] = cscale(xr, wt.beta);
+                    sa[li] = cscale(xr, wt.alpha);
+                    sb[li] = cscale(xr, wt.beta);
                     A = fmaf(wt.alpha * wt.alpha, wt.s2, A);
                     B = fmaf(wt.beta * wt.beta, wt.s2, B);
                     Cn = fmaf(wt.alpha * wt.beta, wt.s2, Cn);
@@ -284,10 +294,9 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
                                     vv[r] = tw[r] = make_float2(0.f, 0.f);
                                     const int rr = (lt + r * B1 + offn) & (L - 1);
                                     if (r < R1 && rr < (int)N_s) {
-                                        int owner = (int)((float)rr * lay.invS);
-                                        owner -= (owner * S > rr);
-                                        owner += ((owner + 1) * S <= rr);
-                                        const float2* sp = sbase + (rr - owner * S);
+                                        const int q = rr >> 7;
+                                        const int owner = q & (CL - 1);
+                                        const float2* sp = sbase + (((q >> lay.log2CL) << 7) | (rr & (KNOT - 1)));
                                         vv[r] = CLUSTER ? *cg::this_cluster().map_shared_rank(sp, owner) : *sp;
                                         tw[r] = __ldg(twr + rr);
                                     }
@@ -299,9 +308,10 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
                                 for (int r = 0; r < 16; ++r) {
                                     float2 acc = make_float2(0.f, 0.f);
                                     if (r < R1) {
-                                        for (int64_t rr = (lt + r * B1 + offn) & (L - 1); rr < N_s; rr += L) {
-                                            const int owner = (int)(rr / S);
-                                            const float2* sp = sbase + (rr - (int64_t)owner * S);
+                                        for (int rr = (lt + r * B1 + offn) & (L - 1); rr < (int)N_s; rr += L) {
+                                            const int q = rr >> 7;
+                                            const int owner = q & (CL - 1);
+                                            const float2* sp = sbase + (((q >> lay.log2CL) << 7) | (rr & (KNOT - 1)));
                                             const float2 vr = CLUSTER ? *cg::this_cluster().map_shared_rank(sp, owner) : *sp;
                                             acc = cadd(acc, cmul(vr, __ldg(twr + rr)));
                                         }
@@ -390,7 +400,10 @@ bool fused_layout(const cc_plan* plan, int64_t n_t, FusedLayout* lay) {
     while (CL * 2 <= std::min(C, MAX_CLUSTER)) CL *= 2;
     if (C % CL) return false;
     lay->CL = CL;
-    lay->S = (int)((p.N_s + CL - 1) / CL);
+    const int nblk = (int)((p.N_s + KNOT - 1) / KNOT);
+    lay->S = ((nblk + CL - 1) / CL) * KNOT;   // local samples: this CTA's KNOT-sample blocks
+    lay->log2CL = 0;
+    while ((1 << lay->log2CL) < CL) ++lay->log2CL;
     // bins per CTA: max over ranks of the sum of its cosets' list lengths
     int nb = 0;
     const std::vector<int>& off = plan->coset_off;
@@ -401,8 +414,7 @@ bool fused_layout(const cc_plan* plan, int64_t n_t, FusedLayout* lay) {
     }
     lay->nb = std::max(nb, 1);
     lay->nkseg = (int)(p.N_s / KNOT + 5);
-    lay->nrec = lay->S / KNOT + 3;
-    lay->invS = 1.0f / (float)lay->S;
+    lay->nrec = 2 * ((nblk + CL - 1) / CL);
     lay->ring_q = p.pair_mode == CC_PAIRS_CROSS_ONLY ? p.Q : 1;
     const int ncos_max = (C + CL - 1) / CL;
     size_t o = 0;

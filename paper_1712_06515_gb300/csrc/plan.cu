@@ -118,7 +118,8 @@ cc_status crosscorr_plan(const cc_config* cfg, const cc_detector* dets, cc_plan*
     if (c.n_det < 1 || c.n_det > CC_MAX_DET) return fail(CC_ERR_INVALID, "n_det must be 1..4");
     if (c.D < 1 || c.D > cc::MAX_D) return fail(CC_ERR_INVALID, "D must be 1..32");
     if (!(c.dt > 0) || !isfinite(c.dt)) return fail(CC_ERR_INVALID, "dt must be positive");
-    if (c.n_samples < 1) return fail(CC_ERR_INVALID, "n_samples must be positive");
+    if (c.n_samples < 1 || c.n_samples > (int64_t(1) << 30))
+        return fail(CC_ERR_INVALID, "n_samples must be in [1, 2^30]");
     if (!(c.f_band > 0) || c.f_band > 1.0 / c.dt + 1e-12)
         return fail(CC_ERR_INVALID, "f_band must be in (0, 1/dt]");
     if (!(c.mu_f > 0) || !isfinite(c.mu_f)) return fail(CC_ERR_INVALID, "mu_f must be positive");

@@ -84,7 +84,7 @@ resample_kernel(DevParams p, const cc_template* __restrict__ tm, int64_t t_base,
         const int64_t r = seg0 + i;
         const int64_t k = r / KNOT;
         const KnotRec kr = rec[k - kA];
-        const SampleTiming st = sample_timing(p, kr, r, k * KNOT);
+        const SampleTiming st = sample_timing(p, kr, (int)r, (int)(k * KNOT));
         const float2 xv = interp_sinc(p, x, st.jstar, st.delta);
         float sn, cs;
         sincospif(2.0f * st.psi, &sn, &cs);
