@@ -183,6 +183,25 @@ cc_status crosscorr_pair_accumulate(cc_plan* plan, const void* F_dev, const floa
 cc_status crosscorr_search(cc_plan* plan, const void* const* x_dev, const cc_template* t_dev,
                            int64_t n_t, float* rho_dev, void* stream);
 
+/* crosscorr_search for callers that cannot allocate device memory while searching:
+ * for example a service that hands all device memory to its own pool at start-up and
+ * forbids later cudaMalloc/cudaFree (which may also synchronise the device and stall
+ * its other streams).  The paper has no counterpart; this is an engineering variant.
+ * Same inputs, output and result as crosscorr_search; it never allocates.  Its only
+ * scratch (one double per template) is a fixed 512 KiB array compiled into the library,
+ * which every GPU that loads the library holds until the process exits:
+ *   - n_t may be at most 65536 (CC_ERR_INVALID above that; split the batch);
+ *   - plans that need the staged path (BF16 storage, very long segments) return
+ *     CC_ERR_UNSUPPORTED;
+ *   - the first call on a device looks up the array's device address with that device
+ *     current, so make that first call before any stream capture;
+ *   - every call shares the array and it keeps the last call's contents; each call
+ *     overwrites the entries it uses before reading them, so nothing needs clearing,
+ *     but calls that overlap on the GPU (other streams, other host threads) race on it
+ *     and must be serialised by the caller. */
+cc_status crosscorr_search_noalloc(cc_plan* plan, const void* const* x_dev, const cc_template* t_dev,
+                                   int64_t n_t, float* rho_dev, void* stream);
+
 /* The k largest rho over (template, bin) of a device float[n_t][N_f] array,
  * descending, ties by (template, bin) ascending; hits_host receives
  * min(k, n_t*N_f) records.  Synchronises the stream.  1 <= k <= 4096. */

@@ -20,7 +20,7 @@ BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "lib")
 LIBPATH = os.path.join(LIBDIR, "libcrosscorr.so")
 
-SOURCES = ["plan.cu", "stages.cu", "search.cu", "topk.cu", "fused.cu"]
+SOURCES = ["plan.cu", "stages.cu", "search.cu", "topk.cu", "fused.cu", "noalloc.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 
@@ -112,6 +112,8 @@ SIGNATURES = {
     "crosscorr_segment_fft": (c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
     "crosscorr_pair_accumulate": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
     "crosscorr_search": (c_int, [c_void_p, POINTER(c_void_p), c_void_p, c_int64, c_void_p, c_void_p]),
+    "crosscorr_search_noalloc": (c_int, [c_void_p, POINTER(c_void_p), c_void_p, c_int64, c_void_p,
+                                         c_void_p]),
     "crosscorr_rho_topk": (c_int, [c_void_p, c_void_p, c_int64, c_int, POINTER(CcHit), c_void_p]),
     "crosscorr_plan_destroy": (None, [c_void_p]),
     "crosscorr_status_string": (ctypes.c_char_p, [c_int]),
