@@ -119,7 +119,9 @@ cc_status ensure_workspace(cc_plan* p, size_t bytes);
 int launch_blocks_for(int64_t n, int threads);
 bool fused_layout(const cc_plan* plan, int64_t n_t, FusedLayout* lay);
 cc_status launch_fused(cc_plan* plan, const cc_template* t_dev, int64_t n_t, float* rho,
-                       const FusedLayout& lay, float* raw, double* dpart, cudaStream_t st);
+                       const FusedLayout& lay, float* raw, double* dpart, cudaStream_t st,
+                       KnotRec* kn_ws = nullptr, int64_t kn_batch = 0);
+int64_t knot_rows(const cc_plan* plan);
 void count_launch(uint64_t n = 1);
 
 // ---------------------------------------------------------------------------
@@ -217,6 +219,20 @@ __device__ __forceinline__ KnotRec make_knot(const DevParams& p, double dm1, dou
     double c = -p.f_h * d0 - p.f_r * tau_k;
     r.psi = (float)(c - floor(c));
     r.pad0 = r.pad1 = 0.f;
+    return r;
+}
+
+__device__ __forceinline__ KnotRec load_knot(const KnotRec* q) {
+    const float4 a = __ldg((const float4*)q), b = __ldg((const float4*)q + 1);
+    KnotRec r;
+    r.N = __float_as_int(a.x);
+    r.f = a.y;
+    r.psi = a.z;
+    r.dm1 = a.w;
+    r.dp1 = b.x;
+    r.dp2 = b.y;
+    r.pad0 = b.z;
+    r.pad1 = b.w;
     return r;
 }
 

@@ -177,3 +177,46 @@ __device__ __forceinline__ void stockham_rest(float2* buf, int L, int log2L, int
 }
 
 }  // namespace cc
+
+namespace cc {
+
+__host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x >> 1); }
+
+// Compile-time-L versions: constant strides and masks throughout.
+template <int R, int L, int NS, typename Sync>
+__device__ __forceinline__ void stockham_pass_t(float2* buf, int j, const float2* __restrict__ twL, Sync sync) {
+    constexpr int B = L / R;
+    float2 v[16];
+    const bool act = j < B;
+    const int k = j & (NS - 1);
+    if (act) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = buf[padi(j + r * B)];
+        if constexpr (NS > 1) apply_twiddles<R>(v, twL, k * (L / (NS * R)), L - 1);
+        dft_r<R>(v);
+    }
+    sync();
+    if (act) {
+        const int idxD = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[padi(idxD + r * NS)] = v[r];
+    }
+    sync();
+}
+
+template <int L, int NS, typename Sync>
+__device__ __forceinline__ void stockham_rest_t(float2* buf, int j, const float2* __restrict__ twL, Sync sync) {
+    constexpr int rem = ilog2c(L) - ilog2c(NS);
+    if constexpr (rem >= 4) {
+        stockham_pass_t<16, L, NS>(buf, j, twL, sync);
+        stockham_rest_t<L, NS * 16>(buf, j, twL, sync);
+    } else if constexpr (rem == 3) {
+        stockham_pass_t<8, L, NS>(buf, j, twL, sync);
+    } else if constexpr (rem == 2) {
+        stockham_pass_t<4, L, NS>(buf, j, twL, sync);
+    } else if constexpr (rem == 1) {
+        stockham_pass_t<2, L, NS>(buf, j, twL, sync);
+    }
+}
+
+}  // namespace cc

@@ -45,16 +45,21 @@ struct HalfSync {
     }
 };
 
-template <bool CLUSTER>
+// LT: coset transform length (compile-time); PREKNOTS: knot records come from the
+// pre-pass (global memory) instead of being computed and exchanged in the cluster.
+template <int LT, bool PREKNOTS>
 __global__ void __launch_bounds__(FUSED_THREADS, 1)
 fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, int64_t t_base,
-             float* __restrict__ raw_out, double* __restrict__ dpart_out) {
+             float* __restrict__ raw_out, double* __restrict__ dpart_out,
+             const KnotRec* __restrict__ kn, int64_t nkn) {
     extern __shared__ __align__(16) unsigned char sm[];
+    static_assert(LT >= 64 && LT <= 4096, "coset length");
+    constexpr int L = LT;
     const int CL = lay.CL;
-    const int rank = CLUSTER ? (int)cg::this_cluster().block_rank() : 0;
+    const int rank = (int)cg::this_cluster().block_rank();
     const int chunk = blockIdx.y;
     const int64_t t = t_base + blockIdx.z;
-    const int Q = p.Q, L = p.L, nb = lay.nb;
+    const int Q = p.Q, nb = lay.nb;
     const int64_t N_s = p.N_s, R = p.R;
     const int64_t Ka = (int64_t)chunk * lay.chunk_len;
     const int64_t Kb = imin64(p.M, Ka + lay.chunk_len);
@@ -123,11 +128,7 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
     };
     auto remote_dk = [&](int buf, int X, int i) -> double {
         const double* b = dkb + ((size_t)buf * Q + X) * lay.nkseg + i;
-        if (CLUSTER) {
-            cg::cluster_group cl = cg::this_cluster();
-            return *cl.map_shared_rank(b, i % CL);
-        }
-        return *b;
+        return *cg::this_cluster().map_shared_rank(b, i % CL);
     };
     // Slices are dealt in blocks of KNOT samples: segment-local block q belongs to CTA
     // q mod CL and sits at local block q / CL.  A block spans at most two knots.
@@ -151,24 +152,22 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
                           remote_dk(buf, X, i + 2), (double)(k * KNOT) * p.dt);
         }
     };
-    auto cluster_sync = [&]() {
-        if (CLUSTER)
-            cg::this_cluster().sync();
-        else
-            __syncthreads();
-    };
+    auto cluster_sync = [&]() { cg::this_cluster().sync(); };
 
     // prologue: knots and records of the first segment
-    compute_knots(Kl, 0);
-    cluster_sync();
-    build_records(Kl, 0);
-    __syncthreads();
+    if constexpr (!PREKNOTS) {
+        compute_knots(Kl, 0);
+        cluster_sync();
+        build_records(Kl, 0);
+        __syncthreads();
+    }
 
     for (int64_t K = Kl; K < Kb; ++K) {
         const int b = (int)((K - Kl) & 1);
         const int64_t seg0 = K * N_s;
         // (1) knot delays of the next segment (FP64, a few threads)
-        if (K + 1 < Kb) compute_knots(K + 1, b ^ 1);
+        if constexpr (!PREKNOTS)
+            if (K + 1 < Kb) compute_knots(K + 1, b ^ 1);
         // (2) resample this CTA's blocks of segment K for every detector
         {
             const int nloc = nmyb * KNOT;
@@ -178,14 +177,20 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
                 float2* sa = (float2*)slice_ptr(lay, sm, b, Q, X, 0);
                 float2* sb = (float2*)slice_ptr(lay, sm, b, Q, X, 1);
                 const KnotRec* rec = recb + ((size_t)b * Q + X) * lay.nrec;
+                const KnotRec* __restrict__ knX = kn + ((size_t)blockIdx.z * Q + X) * nkn;
                 for (int li = tid; li < nloc; li += FUSED_THREADS) {
                     const int qi = li >> 7;
                     const int rr = (qi * CL + rank) * KNOT + (li & (KNOT - 1));
                     if (rr >= (int)N_s) continue;
                     const int r = (int)seg0 + rr;
                     const int k = r >> 7;
-                    const int r0 = (int)seg0 + (qi * CL + rank) * KNOT;
-                    const KnotRec kr = rec[2 * qi + (k - (r0 >> 7))];
+                    KnotRec kr;
+                    if constexpr (PREKNOTS) {
+                        kr = load_knot(knX + k);
+                    } else {
+                        const int r0 = (int)seg0 + (qi * CL + rank) * KNOT;
+                        kr = rec[2 * qi + (k - (r0 >> 7))];
+                    }
                     const SampleTiming st = sample_timing(p, kr, r, k * KNOT);
                     const float2 xv = interp_sinc(p, x, st.jstar, st.delta);
                     float sn, cs;
@@ -213,7 +218,8 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
         }
         cluster_sync();
         // (3) knot records of the next segment's slice
-        if (K + 1 < Kb) build_records(K + 1, b ^ 1);
+        if constexpr (!PREKNOTS)
+            if (K + 1 < Kb) build_records(K + 1, b ^ 1);
         // (4) segment norms and the normalisation (rank 0 holds D): one thread per
         //     (peer, detector, component) sums that peer's warp partials
         if (rank == 0) {
@@ -221,7 +227,7 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
             if (tid < CL * Q * 3) {
                 const int rr = tid / (Q * 3), X = (tid / 3) % Q, i = tid % 3;
                 const float* wp = wpart + (size_t)b * FUSED_WARPS * Q * 4;
-                if (CLUSTER) wp = cg::this_cluster().map_shared_rank(wp, rr);
+                wp = cg::this_cluster().map_shared_rank(wp, rr);
                 float v[FUSED_WARPS];
 #pragma unroll
                 for (int wv = 0; wv < FUSED_WARPS; ++wv) v[wv] = wp[(wv * Q + X) * 4 + i];
@@ -268,8 +274,8 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
         const HalfSync hsync{1 + half};
         const int PL = padded_len(L);
         float2* hbuf = fftb + (size_t)half * PL;
-        const int R1 = L >= 16 ? 16 : L;      // radix of the first pass
-        const int B1 = L / R1;
+        constexpr int R1 = 16;                // radix of the first pass
+        constexpr int B1 = L / R1;
         const int offn = (int)((-seg0) & (int64_t)(L - 1));   // position p holds r - seg0 = (p + offn) mod L
         const int64_t cur = R > 0 ? K % nslot : 0;
         const int nround = (Q + 1) / 2;
@@ -293,11 +299,11 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
                                 for (int r = 0; r < 16; ++r) {
                                     vv[r] = tw[r] = make_float2(0.f, 0.f);
                                     const int rr = (lt + r * B1 + offn) & (L - 1);
-                                    if (r < R1 && rr < (int)N_s) {
+                                    if (rr < (int)N_s) {
                                         const int q = rr >> 7;
                                         const int owner = q & (CL - 1);
                                         const float2* sp = sbase + (((q >> lay.log2CL) << 7) | (rr & (KNOT - 1)));
-                                        vv[r] = CLUSTER ? *cg::this_cluster().map_shared_rank(sp, owner) : *sp;
+                                        vv[r] = *cg::this_cluster().map_shared_rank(sp, owner);
                                         tw[r] = __ldg(twr + rr);
                                     }
                                 }
@@ -307,28 +313,24 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
 #pragma unroll
                                 for (int r = 0; r < 16; ++r) {
                                     float2 acc = make_float2(0.f, 0.f);
-                                    if (r < R1) {
+                                    {
                                         for (int rr = (lt + r * B1 + offn) & (L - 1); rr < (int)N_s; rr += L) {
                                             const int q = rr >> 7;
                                             const int owner = q & (CL - 1);
                                             const float2* sp = sbase + (((q >> lay.log2CL) << 7) | (rr & (KNOT - 1)));
-                                            const float2 vr = CLUSTER ? *cg::this_cluster().map_shared_rank(sp, owner) : *sp;
+                                            const float2 vr = *cg::this_cluster().map_shared_rank(sp, owner);
                                             acc = cadd(acc, cmul(vr, __ldg(twr + rr)));
                                         }
                                     }
                                     v[r] = acc;
                                 }
                             }
-                            if (R1 == 16) dft16(v);
-                            else if (R1 == 8) dft8(v);
-                            else if (R1 == 4) dft4(v[0], v[1], v[2], v[3]);
-                            else if (R1 == 2) dft2(v[0], v[1]);
+                            dft16(v);
 #pragma unroll
-                            for (int r = 0; r < 16; ++r)
-                                if (r < R1) hbuf[padi(lt * R1 + r)] = v[r];
+                            for (int r = 0; r < 16; ++r) hbuf[padi(lt * R1 + r)] = v[r];
                         }
                         hsync();
-                        stockham_rest(hbuf, L, p.log2L, R1, lt, p.twL, hsync);
+                        stockham_rest_t<L, 16>(hbuf, lt, p.twL, hsync);
                     }
                     __syncthreads();
                     // pair sum for this round's detectors
@@ -442,7 +444,7 @@ bool fused_layout(const cc_plan* plan, int64_t n_t, FusedLayout* lay) {
     o = al16(o + (size_t)lay->nb * sizeof(int2) + (ncos_max + 1) * sizeof(int));
     lay->bytes = o;
     if (lay->bytes > 227 * 1024) return false;
-    if (p.L > 4096 || p.L < 16) return false;   // one radix-16 butterfly per thread per pass
+    if (p.L > 4096 || p.L < 64) return false;   // one radix-16 butterfly per thread per pass
     if ((int64_t)(p.R + 1) * p.Q > FUSED_THREADS) return false;
     // chunks: enough CTAs to fill the GPU, each chunk at least 4R + 1 segments
     int64_t ctas = (int64_t)C / (C / CL) * n_t;   // = CL * n_t clusters' CTAs
@@ -454,16 +456,85 @@ bool fused_layout(const cc_plan* plan, int64_t n_t, FusedLayout* lay) {
     return true;
 }
 
+// Knot records (FP64 delays at every KNOT-th source sample, four per record) for a batch
+// of templates: one thread per record, the block's 256 records plus three halo knots.
+__global__ void __launch_bounds__(256)
+knots_kernel(DevParams p, const cc_template* __restrict__ tm, int64_t t_base, int64_t nkn,
+             KnotRec* __restrict__ out) {
+    __shared__ double dk[256 + 3];
+    const int X = blockIdx.y;
+    const int64_t tl = blockIdx.z, t = t_base + tl;
+    const int64_t k0 = (int64_t)blockIdx.x * 256;
+    const cc_template T = tm[t];
+    const double tasc_rel = T.T_asc - p.t0, invP = 1.0 / T.P;
+    for (int i = threadIdx.x; i < 256 + 3; i += 256)
+        dk[i] = knot_delay(p, X, T.a_p, tasc_rel, invP, (double)((k0 - 1 + i) * KNOT) * p.dt);
+    __syncthreads();
+    const int64_t k = k0 + threadIdx.x;
+    if (k < nkn)
+        out[((size_t)tl * p.Q + X) * nkn + k] =
+            make_knot(p, dk[threadIdx.x], dk[threadIdx.x + 1], dk[threadIdx.x + 2], dk[threadIdx.x + 3],
+                      (double)(k * KNOT) * p.dt);
+}
+
+int64_t knot_rows(const cc_plan* plan) { return (plan->N_tau + KNOT - 1) / KNOT; }
+
+template <int LT>
+static const void* kernel_for(bool pre) {
+    return pre ? (const void*)fused_kernel<LT, true> : (const void*)fused_kernel<LT, false>;
+}
+
+template <int LT>
+static cudaError_t launch_lt(const cudaLaunchConfig_t& cfg, bool pre, const DevParams& p, const FusedLayout& lay,
+                             const cc_template* t_dev, int64_t tb, float* raw, double* dpart, const KnotRec* kn,
+                             int64_t nkn) {
+    if (pre) return cudaLaunchKernelEx(&cfg, fused_kernel<LT, true>, p, lay, t_dev, tb, raw, dpart, kn, nkn);
+    return cudaLaunchKernelEx(&cfg, fused_kernel<LT, false>, p, lay, t_dev, tb, raw, dpart, kn, nkn);
+}
+
+#define CC_FOR_EACH_L(X) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096)
+
+static const void* kernel_ptr(int L, bool pre) {
+    switch (L) {
+#define CC_CASE(LV) case LV: return kernel_for<LV>(pre);
+        CC_FOR_EACH_L(CC_CASE)
+#undef CC_CASE
+    }
+    return nullptr;
+}
+
+static cudaError_t launch_dispatch(int L, const cudaLaunchConfig_t& cfg, bool pre, const DevParams& p,
+                                   const FusedLayout& lay, const cc_template* t_dev, int64_t tb, float* raw,
+                                   double* dpart, const KnotRec* kn, int64_t nkn) {
+    switch (L) {
+#define CC_CASE(LV) case LV: return launch_lt<LV>(cfg, pre, p, lay, t_dev, tb, raw, dpart, kn, nkn);
+        CC_FOR_EACH_L(CC_CASE)
+#undef CC_CASE
+    }
+    return cudaErrorInvalidValue;
+}
+
+// kn_ws != nullptr: knot records from the pre-pass, kn_batch templates at a time (the
+// workspace holds kn_batch * Q * knot_rows records); otherwise knots are computed in
+// the fused kernel.
 cc_status launch_fused(cc_plan* plan, const cc_template* t_dev, int64_t n_t, float* rho,
-                       const FusedLayout& lay, float* raw, double* dpart, cudaStream_t st) {
+                       const FusedLayout& lay, float* raw, double* dpart, cudaStream_t st,
+                       KnotRec* kn_ws, int64_t kn_batch) {
     const DevParams& p = plan->dp;
-    const bool cluster = lay.CL > 1;
-    const void* fn = cluster ? (const void*)fused_kernel<true> : (const void*)fused_kernel<false>;
+    const bool pre = kn_ws != nullptr;
+    const void* fn = kernel_ptr(p.L, pre);
+    if (!fn) return fail(CC_ERR_UNSUPPORTED, "no fused kernel for this coset length");
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.bytes);
     if (e != cudaSuccess) return cuda_fail(e, "fused smem attribute");
-    const int64_t MAXZ = 65535;
-    for (int64_t t0 = 0; t0 < n_t; t0 += MAXZ) {
-        const int64_t nt = std::min(MAXZ, n_t - t0);
+    const int64_t nkn = knot_rows(plan);
+    const int64_t step = pre ? std::min<int64_t>(kn_batch, 65535) : 65535;
+    for (int64_t tb = 0; tb < n_t; tb += step) {
+        const int64_t nt = std::min(step, n_t - tb);
+        if (pre) {
+            dim3 gk((unsigned)((nkn + 255) / 256), (unsigned)p.Q, (unsigned)nt);
+            knots_kernel<<<gk, 256, 0, st>>>(p, t_dev, tb, nkn, kn_ws);
+            count_launch();
+        }
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)lay.CL, (unsigned)lay.n_chunks, (unsigned)nt);
         cfg.blockDim = dim3(FUSED_THREADS);
@@ -476,14 +547,11 @@ cc_status launch_fused(cc_plan* plan, const cc_template* t_dev, int64_t n_t, flo
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        if (cluster)
-            e = cudaLaunchKernelEx(&cfg, fused_kernel<true>, p, lay, t_dev, t0, raw, dpart);
-        else
-            e = cudaLaunchKernelEx(&cfg, fused_kernel<false>, p, lay, t_dev, t0, raw, dpart);
+        e = launch_dispatch(p.L, cfg, pre, p, lay, t_dev, tb, raw, dpart, kn_ws, nkn);
         count_launch();
         if (e != cudaSuccess) return cuda_fail(e, "fused launch");
         dim3 g2((unsigned)launch_blocks_for(p.N_f, 256), (unsigned)nt);
-        finalize_kernel<<<g2, 256, 0, st>>>(raw, dpart, p.N_f, lay.n_chunks, t0, rho);
+        finalize_kernel<<<g2, 256, 0, st>>>(raw, dpart, p.N_f, lay.n_chunks, tb, rho);
         count_launch();
     }
     e = cudaGetLastError();

@@ -12,6 +12,7 @@ cc_status launch_norm_pairs(cc_plan* plan, const void* F, const float* norm, int
                             float* rho, cudaStream_t st);
 
 constexpr size_t STAGED_WS_BUDGET = (size_t)6 << 30;
+constexpr size_t KNOT_WS_BUDGET = (size_t)2 << 30;
 
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -41,14 +42,19 @@ extern "C" cc_status crosscorr_search(cc_plan* plan, const void* const* x_dev, c
     if (s != CC_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     FusedLayout lay;
-    if (plan->cfg.store == CC_STORE_FP32 && fused_layout(plan, n_t, &lay)) {
+    // knot records from the pre-pass, up to KNOT_WS_BUDGET bytes of them per batch
+    const size_t krow = (size_t)plan->Q * knot_rows(plan) * sizeof(KnotRec);
+    const int64_t kbatch = std::max<int64_t>(1, std::min<int64_t>(n_t, (int64_t)(KNOT_WS_BUDGET / krow)));
+    if (plan->cfg.store == CC_STORE_FP32 && fused_layout(plan, kbatch, &lay)) {
         // raw partial sums go straight into rho when there is one chunk per template
         const size_t dbytes = align256((size_t)n_t * lay.n_chunks * sizeof(double));
-        const size_t rbytes = lay.n_chunks > 1 ? (size_t)n_t * lay.n_chunks * plan->N_f * sizeof(float) : 0;
-        if ((s = ensure_workspace(plan, dbytes + rbytes)) != CC_OK) return s;
+        const size_t rbytes = lay.n_chunks > 1 ? align256((size_t)n_t * lay.n_chunks * plan->N_f * sizeof(float)) : 0;
+        const size_t kbytes = krow * kbatch;
+        if ((s = ensure_workspace(plan, dbytes + rbytes + kbytes)) != CC_OK) return s;
         double* dpart = (double*)plan->ws;
         float* raw = lay.n_chunks > 1 ? (float*)((char*)plan->ws + dbytes) : rho_dev;
-        return launch_fused(plan, t_dev, n_t, rho_dev, lay, raw, dpart, st);
+        KnotRec* kn = (KnotRec*)((char*)plan->ws + dbytes + rbytes);
+        return launch_fused(plan, t_dev, n_t, rho_dev, lay, raw, dpart, st, kn, kbatch);
     }
     int64_t batch;
     size_t bytes;
