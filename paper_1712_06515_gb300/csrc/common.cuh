@@ -52,6 +52,7 @@ struct DevParams {
     int64_t n_ab[CC_MAX_DET];
     const float* sig2[CC_MAX_DET];   // sigma^2 per T_sft block, 0 in gaps
     int64_t n_sig[CC_MAX_DET];
+    const int* lockc[CC_MAX_DET];    // [n_sig + 1] number of locked (sigma > 0) blocks before each block
     const int* coset_off;            // [C+1]
     const int* coset_k;              // [N_f] output index k, grouped by coset
     const int* coset_m;              // [N_f] position in the coset's L-point transform
@@ -85,6 +86,7 @@ struct FusedLayout {
     size_t off_wpart;                // [2][FUSED_WARPS][Q][4] float
     size_t off_nring;                // [R+1][Q] float4 (rank 0)
     size_t off_bins;                 // [nb] int2 (m, k) and [ncos+1] int starts
+    size_t off_flags;                // [2][CC_MAX_DET] int: detector has weight in the segment
     size_t bytes;
 };
 

@@ -77,6 +77,7 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
     float* wpart = (float*)(sm + lay.off_wpart);
     float4* nring = (float4*)(sm + lay.off_nring);
     int2* bins = (int2*)(sm + lay.off_bins);
+    int* segact = (int*)(sm + lay.off_flags);   // [2][CC_MAX_DET]: detector has weight in the segment
     int* cstart = (int*)(bins + nb);
 
     const cc_template T = tm[t];
@@ -154,6 +155,41 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
     };
     auto cluster_sync = [&]() { cg::this_cluster().sync(); };
 
+    // Gap skipping (knot records from the pre-pass): the detector times t = r - d of
+    // segment K lie within [seg0 - max d - 2, seg1 + 2 - min d] (d from the segment's
+    // knots; the cubic between knots stays within 1e-4 samples of them); a detector
+    // whose noise blocks there are all gaps has zero weight in the whole segment, so its
+    // resampling and transforms are skipped and it contributes F = 0.  Called by warp X.
+    auto seg_active = [&](int64_t K, int X) -> int {
+        if constexpr (!PREKNOTS) return 1;
+        const KnotRec* __restrict__ knX = kn + ((size_t)blockIdx.z * Q + X) * nkn;
+        const int64_t s0 = K * N_s, s1 = s0 + N_s;
+        const int64_t ka = s0 >> 7, kb = imin64(((s1 - 1) >> 7) + 1, nkn - 1);
+        float dmin = 3.0e38f, dmax = -3.0e38f;
+        for (int64_t k = ka + lane; k <= kb; k += 32) {
+            const KnotRec kr = load_knot(knX + k);
+            const float d = (float)kr.N + kr.f;
+            dmin = fminf(dmin, d);
+            dmax = fmaxf(dmax, d);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            dmin = fminf(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
+            dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        }
+        const int tlo = (int)s0 - (int)ceilf(dmax) - 2, thi = (int)s1 - (int)floorf(dmin) + 2;
+        int blo = floor_div32(tlo, p.nsft), bhi = floor_div32(thi, p.nsft);
+        const int ns = (int)p.n_sig[X];
+        blo = blo < 0 ? 0 : blo;
+        bhi = bhi > ns - 1 ? ns - 1 : bhi;
+        if (blo > bhi) return 0;
+        return __ldg(p.lockc[X] + bhi + 1) - __ldg(p.lockc[X] + blo) > 0 ? 1 : 0;
+    };
+    if (warp < Q) {
+        const int a = seg_active(Kl, warp);
+        if (lane == 0) segact[warp] = a;
+    }
+    __syncthreads();
+
     // prologue: knots and records of the first segment
     if constexpr (!PREKNOTS) {
         compute_knots(Kl, 0);
@@ -173,12 +209,13 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
             const int nloc = nmyb * KNOT;
             for (int X = 0; X < Q; ++X) {
                 float A = 0.f, B = 0.f, Cn = 0.f;
+                const bool actX = segact[b * CC_MAX_DET + X] != 0;
                 const float2* __restrict__ x = p.x[X];
                 float2* sa = (float2*)slice_ptr(lay, sm, b, Q, X, 0);
                 float2* sb = (float2*)slice_ptr(lay, sm, b, Q, X, 1);
                 const KnotRec* rec = recb + ((size_t)b * Q + X) * lay.nrec;
                 const KnotRec* __restrict__ knX = kn + ((size_t)blockIdx.z * Q + X) * nkn;
-                for (int li = tid; li < nloc; li += FUSED_THREADS) {
+                for (int li = tid; li < (actX ? nloc : 0); li += FUSED_THREADS) {
                     const int qi = li >> 7;
                     const int rr = (qi * CL + rank) * KNOT + (li & (KNOT - 1));
                     if (rr >= (int)N_s) continue;
@@ -220,6 +257,10 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
         // (3) knot records of the next segment's slice
         if constexpr (!PREKNOTS)
             if (K + 1 < Kb) build_records(K + 1, b ^ 1);
+        if (K + 1 < Kb && warp < Q) {
+            const int a = seg_active(K + 1, warp);
+            if (lane == 0) segact[(b ^ 1) * CC_MAX_DET + warp] = a;
+        }
         // (4) segment norms and the normalisation (rank 0 holds D): one thread per
         //     (peer, detector, component) sums that peer's warp partials
         if (rank == 0) {
@@ -289,7 +330,7 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
             for (int w = 0; w < 2; ++w) {
                 for (int g = 0; g < nround; ++g) {
                     const int X = 2 * g + half;
-                    if (X < Q) {
+                    if (X < Q && segact[b * CC_MAX_DET + X]) {
                         const float2* sbase = slice_ptr(lay, sm, b, Q, X, w);
                         float2 v[16];
                         if (lt < B1) {
@@ -342,7 +383,8 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
                         for (int hh = 0; hh < 2; ++hh) {
                             const int Xh = 2 * g + hh;
                             if (Xh >= Q) break;
-                            const float2 F = cmul(fftb[(size_t)hh * PL + padi(m)], wseg);
+                            const float2 F = segact[b * CC_MAX_DET + Xh] ? cmul(fftb[(size_t)hh * PL + padi(m)], wseg)
+                                                                         : make_float2(0.f, 0.f);
                             float2 hv = sacc;
                             if (R > 0) {
                                 if (lay.ring_q == 1) {
@@ -442,6 +484,8 @@ bool fused_layout(const cc_plan* plan, int64_t n_t, FusedLayout* lay) {
     o = al16(o + (size_t)(p.R + 1) * p.Q * sizeof(float4));
     lay->off_bins = o;
     o = al16(o + (size_t)lay->nb * sizeof(int2) + (ncos_max + 1) * sizeof(int));
+    lay->off_flags = o;
+    o = al16(o + (size_t)2 * CC_MAX_DET * sizeof(int));
     lay->bytes = o;
     if (lay->bytes > 227 * 1024) return false;
     if (p.L > 4096 || p.L < 64) return false;   // one radix-16 butterfly per thread per pass

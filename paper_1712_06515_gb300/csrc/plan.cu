@@ -253,11 +253,14 @@ cc_status crosscorr_plan(const cc_config* cfg, const cc_detector* dets, cc_plan*
             b[i] = (float)d.b_tab[i];
         }
         for (int64_t i = 0; i < d.n_sigma; ++i) s2[i] = (float)(d.sigma[i] * d.sigma[i]);
+        std::vector<int> lc(d.n_sigma + 1, 0);
+        for (int64_t i = 0; i < d.n_sigma; ++i) lc[i + 1] = lc[i] + (s2[i] > 0.f ? 1 : 0);
         cc_status st;
         if ((st = upload(p, d.ssb_delay, (size_t)d.n_eph, &dp.ssb[q])) != CC_OK ||
             (st = upload(p, a.data(), a.size(), &dp.atab[q])) != CC_OK ||
             (st = upload(p, b.data(), b.size(), &dp.btab[q])) != CC_OK ||
-            (st = upload(p, s2.data(), s2.size(), &dp.sig2[q])) != CC_OK) {
+            (st = upload(p, s2.data(), s2.size(), &dp.sig2[q])) != CC_OK ||
+            (st = upload(p, lc.data(), lc.size(), &dp.lockc[q])) != CC_OK) {
             crosscorr_plan_destroy(p);
             return st;
         }
