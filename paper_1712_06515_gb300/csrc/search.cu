@@ -9,7 +9,8 @@ cc_status launch_resample(cc_plan* plan, const cc_template* t_dev, int64_t n_t, 
                           cudaStream_t st);
 cc_status launch_segfft(cc_plan* plan, const void* ab, int64_t n_t, void* F, cudaStream_t st);
 cc_status launch_norm_pairs(cc_plan* plan, const void* F, const float* norm, int64_t n_t, double* Dws,
-                            float* rho, cudaStream_t st);
+                            float* rawws, float* rho, cudaStream_t st);
+size_t pair_workspace_bytes(const cc_plan* plan, int64_t n_t);
 
 constexpr size_t STAGED_WS_BUDGET = (size_t)6 << 30;
 constexpr size_t KNOT_WS_BUDGET = (size_t)2 << 30;
@@ -26,7 +27,7 @@ static void staged_batch(const cc_plan* p, int64_t n_t, int64_t* batch, size_t* 
     int64_t b = (int64_t)std::max<size_t>(1, STAGED_WS_BUDGET / per);
     b = std::min<int64_t>(b, n_t);
     *batch = b;
-    *bytes = (align256(ab * b) + align256(F * b) + align256(nm * b) + align256(8 * b));
+    *bytes = (align256(ab * b) + align256(F * b) + align256(nm * b) + align256(pair_workspace_bytes(p, b)));
 }
 
 }  // namespace cc
@@ -69,11 +70,12 @@ extern "C" cc_status crosscorr_search(cc_plan* plan, const void* const* x_dev, c
     float* nm = (float*)w;
     w += align256((size_t)plan->Q * plan->M * sizeof(float4) * batch);
     double* Dws = (double*)w;
+    float* rawws = (float*)((char*)w + (((size_t)batch * sizeof(double) + 255) & ~(size_t)255));
     for (int64_t t0 = 0; t0 < n_t; t0 += batch) {
         const int64_t nb = std::min(batch, n_t - t0);
         if ((s = launch_resample(plan, t_dev + t0, nb, ab, nm, st)) != CC_OK) return s;
         if ((s = launch_segfft(plan, ab, nb, F, st)) != CC_OK) return s;
-        if ((s = launch_norm_pairs(plan, F, nm, nb, Dws, rho_dev + t0 * plan->N_f, st)) != CC_OK) return s;
+        if ((s = launch_norm_pairs(plan, F, nm, nb, Dws, rawws, rho_dev + t0 * plan->N_f, st)) != CC_OK) return s;
     }
     return CC_OK;
 }

@@ -165,30 +165,32 @@ __global__ void norm_kernel(DevParams p, const float4* __restrict__ norm, int64_
     if (threadIdx.x == 0) Dout[t] = acc;
 }
 
-// Stage 3: one thread per (template, bin); pairs whose later segment is K are
-// added at step K, so each unordered pair is visited once.
+// Stage 3: one thread per (template, bin, chunk of segments); pairs whose later
+// segment is K are added at step K, so each unordered pair is visited once.  A chunk
+// starts R segments early to see its first segments' partners; the chunk partial
+// sums are combined by pair_finalize_kernel.  The segment loop is unrolled twice so
+// each thread keeps both segments' spectra loads in flight.
 __global__ void __launch_bounds__(PAIR_THREADS)
-pair_kernel(DevParams p, const float2* __restrict__ F, const double* __restrict__ Dn, int64_t t_base,
-            float* __restrict__ rho) {
-    const int64_t t = t_base + blockIdx.y;
+pair_kernel(DevParams p, const float2* __restrict__ F, int64_t t_base, int64_t chunk_len,
+            float* __restrict__ raw) {
+    const int64_t t = t_base + blockIdx.z;
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= p.N_f) return;
     const int Q = p.Q;
     const int64_t M = p.M, R = p.R, Nf = p.N_f;
     const int mode = p.pair_mode;
+    const int64_t Ka = (int64_t)blockIdx.y * chunk_len;
+    const int64_t Kb = Ka + chunk_len < M ? Ka + chunk_len : M;
+    const float2* __restrict__ Ft = F + (size_t)t * Q * M * 2 * Nf + k;
     auto Fat = [&](int X, int64_t K, int w) -> float2 {
-        return __ldg(F + (((t * Q + X) * M + K) * 2 + w) * Nf + k);
+        return __ldg(Ft + (((size_t)X * M + K) * 2 + w) * Nf);
     };
-    float sum = 0.f, comp = 0.f;
-    for (int64_t K = 0; K < M; ++K) {
+    auto step = [&](int64_t K, const float2 (&fk)[2][CC_MAX_DET]) -> float {
         float term = 0.f;
         for (int w = 0; w < 2; ++w) {
-            float2 fk[CC_MAX_DET], winx[CC_MAX_DET];
+            float2 winx[CC_MAX_DET];
             float2 win = make_float2(0.f, 0.f);
-            for (int X = 0; X < Q; ++X) {
-                fk[X] = Fat(X, K, w);
-                winx[X] = make_float2(0.f, 0.f);
-            }
+            for (int X = 0; X < Q; ++X) winx[X] = make_float2(0.f, 0.f);
             for (int64_t Lg = (K - R > 0 ? K - R : 0); Lg < K; ++Lg)
                 for (int X = 0; X < Q; ++X) {
                     const float2 f = Fat(X, Lg, w);
@@ -197,17 +199,57 @@ pair_kernel(DevParams p, const float2* __restrict__ F, const double* __restrict_
                 }
             float2 same = make_float2(0.f, 0.f);
             for (int Y = 0; Y < Q; ++Y) {
-                float2 h = cadd(same, mode == CC_PAIRS_CROSS_ONLY ? csub(win, winx[Y]) : win);
-                float tY = redot(fk[Y], h);
-                if (mode == CC_PAIRS_ALL_ORDERED) tY = fmaf(2.f, tY, redot(fk[Y], fk[Y]));
+                const float2 h = cadd(same, mode == CC_PAIRS_CROSS_ONLY ? csub(win, winx[Y]) : win);
+                float tY = redot(fk[w][Y], h);
+                if (mode == CC_PAIRS_ALL_ORDERED) tY = fmaf(2.f, tY, redot(fk[w][Y], fk[w][Y]));
                 term += tY;
-                same = cadd(same, fk[Y]);
+                same = cadd(same, fk[w][Y]);
             }
         }
-        kahan_add(sum, comp, term);
+        return term;
+    };
+    float sum = 0.f, comp = 0.f;
+    int64_t K = Ka;
+    for (; K + 1 < Kb; K += 2) {
+        float2 f0[2][CC_MAX_DET], f1[2][CC_MAX_DET];
+        for (int w = 0; w < 2; ++w)
+            for (int X = 0; X < Q; ++X) {
+                f0[w][X] = Fat(X, K, w);
+                f1[w][X] = Fat(X, K + 1, w);
+            }
+        kahan_add(sum, comp, step(K, f0));
+        kahan_add(sum, comp, step(K + 1, f1));
     }
+    if (K < Kb) {
+        float2 f0[2][CC_MAX_DET];
+        for (int w = 0; w < 2; ++w)
+            for (int X = 0; X < Q; ++X) f0[w][X] = Fat(X, K, w);
+        kahan_add(sum, comp, step(K, f0));
+    }
+    raw[((size_t)t * gridDim.y + blockIdx.y) * Nf + k] = sum;
+}
+
+__global__ void pair_finalize_kernel(const float* __restrict__ raw, const double* __restrict__ Dn,
+                                     int64_t N_f, int n_chunks, int64_t t_base, float* __restrict__ rho) {
+    const int64_t t = t_base + blockIdx.y;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N_f) return;
+    float s = 0.f, comp = 0.f;
+    for (int c = 0; c < n_chunks; ++c) kahan_add(s, comp, raw[((size_t)t * n_chunks + c) * N_f + k]);
     const double D = Dn[t];
-    rho[t * Nf + k] = D > 0.0 ? (float)(1.4142135623730951 * (double)sum / sqrt(D)) : 0.f;
+    rho[(size_t)t * N_f + k] = D > 0.0 ? (float)(1.4142135623730951 * (double)s / sqrt(D)) : 0.f;
+}
+
+// chunks of segments for the staged pair kernel: enough blocks to fill the GPU, each
+// chunk at least 4R + 1 segments long
+int64_t pair_chunks(const DevParams& p, int64_t n_t) {
+    const int64_t blocks = (int64_t)launch_blocks_for(p.N_f, PAIR_THREADS) * n_t;
+    const int64_t want = (8 * 152 + blocks - 1) / (blocks > 0 ? blocks : 1);
+    const int64_t maxch = p.M / (4 * p.R + 1) > 0 ? p.M / (4 * p.R + 1) : 1;
+    int64_t nch = want < maxch ? want : maxch;
+    if (nch < 1) nch = 1;
+    if (nch > 65535) nch = 65535;
+    return nch;
 }
 
 size_t resample_smem_bytes(const DevParams& p) {
@@ -251,18 +293,31 @@ cc_status launch_segfft(cc_plan* plan, const void* ab, int64_t n_t, void* F, cud
 }
 
 cc_status launch_norm_pairs(cc_plan* plan, const void* F, const float* norm, int64_t n_t,
-                            double* Dws, float* rho, cudaStream_t st) {
+                            double* Dws, float* rawws, float* rho, cudaStream_t st) {
     const DevParams& p = plan->dp;
+    const int64_t nch = pair_chunks(p, n_t);
+    const int64_t clen = (p.M + nch - 1) / nch;
+    const int64_t nchr = (p.M + clen - 1) / clen;
     for (int64_t t0 = 0; t0 < n_t; t0 += MAX_GRID_YZ) {
         const int64_t nt = std::min<int64_t>(MAX_GRID_YZ, n_t - t0);
         norm_kernel<<<(unsigned)nt, 256, 0, st>>>(p, (const float4*)norm, t0, Dws);
         count_launch();
-        dim3 grid((unsigned)launch_blocks_for(p.N_f, PAIR_THREADS), (unsigned)nt);
-        pair_kernel<<<grid, PAIR_THREADS, 0, st>>>(p, (const float2*)F, Dws, t0, rho);
+        dim3 grid((unsigned)launch_blocks_for(p.N_f, PAIR_THREADS), (unsigned)nchr, (unsigned)nt);
+        pair_kernel<<<grid, PAIR_THREADS, 0, st>>>(p, (const float2*)F, t0, clen, rawws);
+        count_launch();
+        dim3 g2((unsigned)launch_blocks_for(p.N_f, 256), (unsigned)nt);
+        pair_finalize_kernel<<<g2, 256, 0, st>>>(rawws, Dws, p.N_f, (int)nchr, t0, rho);
         count_launch();
     }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? CC_OK : cuda_fail(e, "pair launch");
+}
+
+size_t pair_workspace_bytes(const cc_plan* plan, int64_t n_t) {
+    const int64_t nch = pair_chunks(plan->dp, n_t);
+    const int64_t clen = (plan->M + nch - 1) / nch;
+    const int64_t nchr = (plan->M + clen - 1) / clen;
+    return (((size_t)n_t * sizeof(double) + 255) & ~(size_t)255) + (size_t)n_t * nchr * plan->N_f * sizeof(float);
 }
 
 cc_status set_inputs(cc_plan* plan, const void* const* x_dev) {
@@ -309,10 +364,11 @@ cc_status crosscorr_pair_accumulate(cc_plan* plan, const void* F_dev, const floa
     if (n_t < 0) return fail(CC_ERR_INVALID, "n_t must be >= 0");
     if (n_t == 0) return CC_OK;
     if (!F_dev || !norm_dev || !rho_dev) return fail(CC_ERR_INVALID, "null device pointer");
-    cc_status s = ensure_workspace(plan, (size_t)n_t * sizeof(double));
+    cc_status s = ensure_workspace(plan, pair_workspace_bytes(plan, n_t));
     if (s != CC_OK) return s;
-    return launch_norm_pairs(plan, F_dev, norm_dev, n_t, (double*)plan->ws, rho_dev,
-                             (cudaStream_t)stream);
+    const size_t dbytes = ((size_t)n_t * sizeof(double) + 255) & ~(size_t)255;
+    return launch_norm_pairs(plan, F_dev, norm_dev, n_t, (double*)plan->ws,
+                             (float*)((char*)plan->ws + dbytes), rho_dev, (cudaStream_t)stream);
 }
 
 }  // extern "C"
