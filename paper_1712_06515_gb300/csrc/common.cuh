@@ -64,6 +64,7 @@ struct DevParams {
 constexpr int FUSED_THREADS = 512;
 constexpr int FUSED_WARPS = FUSED_THREADS / 32;
 constexpr int MAX_CLUSTER = 8;
+constexpr int ACC_SLOTS = 4;   // register pair-sum accumulators per thread (bins per coset <= 2048)
 
 // Shared-memory layout and work split of the fused kernel (byte offsets).
 struct FusedLayout {
@@ -74,13 +75,15 @@ struct FusedLayout {
     int nrec;          // knot records per CTA: two per owned block
     int ring_q;        // detectors kept per ring slot (1: summed; Q: cross-only mode)
     int log2CL;        // CL is a power of two
+    int bothw;         // Q <= 2: both weights' transforms buffered, one pair pass per coset
+    int regacc;        // one coset per CTA with few bins: pair sums in registers
     int64_t chunk_len; // segments per chunk
     int n_chunks;
     size_t off_slice, slice_bytes;   // [2][Q][2][S] float2
-    size_t off_fft;                  // [2 halves][padded L] float2
+    size_t off_fft;                  // [weights (2 if bothw)][2 halves][padded L] float2
     size_t off_ring;                 // [slots][ring_q][2][nb] float2; slots = R (summed) or R+1
-    size_t off_same;                 // [nb] float2: running detector sum across rounds
-    size_t off_rho;                  // [nb] float, then [nb] float compensation
+    size_t off_same;                 // [nb] float2: running detector sum across rounds (Q > 2)
+    size_t off_rho;                  // [nb] float, then [nb] float compensation (unless regacc)
     size_t off_dk;                   // [2][Q][nkseg] double
     size_t off_rec;                  // [2][Q][nrec] KnotRec
     size_t off_wpart;                // [2][FUSED_WARPS][Q][4] float

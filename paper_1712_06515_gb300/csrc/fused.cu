@@ -105,7 +105,13 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
     const int64_t nslot = lay.ring_q > 1 ? R + 1 : R;   // per-detector rings keep one spare slot
     const int ringn = R > 0 ? (int)nslot * lay.ring_q * 2 * nb : 0;
     for (int i = tid; i < ringn; i += FUSED_THREADS) ring[i] = make_float2(0.f, 0.f);
-    for (int i = tid; i < nb; i += FUSED_THREADS) rho[i] = comp[i] = 0.f;
+    if (!lay.regacc)
+        for (int i = tid; i < nb; i += FUSED_THREADS) rho[i] = comp[i] = 0.f;
+    // with one coset per CTA and at most ACC_SLOTS * FUSED_THREADS bins, thread tid owns
+    // bins tid + s FUSED_THREADS and keeps their compensated sums in registers
+    float rhoR[ACC_SLOTS], compR[ACC_SLOTS];
+#pragma unroll
+    for (int s2 = 0; s2 < ACC_SLOTS; ++s2) rhoR[s2] = compR[s2] = 0.f;
     if (tid < (int)(R + 1) * Q) nring[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
     double Dacc = 0.0;
 
@@ -309,17 +315,97 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
                     for (int X = 0; X < Q; ++X) nring[(K % R) * Q + X] = nK[X];
             }
         }
-        // (5) spectra of this CTA's cosets and the pair sum.  Rounds of two detectors:
-        //     half h of the CTA transforms detector 2g + h of round g.
+        // (5) spectra of this CTA's cosets and the pair sum.  Half h of the CTA transforms
+        //     detector 2g + h of round g; with at most two detectors (one round) each half
+        //     transforms both weights into their own buffers and one pass over the bins
+        //     updates the pair sum, otherwise every (weight, round) has its own pass.
         const int half = tid >> 8, lt = tid & 255;
         const HalfSync hsync{1 + half};
-        const int PL = padded_len(L);
-        float2* hbuf = fftb + (size_t)half * PL;
+        constexpr int PL = padded_len(L);
         constexpr int R1 = 16;                // radix of the first pass
         constexpr int B1 = L / R1;
         const int offn = (int)((-seg0) & (int64_t)(L - 1));   // position p holds r - seg0 = (p + offn) mod L
-        const int64_t cur = R > 0 ? K % nslot : 0;
+        const int cur = R > 0 ? (int)(K % nslot) : 0;
         const int nround = (Q + 1) / 2;
+        const int* act = segact + b * CC_MAX_DET;
+        // gather + first radix-16 pass into registers, later passes through `buf`
+        auto transform = [&](int X, int w, float2* buf, const float2* __restrict__ twr) {
+            const float2* sbase = slice_ptr(lay, sm, b, Q, X, w);
+            if (lt < B1) {
+                float2 v[16];
+                if (N_s <= L) {
+                    float2 vv[16], tw[16];
+#pragma unroll
+                    for (int r = 0; r < 16; ++r) {
+                        vv[r] = tw[r] = make_float2(0.f, 0.f);
+                        const int rr = (lt + r * B1 + offn) & (L - 1);
+                        if (rr < (int)N_s) {
+                            const int q = rr >> 7;
+                            const int owner = q & (CL - 1);
+                            const float2* sp = sbase + (((q >> lay.log2CL) << 7) | (rr & (KNOT - 1)));
+                            vv[r] = *cg::this_cluster().map_shared_rank(sp, owner);
+                            tw[r] = __ldg(twr + rr);
+                        }
+                    }
+#pragma unroll
+                    for (int r = 0; r < 16; ++r) v[r] = cmul(vv[r], tw[r]);
+                } else {
+#pragma unroll
+                    for (int r = 0; r < 16; ++r) {
+                        float2 acc = make_float2(0.f, 0.f);
+                        for (int rr = (lt + r * B1 + offn) & (L - 1); rr < (int)N_s; rr += L) {
+                            const int q = rr >> 7;
+                            const int owner = q & (CL - 1);
+                            const float2* sp = sbase + (((q >> lay.log2CL) << 7) | (rr & (KNOT - 1)));
+                            const float2 vr = *cg::this_cluster().map_shared_rank(sp, owner);
+                            acc = cadd(acc, cmul(vr, __ldg(twr + rr)));
+                        }
+                        v[r] = acc;
+                    }
+                }
+                dft16(v);
+#pragma unroll
+                for (int r = 0; r < 16; ++r) buf[padi(lt * R1 + r)] = v[r];
+            }
+            hsync();
+            stockham_rest_t<L, 16>(buf, lt, p.twL, hsync);
+        };
+        // pair-sum term of bin i (transform position m) for weight w and round g, with the
+        // round's transforms in bufw[hh * PL]; updates the running detector sum and ring
+        auto pair_term = [&](int i, int m, int w, int g, const float2* bufw, float2 wseg) -> float {
+            float2 sacc = g == 0 ? make_float2(0.f, 0.f) : same[i];
+            float term = 0.f;
+            for (int hh = 0; hh < 2; ++hh) {
+                const int Xh = 2 * g + hh;
+                if (Xh >= Q) break;
+                const float2 F = act[Xh] ? cmul(bufw[hh * PL + padi(m)], wseg) : make_float2(0.f, 0.f);
+                float2 hv = sacc;
+                if (R > 0) {
+                    if (lay.ring_q == 1) {
+                        for (int sl = 0; sl < (int)R; ++sl) hv = cadd(hv, ring[(sl * 2 + w) * nb + i]);
+                    } else {
+                        for (int sl = 0; sl < (int)nslot; ++sl) {
+                            if (sl == cur) continue;
+                            for (int X2 = 0; X2 < Q; ++X2)
+                                if (X2 != Xh) hv = cadd(hv, ring[((sl * Q + X2) * 2 + w) * nb + i]);
+                        }
+                        ring[((cur * Q + Xh) * 2 + w) * nb + i] = F;
+                    }
+                }
+                float tX = redot(F, hv);
+                if (p.pair_mode == CC_PAIRS_ALL_ORDERED) tX = fmaf(2.f, tX, redot(F, F));
+                term += tX;
+                sacc = cadd(sacc, F);
+            }
+            if (g < nround - 1) same[i] = sacc;
+            else if (R > 0 && lay.ring_q == 1) ring[(cur * 2 + w) * nb + i] = sacc;
+            return term;
+        };
+        auto accumulate = [&](int s, int i, float term) {
+            if (K < Ka) return;
+            if (lay.regacc) kahan_add(rhoR[s], compR[s], term);
+            else kahan_add(rho[i], comp[i], term);
+        };
         for (int j = 0; j < ncos; ++j) {
             const int c = rank + j * CL;
             const uint64_t N = (uint64_t)p.N_FFT, mask = N - 1;
@@ -327,87 +413,46 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
             const float2 wseg = twiddle_N((bc * ((uint64_t)seg0 & mask)) & mask, N);
             const float2* __restrict__ twr = p.twc + (size_t)c * N_s;
             const int i0 = cstart[j], i1 = cstart[j + 1];
-            for (int w = 0; w < 2; ++w) {
-                for (int g = 0; g < nround; ++g) {
-                    const int X = 2 * g + half;
-                    if (X < Q && segact[b * CC_MAX_DET + X]) {
-                        const float2* sbase = slice_ptr(lay, sm, b, Q, X, w);
-                        float2 v[16];
-                        if (lt < B1) {
-                            if (N_s <= L) {
-                                float2 vv[16], tw[16];
+            if (lay.bothw) {
+                if (half < Q && act[half]) {
+#pragma unroll 1
+                    for (int w = 0; w < 2; ++w) transform(half, w, fftb + (2 * w + half) * PL, twr);
+                }
+                __syncthreads();
 #pragma unroll
-                                for (int r = 0; r < 16; ++r) {
-                                    vv[r] = tw[r] = make_float2(0.f, 0.f);
-                                    const int rr = (lt + r * B1 + offn) & (L - 1);
-                                    if (rr < (int)N_s) {
-                                        const int q = rr >> 7;
-                                        const int owner = q & (CL - 1);
-                                        const float2* sp = sbase + (((q >> lay.log2CL) << 7) | (rr & (KNOT - 1)));
-                                        vv[r] = *cg::this_cluster().map_shared_rank(sp, owner);
-                                        tw[r] = __ldg(twr + rr);
-                                    }
-                                }
-#pragma unroll
-                                for (int r = 0; r < 16; ++r) v[r] = cmul(vv[r], tw[r]);
-                            } else {
-#pragma unroll
-                                for (int r = 0; r < 16; ++r) {
-                                    float2 acc = make_float2(0.f, 0.f);
-                                    {
-                                        for (int rr = (lt + r * B1 + offn) & (L - 1); rr < (int)N_s; rr += L) {
-                                            const int q = rr >> 7;
-                                            const int owner = q & (CL - 1);
-                                            const float2* sp = sbase + (((q >> lay.log2CL) << 7) | (rr & (KNOT - 1)));
-                                            const float2 vr = *cg::this_cluster().map_shared_rank(sp, owner);
-                                            acc = cadd(acc, cmul(vr, __ldg(twr + rr)));
-                                        }
-                                    }
-                                    v[r] = acc;
-                                }
-                            }
-                            dft16(v);
-#pragma unroll
-                            for (int r = 0; r < 16; ++r) hbuf[padi(lt * R1 + r)] = v[r];
-                        }
-                        hsync();
-                        stockham_rest_t<L, 16>(hbuf, lt, p.twL, hsync);
-                    }
-                    __syncthreads();
-                    // pair sum for this round's detectors
-                    const bool lastg = (g == nround - 1);
-                    for (int i = i0 + tid; i < i1; i += FUSED_THREADS) {
+                for (int s = 0; s < ACC_SLOTS; ++s) {
+                    const int i = i0 + tid + s * FUSED_THREADS;
+                    if (s * FUSED_THREADS < i1 - i0 && i < i1) {
                         const int m = bins[i].x;
-                        float2 sacc = g == 0 ? make_float2(0.f, 0.f) : same[i];
                         float term = 0.f;
-                        for (int hh = 0; hh < 2; ++hh) {
-                            const int Xh = 2 * g + hh;
-                            if (Xh >= Q) break;
-                            const float2 F = segact[b * CC_MAX_DET + Xh] ? cmul(fftb[(size_t)hh * PL + padi(m)], wseg)
-                                                                         : make_float2(0.f, 0.f);
-                            float2 hv = sacc;
-                            if (R > 0) {
-                                if (lay.ring_q == 1) {
-                                    for (int sl = 0; sl < (int)R; ++sl) hv = cadd(hv, ring[((size_t)sl * 2 + w) * nb + i]);
-                                } else {
-                                    for (int sl = 0; sl < (int)nslot; ++sl) {
-                                        if (sl == (int)cur) continue;
-                                        for (int X2 = 0; X2 < Q; ++X2)
-                                            if (X2 != Xh) hv = cadd(hv, ring[(((size_t)sl * Q + X2) * 2 + w) * nb + i]);
-                                    }
-                                    ring[(((size_t)cur * Q + Xh) * 2 + w) * nb + i] = F;
-                                }
-                            }
-                            float tX = redot(F, hv);
-                            if (p.pair_mode == CC_PAIRS_ALL_ORDERED) tX = fmaf(2.f, tX, redot(F, F));
-                            term += tX;
-                            sacc = cadd(sacc, F);
-                        }
-                        if (K >= Ka) kahan_add(rho[i], comp[i], term);
-                        if (!lastg) same[i] = sacc;
-                        else if (R > 0 && lay.ring_q == 1) ring[((size_t)cur * 2 + w) * nb + i] = sacc;
+#pragma unroll 1
+                        for (int w = 0; w < 2; ++w) term += pair_term(i, m, w, 0, fftb + 2 * w * PL, wseg);
+                        accumulate(s, i, term);
                     }
-                    __syncthreads();
+                }
+                for (int i = i0 + tid + ACC_SLOTS * FUSED_THREADS; i < i1; i += FUSED_THREADS) {
+                    const int m = bins[i].x;
+                    float term = 0.f;
+#pragma unroll 1
+                    for (int w = 0; w < 2; ++w) term += pair_term(i, m, w, 0, fftb + 2 * w * PL, wseg);
+                    accumulate(0, i, term);
+                }
+                __syncthreads();
+            } else {
+                for (int w = 0; w < 2; ++w) {
+                    for (int g = 0; g < nround; ++g) {
+                        const int X = 2 * g + half;
+                        if (X < Q && act[X]) transform(X, w, fftb + half * PL, twr);
+                        __syncthreads();
+#pragma unroll
+                        for (int s = 0; s < ACC_SLOTS; ++s) {
+                            const int i = i0 + tid + s * FUSED_THREADS;
+                            if (i < i1) accumulate(s, i, pair_term(i, bins[i].x, w, g, fftb, wseg));
+                        }
+                        for (int i = i0 + tid + ACC_SLOTS * FUSED_THREADS; i < i1; i += FUSED_THREADS)
+                            accumulate(0, i, pair_term(i, bins[i].x, w, g, fftb, wseg));
+                        __syncthreads();
+                    }
                 }
             }
         }
@@ -415,7 +460,15 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
     // every peer may still read this CTA's shared memory until the cluster is done
     cluster_sync();
     float* outp = raw_out + ((size_t)t * lay.n_chunks + chunk) * p.N_f;
-    for (int i = tid; i < nmine; i += FUSED_THREADS) outp[bins[i].y] = rho[i];
+    if (lay.regacc) {
+#pragma unroll
+        for (int s2 = 0; s2 < ACC_SLOTS; ++s2) {
+            const int i = tid + s2 * FUSED_THREADS;
+            if (i < nmine) outp[bins[i].y] = rhoR[s2];
+        }
+    } else {
+        for (int i = tid; i < nmine; i += FUSED_THREADS) outp[bins[i].y] = rho[i];
+    }
     if (rank == 0 && tid == 0) dpart_out[(size_t)t * lay.n_chunks + chunk] = Dacc;
 }
 
@@ -466,14 +519,16 @@ bool fused_layout(const cc_plan* plan, int64_t n_t, FusedLayout* lay) {
     lay->slice_bytes = (size_t)2 * p.Q * 2 * lay->S * sizeof(float2);
     o = al16(o + lay->slice_bytes);
     lay->off_fft = o;
-    o = al16(o + (size_t)2 * padded_len(p.L) * sizeof(float2));
+    lay->bothw = p.Q <= 2 ? 1 : 0;
+    lay->regacc = (C == CL && lay->nb <= ACC_SLOTS * FUSED_THREADS) ? 1 : 0;
+    o = al16(o + (size_t)(lay->bothw ? 4 : 2) * padded_len(p.L) * sizeof(float2));
     lay->off_ring = o;
     const int64_t nslot = lay->ring_q > 1 ? p.R + 1 : p.R;
     o = al16(o + (size_t)nslot * lay->ring_q * 2 * lay->nb * sizeof(float2));
     lay->off_same = o;
-    o = al16(o + (size_t)lay->nb * sizeof(float2));
+    o = al16(o + (size_t)(p.Q > 2 ? lay->nb : 0) * sizeof(float2));
     lay->off_rho = o;
-    o = al16(o + (size_t)2 * lay->nb * sizeof(float));
+    o = al16(o + (size_t)(lay->regacc ? 0 : 2 * lay->nb) * sizeof(float));
     lay->off_dk = o;
     o = al16(o + (size_t)2 * p.Q * lay->nkseg * sizeof(double));
     lay->off_rec = o;
