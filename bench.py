@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--templates", type=int, default=GRID_TEMPLATES,
                     help="templates per step per rank (default: the whole 40x200 grid)")
     ap.add_argument("--path", default="search", choices=["search", "staged"])
+    ap.add_argument("--interp", default="exact", choices=["exact", "learned"],
+                    help="exact: windowed sinc, 2D+1 = 17 taps; learned: the 8-tap network")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-days", type=float, default=120.0,
                     help="days of data in the bounded CPU oracle sample")
@@ -157,18 +159,21 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU run
 # ---------------------------------------------------------------------------
-def algorithmic_costs(plan_info, Q, n_t, D=8):
+def algorithmic_costs(plan_info, Q, n_t, D=8, learned=False):
     """Algorithmic flops / bytes of the path for n_t templates.
 
     Whole-path flops per template: FFT at 5 N log2 N per zero-padded segment
-    transform (2 weights x Q detectors x M segments); windowed-sinc at (2D+1)
-    complex multiply-adds (8 flops) + 30 for timing, phase and weights per source
-    sample and detector; pair sum at 8 flops per (detector, segment, weight, bin)
-    and partner (2R + 2 partners).  Staged kernels: bytes each reads and writes."""
+    transform (2 weights x Q detectors x M segments); per source sample and
+    detector, 8 flops per windowed-sinc tap (coefficient and complex multiply-add,
+    2D+1 taps) or 4 per learned tap (8 taps, plus 16 for the tap-table
+    interpolation), + 30 for timing, phase and weights; pair sum at 8 flops per (detector,
+    segment, weight, bin) and partner (2R + 2 partners).  Staged kernels: bytes each
+    reads and writes."""
     N = plan_info["N_FFT"]
     M, N_f, N_tau, R = plan_info["M"], plan_info["N_f"], plan_info["N_tau"], plan_info["R"]
     fft = 2 * Q * M * 5.0 * N * math.log2(N)
-    interp = Q * N_tau * (8.0 * (2 * D + 1) + 30.0)
+    per_sample = (4.0 * 8 + 16.0) if learned else 8.0 * (2 * D + 1)
+    interp = Q * N_tau * (per_sample + 30.0)
     pairs = 2 * Q * M * N_f * 8.0 * (2 * R + 2)
     return {
         "fft_flops": fft * n_t, "interp_flops": interp * n_t, "pair_flops": pairs * n_t,
@@ -199,7 +204,8 @@ def run_gpu(args):
     grid = ds.templates
     idx = (np.arange(B) + rank * B) % grid.shape[0]
     tm_host = np.ascontiguousarray(grid[idx])
-    plan = cc.CrossCorrPlan(ds.cfg, ds.dets)
+    learned = args.interp == "learned"
+    plan = cc.CrossCorrPlan(ds.cfg, ds.dets, interp=cc.INTERP_LEARNED if learned else cc.INTERP_EXACT)
     Q, N_f = plan.Q, plan.N_f
     x = torch.from_numpy(ds.x64).to(dev)
     tm = torch.from_numpy(tm_host).to(dev)
@@ -276,7 +282,7 @@ def run_gpu(args):
     peaks, peak_kind = load_peaks()
     out = None
     if rank == 0:
-        costs = algorithmic_costs(info, Q, 1, ds.cfg.D)
+        costs = algorithmic_costs(info, Q, 1, ds.cfg.D, learned)
         # the fused kernel is the step (plus a finalize pass of N_f floats per template):
         # FP32-ALU roofline from the SM count, FP32 lanes and the maximum SM clock
         fl = costs["total_flops"] * B
@@ -298,7 +304,9 @@ def run_gpu(args):
                        "templates_per_step_per_rank": B, "grid_templates": GRID_TEMPLATES,
                        "N_f": N_f, "N_FFT": info["N_FFT"], "M": info["M"], "L": info["L"], "C": info["C"],
                        "l2": "inputs larger than L2 (2 x 83 MB complex64 series)",
-                       "timing_precision": "f64 knots, f32 interpolation/FFT/pairs"},
+                       "timing_precision": "f64 knots, f32 interpolation/FFT/pairs",
+                       "interp": ("learned 8-tap network (bf16 weights, tabulated taps)" if learned
+                                  else f"windowed sinc, {2 * ds.cfg.D + 1} taps")},
             "roofline": roof,
             "clocks": clk,
             "gpu_launches": int(launches),

@@ -80,7 +80,8 @@ typedef struct {
     double mu_f;      /* frequency mismatch for the metric spacing (0.1 typical) */
     int32_t n_det;    /* Q, 1..CC_MAX_DET */
     int32_t D;        /* windowed-sinc half width: 2D+1 taps, 1..32 */
-    int32_t interp;   /* CC_INTERP_EXACT (CC_INTERP_LEARNED reserved) */
+    int32_t interp;   /* CC_INTERP_EXACT, or CC_INTERP_LEARNED (then call
+                         crosscorr_plan_set_learned_interp before any compute call) */
     int32_t store;    /* CC_STORE_FP32 or CC_STORE_BF16 for the resampled a_r, b_r series */
     int32_t pair_mode;/* CC_PAIRS_* */
     int32_t reserved;
@@ -141,6 +142,33 @@ typedef struct cc_plan cc_plan;
  * to the device.  dets: host array of cfg->n_det detectors.  *out receives a
  * plan owned by the caller and released with crosscorr_plan_destroy. */
 cc_status crosscorr_plan(const cc_config* cfg, const cc_detector* dets, cc_plan** out);
+
+/* Learned 8-tap interpolator.  The paper has no counterpart: it is a stand-in for the
+ * 2D+1-tap windowed sinc of Eq. shannon-interp-formula.  A network maps the fractional
+ * offset u = t/dt' - floor(t/dt') in [0, 1) and the band half-width nu_c (cycles per
+ * sample; the local spectral context) to 8 taps c_0..c_7:
+ *   s  = (2u - 1, (2 nu_c - nu_lo - nu_hi) / (nu_hi - nu_lo))
+ *   h1 = tanh(s W1 + b1),  h2 = tanh(h1 W2 + b2),  c = h2 W3 + b3
+ *   x(t) = sum_n c_n x[floor(t/dt') - 3 + n]     (samples outside [0, N_t) are zero)
+ * Weights are BF16 bit patterns, concatenated row-major in the order
+ *   W1 [2][64], b1 [64], W2 [64][64], b2 [64], W3 [64][8], b3 [8]   (4872 values),
+ * W[i][o] multiplying input i into output o.  The network is evaluated with FP32
+ * accumulation; the plan tabulates the taps on a fine grid of u (1025 nodes) once and
+ * interpolates them linearly in u per sample. */
+#define CC_LEARNED_N_WEIGHTS 4872
+typedef struct {
+    const uint16_t* weights_bf16;  /* host, CC_LEARNED_N_WEIGHTS values; copied */
+    int64_t n_weights;             /* must equal CC_LEARNED_N_WEIGHTS */
+    double nu_lo, nu_hi;           /* nu_c range the network was trained for (nu_lo < nu_hi) */
+    double nu_c;                   /* this plan's band half-width, within [nu_lo, nu_hi] */
+} cc_learned_interp;
+
+/* Install the learned interpolator in a plan built with interp = CC_INTERP_LEARNED
+ * (CC_ERR_INVALID otherwise, or on a wrong weight count, a non-finite weight or an
+ * inverted range; CC_ERR_UNSUPPORTED if nu_c is outside [nu_lo, nu_hi]).  Synchronous:
+ * uploads the weights and tabulates the taps on the device before returning.  May be
+ * called again to replace the weights. */
+cc_status crosscorr_plan_set_learned_interp(cc_plan* plan, const cc_learned_interp* li);
 
 /* Plan quantities; freqs_host (nullable, N_f doubles) receives the absolute
  * output frequencies f_FFT + k-bar/T_FFT, kbar_host (nullable, N_f int64) the bins. */

@@ -7,10 +7,12 @@ does, and it shares no code with the CUDA library (only the seeded input
 generator in ``synth`` serves both sides).
 
 Every function cites the passage of the paper it follows.  Parity status:
-all functions are pinned by ``tests/test_oracle_pins.py`` except the learned
-interpolator, which the paper does not have (it is judged against the exact
-stencil instead).
+all functions are pinned by ``tests/test_oracle_pins.py``.  The learned
+interpolator (``oracle.learned``) is PARITY UNPINNED against the paper, which has no
+such component; it is pinned by tone reproduction and judged against the exact
+stencil.
 """
+from . import learned  # noqa: F401
 from .crosscorr import (  # noqa: F401
     PAIR_UNORDERED, PAIR_CROSS_ONLY, PAIR_ALL_ORDERED,
     Plan, make_plan, ssb_delay, delay, stencil_position, interpolate, hamming, timing,

@@ -221,13 +221,14 @@ def timing(det, cfg, plan: Plan, tmpl):
     return jstar, delta, d
 
 
-def resample(x: np.ndarray, det, cfg, plan: Plan, tmpl):
+def resample(x: np.ndarray, det, cfg, plan: Plan, tmpl, interp=None):
     """Source-frame series x'_r, r = 0..M N_s - 1, of one detector for one template:
     the interpolated x'(t(tau_r)) times exp(-2 pi i f_h [tau_r - t(tau_r)])
     (Eq. resampled-time-series-q-eq; reading 4: the printed exponent lacks the i
-    that the sentence before it has).  Returns (x'_r, j*, delta)."""
+    that the sentence before it has).  Returns (x'_r, j*, delta).  `interp`, if
+    given, replaces the windowed sinc: interp(x, j*, delta) -> x(t)."""
     jstar, delta, d = timing(det, cfg, plan, tmpl)
-    xi = interpolate(x, jstar, delta, cfg.D)
+    xi = interpolate(x, jstar, delta, cfg.D) if interp is None else interp(x, jstar, delta)
     cyc = cfg.f_h * d
     cyc = cyc - np.floor(cyc)
     return xi * np.exp(-2j * np.pi * cyc), jstar, delta
@@ -364,16 +365,16 @@ def pair_sum(Fa, Fb, plan: Plan, mode: int) -> np.ndarray:
 # Whole statistic
 # ---------------------------------------------------------------------------
 def rho_template(ds, tmpl, plan: Optional[Plan] = None, spectra: str = "fft",
-                 mode: Optional[int] = None, return_parts: bool = False):
+                 mode: Optional[int] = None, return_parts: bool = False, interp=None):
     """rho_k for one template (Eq. final-formatted-rho): sqrt(2) times the pair sum
-    over sqrt(A^2 + 2C^2 + B^2)."""
+    over sqrt(A^2 + 2C^2 + B^2).  `interp` as in resample()."""
     cfg = ds.cfg
     plan = plan or make_plan(cfg)
     mode = cfg.pair_mode if mode is None else mode
     spec = spectra_fft if spectra == "fft" else spectra_direct
     Fa, Fb, norms = [], [], []
     for q, det in enumerate(ds.dets):
-        xr, jstar, delta = resample(ds.x[q], det, cfg, plan, tmpl)
+        xr, jstar, delta = resample(ds.x[q], det, cfg, plan, tmpl, interp)
         alpha, beta, s2 = weights(det, cfg, jstar, delta)
         Fa.append(spec(alpha * xr, plan))
         Fb.append(spec(beta * xr, plan))
@@ -387,11 +388,11 @@ def rho_template(ds, tmpl, plan: Optional[Plan] = None, spectra: str = "fft",
 
 
 def rho(ds, templates=None, spectra: str = "fft", mode: Optional[int] = None,
-        plan: Optional[Plan] = None) -> np.ndarray:
+        plan: Optional[Plan] = None, interp=None) -> np.ndarray:
     """rho[template][bin] for a set of templates."""
     plan = plan or make_plan(ds.cfg)
     tm = ds.templates if templates is None else np.asarray(templates, np.float64)
-    return np.stack([rho_template(ds, t, plan, spectra, mode) for t in tm])
+    return np.stack([rho_template(ds, t, plan, spectra, mode, interp=interp) for t in tm])
 
 
 def topk(rho_tb: np.ndarray, k: int):

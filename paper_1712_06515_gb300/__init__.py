@@ -15,7 +15,7 @@ from typing import Optional, Sequence
 import numpy as np
 
 from . import _lib
-from ._lib import CcConfig, CcDetector, CcHit, CcPlanInfo, CrossCorrError, check
+from ._lib import CcConfig, CcDetector, CcHit, CcLearnedInterp, CcPlanInfo, CrossCorrError, check
 
 __all__ = ["CrossCorrPlan", "CrossCorrError", "PAIR_UNORDERED", "PAIR_CROSS_ONLY",
            "PAIR_ALL_ORDERED", "STORE_FP32", "STORE_BF16", "build", "load"]
@@ -57,11 +57,15 @@ class CrossCorrPlan:
     ``cfg`` needs the attributes t0, dt, n_samples, f_h, f_band, T_sft, T_max,
     T_short, mu_f, D, n_det, pair_mode; each detector in ``dets`` needs eph_t0,
     eph_dt, ssb_delay, ab_t0, ab_dt, a_tab, b_tab, sigma (numpy arrays for the
-    tables; times relative to t0).
+    tables; times relative to t0).  With ``interp=INTERP_LEARNED`` the learned
+    8-tap interpolator is installed from ``learned_weights`` (a weight file; the
+    packaged one by default) at the band half-width ``nu_c`` (by default the one
+    ``learned_interp.band_halfwidth`` gives for this band).
     """
 
     def __init__(self, cfg, dets: Sequence, store: int = STORE_FP32, interp: int = INTERP_EXACT,
-                 pair_mode: Optional[int] = None):
+                 pair_mode: Optional[int] = None, learned_weights: Optional[str] = None,
+                 nu_c: Optional[float] = None):
         self._lib = _lib.load()
         c = CcConfig()
         c.t0, c.dt, c.f_h, c.f_band = cfg.t0, cfg.dt, cfg.f_h, cfg.f_band
@@ -102,6 +106,29 @@ class CrossCorrPlan:
         self.M = info.M
         self.N_tau = info.N_tau
         self.store = store
+        self.interp = interp
+        self.nu_c = None
+        if interp == INTERP_LEARNED:
+            self.set_learned_interp(learned_weights, nu_c)
+
+    def set_learned_interp(self, path: Optional[str] = None, nu_c: Optional[float] = None):
+        """Install (or replace) the learned interpolator's weights; tabulates its taps."""
+        from . import learned_interp
+        z = np.load(path or learned_interp.WEIGHTS)
+        layers = [np.asarray(z[k], np.float32) for k in ("W1", "b1", "W2", "b2", "W3", "b3")]
+        bits = np.ascontiguousarray(learned_interp.flat_bf16_bits(layers))
+        lo, hi = (float(v) for v in z["nu_c_range"])
+        if int(z["tap_offset"]) != 3 or str(z["activation"]) != "tanh":
+            raise ValueError("the library evaluates tanh networks with taps from floor(t) - 3")
+        if nu_c is None:
+            nu_c = learned_interp.band_halfwidth(self.cfg.f_band, self.cfg.f_h, self.cfg.dt)
+        li = CcLearnedInterp()
+        li.weights_bf16 = bits.ctypes.data_as(POINTER(ctypes.c_uint16))
+        li.n_weights = bits.size
+        li.nu_lo, li.nu_hi, li.nu_c = lo, hi, float(nu_c)
+        check("crosscorr_plan_set_learned_interp",
+              self._lib.crosscorr_plan_set_learned_interp(self._h, byref(li)))
+        self.nu_c = float(nu_c)
 
     # -- helpers ---------------------------------------------------------------
     def _xptrs(self, x):

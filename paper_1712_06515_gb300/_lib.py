@@ -20,7 +20,7 @@ BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "lib")
 LIBPATH = os.path.join(LIBDIR, "libcrosscorr.so")
 
-SOURCES = ["plan.cu", "stages.cu", "search.cu", "topk.cu", "fused.cu", "noalloc.cu"]
+SOURCES = ["plan.cu", "stages.cu", "search.cu", "topk.cu", "fused.cu", "noalloc.cu", "learned.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 
@@ -103,10 +103,16 @@ class CcPlanInfo(ctypes.Structure):
                 ("nu_R", c_double), ("f_r", c_double), ("f_FFT", c_double), ("ws_bytes", c_size_t)]
 
 
+class CcLearnedInterp(ctypes.Structure):
+    _fields_ = [("weights_bf16", POINTER(ctypes.c_uint16)), ("n_weights", c_int64),
+                ("nu_lo", c_double), ("nu_hi", c_double), ("nu_c", c_double)]
+
+
 # every symbol the header declares, with its signature
 SIGNATURES = {
     "crosscorr_plan": (c_int, [POINTER(CcConfig), POINTER(CcDetector), POINTER(c_void_p)]),
     "crosscorr_plan_info": (c_int, [c_void_p, POINTER(CcPlanInfo), POINTER(c_double), POINTER(c_int64)]),
+    "crosscorr_plan_set_learned_interp": (c_int, [c_void_p, POINTER(CcLearnedInterp)]),
     "crosscorr_resample": (c_int, [c_void_p, POINTER(c_void_p), c_void_p, c_int64, c_void_p, c_void_p,
                                    c_void_p]),
     "crosscorr_segment_fft": (c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),

@@ -22,6 +22,14 @@ constexpr int N_BIN_ITER = 4;   // fixed-point steps of the binary delay b = a_p
 constexpr int N_SSB_ITER = 4;   // fixed-point steps of t = u - Delta(t)
 constexpr int MAX_L = 8192;     // largest on-chip coset FFT
 
+// Learned interpolator: 8 taps from a 2 -> 64 -> 64 -> 8 tanh network, tabulated at
+// LEARNED_NODES offsets u = i / (LEARNED_NODES - 1) and interpolated linearly in u.
+// The taps are smooth in u (|d2c/du2| ~ 10), so the table's error is ~1e-6.
+constexpr int LEARNED_TAPS = 8;
+constexpr int LEARNED_WIDTH = 64;
+constexpr int LEARNED_NODES = 1025;
+constexpr int LEARNED_TAP_OFFSET = 3;   // first tap at floor(t/dt') - 3
+
 // Timing record of one knot, built from four FP64 knot delays.
 struct __align__(16) KnotRec {
     int N;        // floor(d_k / dt)
@@ -37,7 +45,7 @@ struct __align__(16) KnotRec {
 struct DevParams {
     int Q, D, pair_mode, store;
     int L, C, log2L, nsft;
-    int n_ab_step, pad_;
+    int n_ab_step, interp;           // interp: CC_INTERP_EXACT or CC_INTERP_LEARNED
     int64_t N_t, N_s, M, R, N_tau, N_FFT, N_f;
     int64_t b0;      // (k0 - N_FFT/2) mod N_FFT: FFT bin of output k = 0
     int64_t ab_j0;   // ab_t0 / dt
@@ -58,6 +66,7 @@ struct DevParams {
     const int* coset_m;              // [N_f] position in the coset's L-point transform
     const float2* twL;               // exp(-2 pi i j / L), j < L
     const float2* twc;               // [C][N_s]: exp(-2 pi i ((b0 + c) s mod N_FFT) / N_FFT)
+    const float* ltaps;              // [LEARNED_NODES][LEARNED_TAPS] learned taps (null until set)
     float ham[MAX_TAPS];             // Hamming window, 2D+1 taps
 };
 
@@ -108,6 +117,9 @@ struct cc_plan {
     cc::DevParams dp;
     // device allocations owned by the plan
     std::vector<void*> dev_allocs;
+    // learned interpolator: device weights (BF16 bits) and tap table, once set
+    uint16_t* learned_w = nullptr;
+    float* learned_taps = nullptr;
     // workspace (grown on demand by staged/fused paths)
     void* ws = nullptr;
     size_t ws_bytes = 0;
@@ -300,6 +312,52 @@ __device__ __forceinline__ float2 interp_sinc(const DevParams& p, const float2* 
         }
     }
     return acc;
+}
+
+// Learned 8-tap interpolation at t/dt = j* + delta: taps from the tabulated network at
+// u = t/dt - floor(t/dt) on x[floor(t/dt) - 3 .. floor(t/dt) + 4].
+__device__ __forceinline__ float2 interp_learned(const DevParams& p, const float2* __restrict__ x,
+                                                 int jstar, float delta) {
+    const int N = (int)p.N_t;
+    const bool neg = delta < 0.0f;
+    const int j0 = jstar - (neg ? 1 : 0) - LEARNED_TAP_OFFSET;
+    const float u = neg ? delta + 1.0f : delta;
+    const float fu = u * (float)(LEARNED_NODES - 1);
+    int i = (int)fu;
+    i = i > LEARNED_NODES - 2 ? LEARNED_NODES - 2 : i;
+    const float f = fu - (float)i;
+    const float4* tb = (const float4*)(p.ltaps + i * LEARNED_TAPS);
+    const float4 a0 = __ldg(tb), a1 = __ldg(tb + 1), n0 = __ldg(tb + 2), n1 = __ldg(tb + 3);
+    const float c[LEARNED_TAPS] = {fmaf(f, n0.x - a0.x, a0.x), fmaf(f, n0.y - a0.y, a0.y),
+                                   fmaf(f, n0.z - a0.z, a0.z), fmaf(f, n0.w - a0.w, a0.w),
+                                   fmaf(f, n1.x - a1.x, a1.x), fmaf(f, n1.y - a1.y, a1.y),
+                                   fmaf(f, n1.z - a1.z, a1.z), fmaf(f, n1.w - a1.w, a1.w)};
+    float2 acc = make_float2(0.f, 0.f);
+    if (j0 >= 0 && j0 + LEARNED_TAPS <= N) {
+#pragma unroll
+        for (int n = 0; n < LEARNED_TAPS; ++n) {
+            const float2 xv = __ldg(x + j0 + n);
+            acc.x = fmaf(c[n], xv.x, acc.x);
+            acc.y = fmaf(c[n], xv.y, acc.y);
+        }
+    } else {
+#pragma unroll
+        for (int n = 0; n < LEARNED_TAPS; ++n) {
+            const int j = j0 + n;
+            if (j < 0 || j >= N) continue;
+            const float2 xv = __ldg(x + j);
+            acc.x = fmaf(c[n], xv.x, acc.x);
+            acc.y = fmaf(c[n], xv.y, acc.y);
+        }
+    }
+    return acc;
+}
+
+// The plan's interpolator (a uniform branch: one plan, one interpolator).
+__device__ __forceinline__ float2 interp_sample(const DevParams& p, const float2* __restrict__ x,
+                                                int jstar, float delta) {
+    return p.interp == CC_INTERP_LEARNED ? interp_learned(p, x, jstar, delta)
+                                         : interp_sinc(p, x, jstar, delta);
 }
 
 // Weights at detector time t/dt = j* + delta: alpha = a/sigma^2, beta = b/sigma^2,

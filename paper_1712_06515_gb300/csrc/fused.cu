@@ -235,7 +235,7 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
                         kr = rec[2 * qi + (k - (r0 >> 7))];
                     }
                     const SampleTiming st = sample_timing(p, kr, r, k * KNOT);
-                    const float2 xv = interp_sinc(p, x, st.jstar, st.delta);
+                    const float2 xv = interp_sample(p, x, st.jstar, st.delta);
                     float sn, cs;
                     sincospif(2.0f * st.psi, &sn, &cs);
                     const float2 xr = cmul(xv, make_float2(cs, sn));

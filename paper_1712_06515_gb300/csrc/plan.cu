@@ -107,6 +107,8 @@ void crosscorr_plan_destroy(cc_plan* p) {
     if (!p) return;
     for (void* d : p->dev_allocs) cudaFree(d);
     if (p->ws) cudaFree(p->ws);
+    if (p->learned_w) cudaFree(p->learned_w);
+    if (p->learned_taps) cudaFree(p->learned_taps);
     delete p;
 }
 
@@ -128,11 +130,8 @@ cc_status crosscorr_plan(const cc_config* cfg, const cc_detector* dets, cc_plan*
     if (c.pair_mode < 0 || c.pair_mode > 2) return fail(CC_ERR_INVALID, "pair_mode must be 0..2");
     if (c.store != CC_STORE_FP32 && c.store != CC_STORE_BF16)
         return fail(CC_ERR_INVALID, "store must be CC_STORE_FP32 or CC_STORE_BF16");
-    if (c.interp != CC_INTERP_EXACT) {
-        if (c.interp == CC_INTERP_LEARNED)
-            return fail(CC_ERR_UNSUPPORTED, "learned interpolation is not available in this build");
+    if (c.interp != CC_INTERP_EXACT && c.interp != CC_INTERP_LEARNED)
         return fail(CC_ERR_INVALID, "interp must be CC_INTERP_EXACT or CC_INTERP_LEARNED");
-    }
     int64_t nsft;
     if (!(c.T_sft > 0) || !is_int_multiple(c.T_sft, c.dt, &nsft) || nsft < 1)
         return fail(CC_ERR_INVALID, "T_sft must be a positive integer multiple of dt");
@@ -316,6 +315,8 @@ cc_status crosscorr_plan(const cc_config* cfg, const cc_detector* dets, cc_plan*
     dp.D = c.D;
     dp.pair_mode = c.pair_mode;
     dp.store = c.store;
+    dp.interp = c.interp;
+    dp.ltaps = nullptr;   // crosscorr_plan_set_learned_interp fills it
     dp.L = (int)L;
     dp.C = (int)C;
     dp.log2L = log2L;

@@ -85,7 +85,7 @@ resample_kernel(DevParams p, const cc_template* __restrict__ tm, int64_t t_base,
         const int64_t k = r / KNOT;
         const KnotRec kr = rec[k - kA];
         const SampleTiming st = sample_timing(p, kr, (int)r, (int)(k * KNOT));
-        const float2 xv = interp_sinc(p, x, st.jstar, st.delta);
+        const float2 xv = interp_sample(p, x, st.jstar, st.delta);
         float sn, cs;
         sincospif(2.0f * st.psi, &sn, &cs);
         const float2 xr = cmul(xv, make_float2(cs, sn));
@@ -321,6 +321,9 @@ size_t pair_workspace_bytes(const cc_plan* plan, int64_t n_t) {
 }
 
 cc_status set_inputs(cc_plan* plan, const void* const* x_dev) {
+    if (plan->dp.interp == CC_INTERP_LEARNED && !plan->dp.ltaps)
+        return fail(CC_ERR_INVALID, "learned interpolation weights not set: call "
+                                    "crosscorr_plan_set_learned_interp first");
     if (!x_dev) return fail(CC_ERR_INVALID, "x_dev is null");
     for (int q = 0; q < plan->Q; ++q) {
         if (!x_dev[q]) return fail(CC_ERR_INVALID, "x_dev[" + std::to_string(q) + "] is null");
