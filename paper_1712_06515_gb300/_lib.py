@@ -20,7 +20,8 @@ BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "lib")
 LIBPATH = os.path.join(LIBDIR, "libcrosscorr.so")
 
-SOURCES = ["plan.cu", "stages.cu", "search.cu", "topk.cu", "fused.cu", "noalloc.cu", "learned.cu"]
+SOURCES = ["plan.cu", "stages.cu", "search.cu", "topk.cu", "fused.cu", "fused_l64_256.cu", "fused_l512_1024.cu",
+           "fused_l2048.cu", "fused_l4096.cu", "noalloc.cu", "learned.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 

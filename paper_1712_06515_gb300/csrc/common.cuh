@@ -86,6 +86,8 @@ struct FusedLayout {
     int log2CL;        // CL is a power of two
     int bothw;         // Q <= 2: both weights' transforms buffered, one pair pass per coset
     int regacc;        // one coset per CTA with few bins: pair sums in registers
+    int regpair;       // pair sums formed in registers from the last FFT pass (see fused_kernel)
+    int mmax;          // largest transform position m of any output bin
     int64_t chunk_len; // segments per chunk
     int n_chunks;
     size_t off_slice, slice_bytes;   // [2][Q][2][S] float2

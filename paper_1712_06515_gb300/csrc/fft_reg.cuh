@@ -220,3 +220,37 @@ __device__ __forceinline__ void stockham_rest_t(float2* buf, int j, const float2
 }
 
 }  // namespace cc
+
+namespace cc {
+
+// Radix of the last Stockham pass for an L-point transform whose first pass is radix 16
+// and whose later passes are radix 16 while at least four bits remain.
+__host__ __device__ constexpr int last_radix(int L) {
+    return (ilog2c(L) - 4) % 4 == 0 ? 16 : 1 << ((ilog2c(L) - 4) % 4);
+}
+
+// As stockham_rest_t, but the last pass leaves its outputs in registers instead of the
+// buffer: thread j < L / last_radix(L) gets outputs j + (L / last_radix(L)) r in v[r],
+// r < last_radix(L).  Nothing is written to `buf` by the last pass and no barrier
+// follows it; the caller orders any later writes to `buf`.
+template <int L, int NS, typename Sync>
+__device__ __forceinline__ void stockham_rest_keep_t(float2* buf, int j, const float2* __restrict__ twL,
+                                                     Sync sync, float2 (&v)[16]) {
+    constexpr int rem = ilog2c(L) - ilog2c(NS);
+    static_assert(rem >= 1, "at least one pass after the first");
+    if constexpr (rem > 4) {
+        stockham_pass_t<16, L, NS>(buf, j, twL, sync);
+        stockham_rest_keep_t<L, NS * 16>(buf, j, twL, sync, v);
+    } else {
+        constexpr int R = 1 << rem;
+        static_assert(NS * R == L, "last pass");
+        if (j < NS) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = buf[padi(j + r * NS)];
+            apply_twiddles<R>(v, twL, j, L - 1);
+            dft_r<R>(v);
+        }
+    }
+}
+
+}  // namespace cc

@@ -86,14 +86,14 @@ def test_learned_resample_stage_parity():
             assert np.abs(ab[t, q, 1] - b)[ok].max() <= 2e-5 * scale
 
 
-def test_learned_staged_equals_search_and_noalloc():
+def test_learned_staged_equals_search():
     ds = synth.tiny(seed=31, n_templates=3, injection=INJ)
     with cc.CrossCorrPlan(ds.cfg, ds.dets, interp=cc.INTERP_LEARNED) as plan:
         x, tm = dev_inputs(ds)
         fused = plan.search(x, tm)
         ab, nrm = plan.resample(x, tm)
-        F = plan.segment_fft(ab)
-        staged = plan.pair_accumulate(F, nrm)
+        F = plan.segment_fft(ab, tm.shape[0])
+        staged = plan.pair_accumulate(F, nrm, tm.shape[0])
         torch.cuda.synchronize()
         f, s = fused.cpu().numpy(), staged.cpu().numpy()
     lim = 1e-4 * max(1.0, float(np.abs(f).max()))

@@ -69,6 +69,12 @@ CASES = {
     "D16": dict(D=16),
     "ragged": dict(n_samples=4096 + 77),
     "short_series": dict(n_samples=300, T_sft=32.0, T_max=64.0, T_short=64.0),
+    # coset lengths 512 / 1024 / 2048: last FFT passes of radix 2 / 4 / 8
+    "L512": dict(T_max=512.0, T_short=512.0),
+    "L1024": dict(n_samples=8192, T_max=1024.0, T_short=1024.0),
+    "L2048": dict(n_samples=16384, T_max=2048.0, T_short=2048.0),
+    "L2048_cross_only": dict(n_samples=16384, T_max=2048.0, T_short=2048.0, pair_mode=1),
+    "L1024_Q3": dict(n_samples=8192, T_max=1024.0, T_short=1024.0, n_det=3),
 }
 
 
