@@ -74,6 +74,7 @@ constexpr int FUSED_THREADS = 512;
 constexpr int FUSED_WARPS = FUSED_THREADS / 32;
 constexpr int MAX_CLUSTER = 8;
 constexpr int ACC_SLOTS = 4;   // register pair-sum accumulators per thread (bins per coset <= 2048)
+constexpr int SEGACT_DEPTH = 4;   // ring of per-segment detector-activity flags in the fused kernel
 
 // Shared-memory layout and work split of the fused kernel (byte offsets).
 struct FusedLayout {
@@ -100,7 +101,7 @@ struct FusedLayout {
     size_t off_wpart;                // [2][FUSED_WARPS][Q][4] float
     size_t off_nring;                // [R+1][Q] float4 (rank 0)
     size_t off_bins;                 // [nb] int2 (m, k) and [ncos+1] int starts
-    size_t off_flags;                // [2][CC_MAX_DET] int: detector has weight in the segment
+    size_t off_flags;                // [SEGACT_DEPTH][CC_MAX_DET] int: detector has weight in a segment
     size_t bytes;
 };
 

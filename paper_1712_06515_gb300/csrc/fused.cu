@@ -77,7 +77,7 @@ bool fused_layout(const cc_plan* plan, int64_t n_t, FusedLayout* lay) {
     lay->off_bins = o;
     o = al16(o + (size_t)lay->nb * sizeof(int2) + (ncos_max + 1) * sizeof(int));
     lay->off_flags = o;
-    o = al16(o + (size_t)2 * CC_MAX_DET * sizeof(int));
+    o = al16(o + (size_t)SEGACT_DEPTH * CC_MAX_DET * sizeof(int));
     lay->bytes = o;
     if (lay->bytes > 227 * 1024) return false;
     if (p.L > 4096 || p.L < 64) return false;   // one radix-16 butterfly per thread per pass

@@ -78,7 +78,8 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
     float* wpart = (float*)(sm + lay.off_wpart);
     float4* nring = (float4*)(sm + lay.off_nring);
     int2* bins = (int2*)(sm + lay.off_bins);
-    int* segact = (int*)(sm + lay.off_flags);   // [2][CC_MAX_DET]: detector has weight in the segment
+    // [SEGACT_DEPTH][CC_MAX_DET]: detector has weight in segment K (slot (K - Kl) mod depth)
+    int* segact = (int*)(sm + lay.off_flags);
     int* cstart = (int*)(bins + nb);
 
     const cc_template T = tm[t];
@@ -204,9 +205,14 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
         if (blo > bhi) return 0;
         return __ldg(p.lockc[X] + bhi + 1) - __ldg(p.lockc[X] + blo) > 0 ? 1 : 0;
     };
+    // Flags are written two segments ahead (by warp X, after the cluster barrier of
+    // segment K for segment K + 2) so that a cluster barrier always separates a flag's
+    // write from its reads: the two halves of a CTA meet at no other barrier.
     if (warp < Q) {
-        const int a = seg_active(Kl, warp);
-        if (lane == 0) segact[warp] = a;
+        for (int64_t K = Kl; K < imin64(Kl + 2, Kb); ++K) {
+            const int a = seg_active(K, warp);
+            if (lane == 0) segact[(int)((K - Kl) & (SEGACT_DEPTH - 1)) * CC_MAX_DET + warp] = a;
+        }
     }
     __syncthreads();
 
@@ -220,6 +226,7 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
 
     for (int64_t K = Kl; K < Kb; ++K) {
         const int b = (int)((K - Kl) & 1);
+        const int sa_slot = (int)((K - Kl) & (SEGACT_DEPTH - 1));
         const int64_t seg0 = K * N_s;
         // (1) knot delays of the next segment (FP64, a few threads)
         if constexpr (!PREKNOTS)
@@ -229,7 +236,7 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
             const int nloc = nmyb * KNOT;
             for (int X = 0; X < Q; ++X) {
                 float A = 0.f, B = 0.f, Cn = 0.f;
-                const bool actX = segact[b * CC_MAX_DET + X] != 0;
+                const bool actX = segact[sa_slot * CC_MAX_DET + X] != 0;
                 const float2* __restrict__ x = p.x[X];
                 float2* sa = (float2*)slice_ptr(lay, sm, b, Q, X, 0);
                 float2* sb = (float2*)slice_ptr(lay, sm, b, Q, X, 1);
@@ -277,9 +284,9 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
         // (3) knot records of the next segment's slice
         if constexpr (!PREKNOTS)
             if (K + 1 < Kb) build_records(K + 1, b ^ 1);
-        if (K + 1 < Kb && warp < Q) {
-            const int a = seg_active(K + 1, warp);
-            if (lane == 0) segact[(b ^ 1) * CC_MAX_DET + warp] = a;
+        if (K + 2 < Kb && warp < Q) {
+            const int a = seg_active(K + 2, warp);
+            if (lane == 0) segact[(int)((K + 2 - Kl) & (SEGACT_DEPTH - 1)) * CC_MAX_DET + warp] = a;
         }
         // (4) segment norms and the normalisation (rank 0 holds D): one thread per
         //     (peer, detector, component) sums that peer's warp partials
@@ -341,7 +348,7 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
         const int offn = (int)((-seg0) & (int64_t)(L - 1));   // position p holds r - seg0 = (p + offn) mod L
         const int cur = R > 0 ? (int)(K % nslot) : 0;
         const int nround = (Q + 1) / 2;
-        const int* act = segact + b * CC_MAX_DET;
+        const int* act = segact + sa_slot * CC_MAX_DET;
         // gather + first radix-16 pass into registers, stored to `buf` for the later passes
         auto first_pass = [&](int X, int w, float2* buf, const float2* __restrict__ twr) {
             const float2* sbase = slice_ptr(lay, sm, b, Q, X, w);
@@ -470,6 +477,9 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
                     }
                 }
             }
+            // with knots computed in the cluster, the next segment's knot records (built
+            // by all threads above) are read by both halves in the next resampling pass
+            if constexpr (!PREKNOTS) __syncthreads();
         } else
         for (int j = 0; j < ncos; ++j) {
             const int c = rank + j * CL;

@@ -302,3 +302,26 @@ def test_o1_band_full_size_injected_template():
         x = torch.from_numpy(ds.x64).to(DEV)
         got = plan.search(x, torch.from_numpy(tm).to(DEV)).cpu().numpy().astype(np.float64)
     assert_rho_close(got, ref)
+
+
+def test_fused_search_is_deterministic_on_full_size_chunked_batch():
+    """Race check: the fused kernel's halves and cluster peers meet only at barriers, so a
+    chunked full-size batch (long gaps, segments with inactive detectors) gives the same
+    bits every run and agrees with the staged path (no shared-memory hand-offs) to
+    rounding, batched or one template at a time."""
+    ds = synth.o1_band(n_ap=1, n_tasc=1)
+    inj = ds.injection
+    tm = np.array([[inj.a_p, inj.T_asc, inj.P], [1.40, inj.T_asc - 200.0, inj.P],
+                   [1.52, inj.T_asc + 300.0, inj.P]])
+    with cc.CrossCorrPlan(ds.cfg, ds.dets) as plan:
+        x = torch.from_numpy(ds.x64).to(DEV)
+        tmd = torch.from_numpy(tm).to(DEV)
+        runs = [plan.search(x, tmd).cpu().numpy() for _ in range(4)]
+        singles = np.stack([plan.search(x, tmd[i:i + 1]).cpu().numpy()[0] for i in range(3)])
+        ab, nrm = plan.resample(x, tmd)
+        staged = plan.pair_accumulate(plan.segment_fft(ab, 3), nrm, 3).cpu().numpy()
+    for r in runs[1:]:
+        assert np.array_equal(r, runs[0])
+    lim = 1e-5 * max(1.0, float(np.abs(staged).max()))
+    assert np.abs(runs[0] - staged).max() <= lim
+    assert np.abs(singles - staged).max() <= lim
