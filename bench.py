@@ -223,6 +223,8 @@ def run_gpu(args):
         dist.barrier()
     clocks = ClockSampler(local)
     clocks.start()
+    plan.kernel_time()            # clear
+    plan.set_kernel_timing(True)  # event pair around every fused-kernel launch, same stream
     n0 = lib.crosscorr_kernel_launches()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -232,6 +234,8 @@ def run_gpu(args):
     ev1.record(stream)
     torch.cuda.synchronize()
     launches = lib.crosscorr_kernel_launches() - n0
+    plan.set_kernel_timing(False)
+    fused_ms, fused_launches = plan.kernel_time()
     clk = clocks.stop()
     elapsed = ev0.elapsed_time(ev1) / 1000.0
     if dist:
@@ -283,16 +287,19 @@ def run_gpu(args):
     out = None
     if rank == 0:
         costs = algorithmic_costs(info, Q, 1, ds.cfg.D, learned)
-        # the fused kernel is the step (plus a finalize pass of N_f floats per template):
-        # FP32-ALU roofline from the SM count, FP32 lanes and the maximum SM clock
-        fl = costs["total_flops"] * B
-        achieved = fl / (elapsed / args.steps) / 1e12
+        # the fused kernel dominates the step (the knot pre-pass and the final normalisation
+        # pass are the rest): its algorithmic flops over its own event-timed launches,
+        # against the FP32-ALU roofline from the SM count, FP32 lanes and the maximum SM clock
+        fl = costs["total_flops"] * B * args.steps
+        achieved = fl / (fused_ms / 1e3) / 1e12
         clk_max = float((clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0))
         peak = SM_COUNT * FP32_LANES * 2 * clk_max * 1e6 / 1e12
         roof = {"bound": "alu", "kernel": "fused_kernel", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                 "peak_kind": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 flop x {clk_max:g} MHz",
                 "flops_per_template": costs["total_flops"],
+                "kernel_ms_per_launch": fused_ms / max(fused_launches, 1),
+                "kernel_launches": fused_launches, "kernel_share_of_step": fused_ms / (1e3 * elapsed),
                 "staged_ms_per_template": stage_ms}
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

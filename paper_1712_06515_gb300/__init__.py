@@ -202,6 +202,16 @@ class CrossCorrPlan:
             self._h, xp, _dptr(templates), n_t, _dptr(rho), _stream_handle(stream)))
         return rho
 
+    def set_kernel_timing(self, on: bool = True):
+        """Diagnostic: bracket each fused-kernel launch with CUDA events on its stream."""
+        check("crosscorr_plan_set_kernel_timing", self._lib.crosscorr_plan_set_kernel_timing(self._h, int(on)))
+
+    def kernel_time(self):
+        """(total ms, launches) of the fused-kernel launches timed since the last call."""
+        ms, n = c_double(), c_int64()
+        check("crosscorr_plan_kernel_time", self._lib.crosscorr_plan_kernel_time(self._h, byref(ms), byref(n)))
+        return ms.value, n.value
+
     def topk(self, rho, k, stream=None):
         """k best (template, bin, freq, rho), descending, ties by (template, bin)."""
         import torch

@@ -126,6 +126,8 @@ SIGNATURES = {
     "crosscorr_status_string": (ctypes.c_char_p, [c_int]),
     "crosscorr_last_error": (ctypes.c_char_p, []),
     "crosscorr_kernel_launches": (ctypes.c_uint64, []),
+    "crosscorr_plan_set_kernel_timing": (c_int, [c_void_p, c_int]),
+    "crosscorr_plan_kernel_time": (c_int, [c_void_p, POINTER(c_double), POINTER(c_int64)]),
 }
 
 _LIB = None

@@ -123,6 +123,10 @@ struct cc_plan {
     // learned interpolator: device weights (BF16 bits) and tap table, once set
     uint16_t* learned_w = nullptr;
     float* learned_taps = nullptr;
+    // diagnostic event pairs around fused-kernel launches (crosscorr_plan_set_kernel_timing)
+    bool kernel_timing = false;
+    std::vector<cudaEvent_t> timing_events;   // [2 * n] start, stop
+    size_t timing_used = 0;                   // pairs recorded since the last read
     // workspace (grown on demand by staged/fused paths)
     void* ws = nullptr;
     size_t ws_bytes = 0;
@@ -143,6 +147,8 @@ cc_status launch_fused(cc_plan* plan, const cc_template* t_dev, int64_t n_t, flo
                        KnotRec* kn_ws = nullptr, int64_t kn_batch = 0);
 int64_t knot_rows(const cc_plan* plan);
 void count_launch(uint64_t n = 1);
+// Event pair for the next timed fused launch (nullptrs when timing is off or fails).
+void timing_pair(cc_plan* plan, cudaEvent_t* start, cudaEvent_t* stop);
 
 // ---------------------------------------------------------------------------
 // Device helpers

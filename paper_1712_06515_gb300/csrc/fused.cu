@@ -172,8 +172,12 @@ cc_status launch_fused(cc_plan* plan, const cc_template* t_dev, int64_t n_t, flo
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
+        cudaEvent_t ev0, ev1;
+        timing_pair(plan, &ev0, &ev1);
+        if (ev0) cudaEventRecord(ev0, st);
         e = launch_dispatch(p.L, cfg, pre, lay.regpair != 0, p, lay, t_dev, tb, raw, dpart, kn_ws, nkn);
         count_launch();
+        if (ev1) cudaEventRecord(ev1, st);
         if (e != cudaSuccess) return cuda_fail(e, "fused launch");
         dim3 g2((unsigned)launch_blocks_for(p.N_f, 256), (unsigned)nt);
         finalize_kernel<<<g2, 256, 0, st>>>(raw, dpart, p.N_f, lay.n_chunks, tb, rho);

@@ -83,6 +83,24 @@ int launch_blocks_for(int64_t n, int threads) { return (int)((n + threads - 1) /
 static std::atomic<uint64_t> g_launches{0};
 void count_launch(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+void timing_pair(cc_plan* plan, cudaEvent_t* start, cudaEvent_t* stop) {
+    *start = *stop = nullptr;
+    if (!plan->kernel_timing) return;
+    if (2 * plan->timing_used + 2 > plan->timing_events.size()) {
+        cudaEvent_t e[2];
+        if (cudaEventCreate(&e[0]) != cudaSuccess) return;
+        if (cudaEventCreate(&e[1]) != cudaSuccess) {
+            cudaEventDestroy(e[0]);
+            return;
+        }
+        plan->timing_events.push_back(e[0]);
+        plan->timing_events.push_back(e[1]);
+    }
+    *start = plan->timing_events[2 * plan->timing_used];
+    *stop = plan->timing_events[2 * plan->timing_used + 1];
+    ++plan->timing_used;
+}
+
 }  // namespace cc
 
 extern "C" {
@@ -103,10 +121,34 @@ const char* crosscorr_last_error(void) { return g_last_error.c_str(); }
 
 uint64_t crosscorr_kernel_launches(void) { return cc::g_launches.load(); }
 
+cc_status crosscorr_plan_set_kernel_timing(cc_plan* plan, int on) {
+    if (!plan) return cc::fail(CC_ERR_INVALID, "plan is null");
+    plan->kernel_timing = on != 0;
+    return CC_OK;
+}
+
+cc_status crosscorr_plan_kernel_time(cc_plan* plan, double* ms, int64_t* launches) {
+    if (!plan || !ms || !launches) return cc::fail(CC_ERR_INVALID, "null argument to crosscorr_plan_kernel_time");
+    double tot = 0.0;
+    const size_t n = plan->timing_used;
+    plan->timing_used = 0;
+    for (size_t i = 0; i < n; ++i) {
+        cudaError_t e = cudaEventSynchronize(plan->timing_events[2 * i + 1]);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, plan->timing_events[2 * i], plan->timing_events[2 * i + 1]);
+        if (e != cudaSuccess) return cc::cuda_fail(e, "kernel timing events");
+        tot += t;
+    }
+    *ms = tot;
+    *launches = (int64_t)n;
+    return CC_OK;
+}
+
 void crosscorr_plan_destroy(cc_plan* p) {
     if (!p) return;
     for (void* d : p->dev_allocs) cudaFree(d);
     if (p->ws) cudaFree(p->ws);
+    for (cudaEvent_t e : p->timing_events) cudaEventDestroy(e);
     if (p->learned_w) cudaFree(p->learned_w);
     if (p->learned_taps) cudaFree(p->learned_taps);
     delete p;

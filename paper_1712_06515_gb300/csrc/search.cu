@@ -13,7 +13,7 @@ cc_status launch_norm_pairs(cc_plan* plan, const void* F, const float* norm, int
 size_t pair_workspace_bytes(const cc_plan* plan, int64_t n_t);
 
 constexpr size_t STAGED_WS_BUDGET = (size_t)6 << 30;
-constexpr size_t KNOT_WS_BUDGET = (size_t)2 << 30;
+constexpr size_t KNOT_WS_BUDGET = (size_t)8 << 30;
 
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 

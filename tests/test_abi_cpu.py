@@ -138,5 +138,8 @@ def test_entry_points_reject_null_plan(lib):
     assert lib.crosscorr_search(None, None, None, 1, None, None) == CC_ERR_INVALID
     hits = (_lib.CcHit * 1)()
     assert lib.crosscorr_rho_topk(None, None, 1, 1, hits, None) == CC_ERR_INVALID
+    assert lib.crosscorr_plan_set_kernel_timing(None, 1) == CC_ERR_INVALID
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    assert lib.crosscorr_plan_kernel_time(None, ctypes.byref(ms), ctypes.byref(n)) == CC_ERR_INVALID
     lib.crosscorr_plan_destroy(None)
     assert lib.crosscorr_status_string(3) == b"CUDA error"

@@ -325,3 +325,19 @@ def test_fused_search_is_deterministic_on_full_size_chunked_batch():
     lim = 1e-5 * max(1.0, float(np.abs(staged).max()))
     assert np.abs(runs[0] - staged).max() <= lim
     assert np.abs(singles - staged).max() <= lim
+
+
+def test_fused_kernel_timing_events():
+    ds = case_ds("default")
+    with cc.CrossCorrPlan(ds.cfg, ds.dets) as plan:
+        x, tm = dev_inputs(ds)
+        plan.search(x, tm)
+        assert plan.kernel_time() == (0.0, 0)       # off by default
+        plan.set_kernel_timing(True)
+        plan.search(x, tm)
+        plan.search(x, tm)
+        plan.set_kernel_timing(False)
+        plan.search(x, tm)
+        ms, n = plan.kernel_time()
+        assert n == 2 and ms > 0.0
+        assert plan.kernel_time() == (0.0, 0)       # cleared by the read
