@@ -230,6 +230,26 @@ cc_status crosscorr_search(cc_plan* plan, const void* const* x_dev, const cc_tem
 cc_status crosscorr_search_noalloc(cc_plan* plan, const void* const* x_dev, const cc_template* t_dev,
                                    int64_t n_t, float* rho_dev, void* stream);
 
+/* How crosscorr_search computes rho (all give the same rho to rounding):
+ *   CC_PATH_AUTO      the fastest path the plan supports (the default): TWO_PASS, else
+ *                     FUSED, else STAGED;
+ *   CC_PATH_FUSED     one kernel per template batch: a thread-block cluster resamples
+ *                     each segment into shared memory and transforms it on chip; needs
+ *                     a few MB of workspace (FP32 storage, coset length <= 4096);
+ *   CC_PATH_TWO_PASS  a_r, b_r of a template batch written to HBM (up to 24 GB of
+ *                     workspace), then one CTA per (coset, weight) transforms each
+ *                     segment and folds it into the pair sum on chip (FP32 storage,
+ *                     Q <= 2, R <= 1, not CC_PAIRS_CROSS_ONLY, coset length <= 4096);
+ *   CC_PATH_STAGED    the three stage kernels with spectra in HBM (any plan). */
+enum { CC_PATH_AUTO = 0, CC_PATH_FUSED = 1, CC_PATH_TWO_PASS = 2, CC_PATH_STAGED = 3 };
+
+/* Select the path of crosscorr_search (CC_ERR_INVALID for an unknown value,
+ * CC_ERR_UNSUPPORTED if the plan does not fit it). */
+cc_status crosscorr_plan_set_path(cc_plan* plan, int path);
+
+/* The path crosscorr_search takes for this plan (never CC_PATH_AUTO). */
+cc_status crosscorr_plan_search_path(const cc_plan* plan, int* path);
+
 /* The k largest rho over (template, bin) of a device float[n_t][N_f] array,
  * descending, ties by (template, bin) ascending; hits_host receives
  * min(k, n_t*N_f) records.  Synchronises the stream.  1 <= k <= 4096. */

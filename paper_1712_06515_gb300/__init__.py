@@ -23,6 +23,7 @@ __all__ = ["CrossCorrPlan", "CrossCorrError", "PAIR_UNORDERED", "PAIR_CROSS_ONLY
 PAIR_UNORDERED, PAIR_CROSS_ONLY, PAIR_ALL_ORDERED = 0, 1, 2
 STORE_FP32, STORE_BF16 = 0, 1
 INTERP_EXACT, INTERP_LEARNED = 0, 1
+PATH_AUTO, PATH_FUSED, PATH_TWO_PASS, PATH_STAGED = 0, 1, 2, 3
 
 build = _lib.build
 load = _lib.load
@@ -201,6 +202,17 @@ class CrossCorrPlan:
         check("crosscorr_search", self._lib.crosscorr_search(
             self._h, xp, _dptr(templates), n_t, _dptr(rho), _stream_handle(stream)))
         return rho
+
+    def set_path(self, path: int):
+        """How search() computes rho: PATH_AUTO, PATH_FUSED, PATH_TWO_PASS or PATH_STAGED."""
+        check("crosscorr_plan_set_path", self._lib.crosscorr_plan_set_path(self._h, int(path)))
+
+    @property
+    def search_path(self) -> int:
+        """The path search() takes (PATH_FUSED, PATH_TWO_PASS or PATH_STAGED)."""
+        v = ctypes.c_int()
+        check("crosscorr_plan_search_path", self._lib.crosscorr_plan_search_path(self._h, byref(v)))
+        return v.value
 
     def set_kernel_timing(self, on: bool = True):
         """Diagnostic: bracket each fused-kernel launch with CUDA events on its stream."""

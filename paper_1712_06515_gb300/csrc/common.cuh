@@ -123,6 +123,7 @@ struct cc_plan {
     // learned interpolator: device weights (BF16 bits) and tap table, once set
     uint16_t* learned_w = nullptr;
     float* learned_taps = nullptr;
+    int search_path = CC_PATH_AUTO;           // crosscorr_plan_set_path
     // diagnostic event pairs around fused-kernel launches (crosscorr_plan_set_kernel_timing)
     bool kernel_timing = false;
     std::vector<cudaEvent_t> timing_events;   // [2 * n] start, stop

@@ -254,3 +254,55 @@ __device__ __forceinline__ void stockham_rest_keep_t(float2* buf, int j, const f
 }
 
 }  // namespace cc
+
+namespace cc {
+
+// One out-of-place Stockham pass (src -> dst, both padded); no barrier inside: the
+// caller synchronises before dst is read or src rewritten.
+template <int R, int L, int NS>
+__device__ __forceinline__ void stockham_pass_oop_t(const float2* src, float2* dst, int j,
+                                                    const float2* __restrict__ twL) {
+    constexpr int B = L / R;
+    if (j < B) {
+        float2 v[16];
+        const int k = j & (NS - 1);
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = src[padi(j + r * B)];
+        if constexpr (NS > 1) apply_twiddles<R>(v, twL, k * (L / (NS * R)), L - 1);
+        dft_r<R>(v);
+        const int idxD = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[padi(idxD + r * NS)] = v[r];
+    }
+}
+
+// Passes after the first, out of place (a -> b -> a ...), the last one into registers as
+// in stockham_rest_keep_t: one barrier per intermediate pass instead of two.
+template <int L, int NS, typename Sync>
+__device__ __forceinline__ void stockham_pp_keep_t(float2* a, float2* b, int j, const float2* __restrict__ twL,
+                                                   Sync sync, float2 (&v)[16]) {
+    constexpr int rem = ilog2c(L) - ilog2c(NS);
+    static_assert(rem >= 1, "at least one pass after the first");
+    if constexpr (rem > 4) {
+        stockham_pass_oop_t<16, L, NS>(a, b, j, twL);
+        sync();
+        stockham_pp_keep_t<L, NS * 16>(b, a, j, twL, sync, v);
+    } else {
+        constexpr int R = 1 << rem;
+        static_assert(NS * R == L, "last pass");
+        if (j < NS) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = a[padi(j + r * NS)];
+            apply_twiddles<R>(v, twL, j, L - 1);
+            dft_r<R>(v);
+        }
+    }
+}
+
+// Number of intermediate passes of stockham_pp_keep_t after a radix-16 first pass; the
+// register pass reads the first buffer when it is even.
+__host__ __device__ constexpr int pp_intermediate_passes(int L) {
+    return (ilog2c(L) - 4 - 1) / 4;
+}
+
+}  // namespace cc

@@ -11,6 +11,8 @@ cc_status launch_segfft(cc_plan* plan, const void* ab, int64_t n_t, void* F, cud
 cc_status launch_norm_pairs(cc_plan* plan, const void* F, const float* norm, int64_t n_t, double* Dws,
                             float* rawws, float* rho, cudaStream_t st);
 size_t pair_workspace_bytes(const cc_plan* plan, int64_t n_t);
+bool two_pass_supported(const cc_plan* plan);
+cc_status search_two_pass(cc_plan* plan, const cc_template* t_dev, int64_t n_t, float* rho, cudaStream_t st);
 
 constexpr size_t STAGED_WS_BUDGET = (size_t)6 << 30;
 constexpr size_t KNOT_WS_BUDGET = (size_t)8 << 30;
@@ -30,7 +32,38 @@ static void staged_batch(const cc_plan* p, int64_t n_t, int64_t* batch, size_t* 
     *bytes = (align256(ab * b) + align256(F * b) + align256(nm * b) + align256(pair_workspace_bytes(p, b)));
 }
 
+static bool fused_supported(const cc_plan* plan) {
+    FusedLayout lay;
+    return plan->cfg.store == CC_STORE_FP32 && fused_layout(plan, 1, &lay);
+}
+
+static int resolve_path(const cc_plan* plan) {
+    if (plan->search_path != CC_PATH_AUTO) return plan->search_path;
+    if (two_pass_supported(plan)) return CC_PATH_TWO_PASS;
+    if (fused_supported(plan)) return CC_PATH_FUSED;
+    return CC_PATH_STAGED;
+}
+
 }  // namespace cc
+
+extern "C" cc_status crosscorr_plan_set_path(cc_plan* plan, int path) {
+    using namespace cc;
+    if (!plan) return fail(CC_ERR_INVALID, "plan is null");
+    if (path < CC_PATH_AUTO || path > CC_PATH_STAGED) return fail(CC_ERR_INVALID, "unknown search path");
+    if (path == CC_PATH_TWO_PASS && !two_pass_supported(plan))
+        return fail(CC_ERR_UNSUPPORTED, "plan does not fit the two-pass path");
+    if (path == CC_PATH_FUSED && !fused_supported(plan))
+        return fail(CC_ERR_UNSUPPORTED, "plan does not fit the fused path");
+    plan->search_path = path;
+    return CC_OK;
+}
+
+extern "C" cc_status crosscorr_plan_search_path(const cc_plan* plan, int* path) {
+    using namespace cc;
+    if (!plan || !path) return fail(CC_ERR_INVALID, "null argument to crosscorr_plan_search_path");
+    *path = resolve_path(plan);
+    return CC_OK;
+}
 
 extern "C" cc_status crosscorr_search(cc_plan* plan, const void* const* x_dev, const cc_template* t_dev,
                                       int64_t n_t, float* rho_dev, void* stream) {
@@ -42,11 +75,13 @@ extern "C" cc_status crosscorr_search(cc_plan* plan, const void* const* x_dev, c
     cc_status s = set_inputs(plan, x_dev);
     if (s != CC_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
+    const int path = resolve_path(plan);
+    if (path == CC_PATH_TWO_PASS) return search_two_pass(plan, t_dev, n_t, rho_dev, st);
     FusedLayout lay;
     // knot records from the pre-pass, up to KNOT_WS_BUDGET bytes of them per batch
     const size_t krow = (size_t)plan->Q * knot_rows(plan) * sizeof(KnotRec);
     const int64_t kbatch = std::max<int64_t>(1, std::min<int64_t>(n_t, (int64_t)(KNOT_WS_BUDGET / krow)));
-    if (plan->cfg.store == CC_STORE_FP32 && fused_layout(plan, kbatch, &lay)) {
+    if (path == CC_PATH_FUSED && fused_layout(plan, kbatch, &lay)) {
         // raw partial sums go straight into rho when there is one chunk per template
         const size_t dbytes = align256((size_t)n_t * lay.n_chunks * sizeof(double));
         const size_t rbytes = lay.n_chunks > 1 ? align256((size_t)n_t * lay.n_chunks * plan->N_f * sizeof(float)) : 0;

@@ -1,0 +1,299 @@
+// Two-pass search: the resampling kernel writes the weighted source-frame series a_r, b_r
+// of a template batch to HBM, then segpair_kernel forms every segment's spectrum on chip
+// (one coset and one weight per CTA) and folds it straight into the pair sum.
+//
+// Compared with the one-pass cluster kernel this needs no thread-block cluster (whose
+// 8-CTA placement leaves 32 of the 152 SMs idle), no distributed shared-memory gathers
+// and no cluster barrier per segment; the price is one write and one read of a_r, b_r
+// per template (about 0.1 ms of HBM time at the 120-day workload), with the eight coset
+// CTAs of a segment reading the same rows back-to-back from L2.
+//
+// Pair sum (Sec. III B 1, Eq. final-formatted-rho) as in the cluster kernel's register
+// form: with S = F_0 + F_1 this segment's detector sum and P the previous segment's
+// (R = 1), the weight-w term of a bin is Re(conj(S) P) + Re(conj(F_1) F_0) for the
+// unordered pair set, 2 Re(conj(S) P) + |S|^2 with auto-correlation included.
+#include <algorithm>
+
+#include "common.cuh"
+#include "fft_reg.cuh"
+
+namespace cc {
+
+cc_status launch_resample(cc_plan* plan, const cc_template* t_dev, int64_t n_t, void* ab, float* norm,
+                          cudaStream_t st);
+cc_status launch_norm(cc_plan* plan, const float* norm, int64_t n_t, double* Dws, cudaStream_t st);
+cc_status launch_pair_finalize(cc_plan* plan, const float* raw, const double* Dws, int n_rows, int64_t n_t,
+                               float* rho, cudaStream_t st);
+
+constexpr int SP_THREADS = 256;
+constexpr size_t TWO_PASS_WS_BUDGET = (size_t)24 << 30;   // a_r, b_r of one template batch
+
+struct SegPairLayout {
+    int nb;             // largest coset bin list
+    int mmax;           // largest transform position of any bin
+    int n_chunks;       // segment chunks per (template, weight, coset)
+    int pad_;
+    int64_t chunk_len;  // segments per chunk
+    size_t off_fft;     // [2][padded L] float2: out-of-place transform buffers
+    size_t off_h;       // [L/2] float2: detector 0's kept outputs (thread-private slots)
+    size_t off_bins;    // [nb] int2 (m, k)
+    size_t bytes;
+};
+
+// grid: x = coset c, y = weight w * n_chunks + chunk, z = template within the batch.
+// ab: [n_t][Q][2][N_tau] complex64, norm: [n_t][Q][M] (hat-A, hat-B, hat-C, 0),
+// raw: [n_t][2 * n_chunks][N_f] partial pair sums.
+template <int LT>
+__global__ void __launch_bounds__(SP_THREADS, 2)
+segpair_kernel(DevParams p, SegPairLayout lay, const float2* __restrict__ ab, const float4* __restrict__ norm,
+               float* __restrict__ raw) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    constexpr int L = LT;
+    constexpr int PL = padded_len(L);
+    constexpr int B1 = L / 16;                  // butterflies of the first (radix-16) pass
+    constexpr int RLAST = last_radix(L);
+    constexpr int NSL = L / RLAST;              // threads holding outputs after the last pass
+    constexpr int SLP = RLAST / 2 > 0 ? RLAST / 2 : 1;   // outputs per thread with m < L/2
+    constexpr bool KEEP_READS_A = pp_intermediate_passes(L) % 2 == 0;
+    static_assert(B1 <= SP_THREADS && NSL <= SP_THREADS, "one butterfly per thread per pass");
+
+    const int c = blockIdx.x;
+    const int w = blockIdx.y / lay.n_chunks, chunk = blockIdx.y % lay.n_chunks;
+    const int64_t t = blockIdx.z;
+    const int tid = threadIdx.x, Q = p.Q;
+    const int64_t N_s = p.N_s, R = p.R, M = p.M, N_tau = p.N_tau;
+    const int64_t Ka = (int64_t)chunk * lay.chunk_len;
+    const int64_t Kb = imin64(M, Ka + lay.chunk_len);
+    const int64_t Kl = imax64(0, Ka - R);
+
+    float2* A = (float2*)(sm + lay.off_fft);
+    float2* Bf = A + PL;
+    float2* H = (float2*)(sm + lay.off_h);
+    int2* bins = (int2*)(sm + lay.off_bins);
+    const int o = __ldg(p.coset_off + c), nbc = __ldg(p.coset_off + c + 1) - o;
+    for (int i = tid; i < nbc; i += SP_THREADS)
+        bins[i] = make_int2(__ldg(p.coset_m + o + i), __ldg(p.coset_k + o + i));
+
+    float accP[SLP], cmpP[SLP];
+    float2 prevP[SLP];
+#pragma unroll
+    for (int r = 0; r < SLP; ++r) {
+        accP[r] = cmpP[r] = 0.f;
+        prevP[r] = make_float2(0.f, 0.f);
+    }
+    const uint64_t N = (uint64_t)p.N_FFT, mask = N - 1;
+    const uint64_t bc = ((uint64_t)p.b0 + (uint64_t)c) & mask;
+    const float2* __restrict__ twr = p.twc + (size_t)c * N_s;
+    const float4* __restrict__ nt = norm + (size_t)t * Q * M;
+    const float2* __restrict__ abt = ab + (size_t)t * Q * 2 * N_tau;
+    auto sync = []() { __syncthreads(); };
+
+    // segment of detector X, weight w: sample r - seg0 goes to position (r - seg0 + seg0) mod L
+    // (absolute r: the segment-start phase is part of the transform) times the coset
+    // twiddle; first radix-16 pass in registers, stored to buf
+    auto first_pass = [&](int X, int64_t seg0, float2* buf) {
+        const float2* __restrict__ row = abt + ((size_t)X * 2 + w) * N_tau + seg0;
+        const int offn = (int)((-seg0) & (int64_t)(L - 1));
+        if (tid < B1) {
+            float2 v[16];
+            if (N_s <= L) {
+                float2 vv[16], tw[16];
+#pragma unroll
+                for (int r = 0; r < 16; ++r) {
+                    const int rr = (tid + r * B1 + offn) & (L - 1);
+                    const bool in = rr < (int)N_s;
+                    vv[r] = in ? __ldg(row + rr) : make_float2(0.f, 0.f);
+                    tw[r] = in ? __ldg(twr + rr) : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int r = 0; r < 16; ++r) v[r] = cmul(vv[r], tw[r]);
+            } else {
+#pragma unroll
+                for (int r = 0; r < 16; ++r) {
+                    float2 acc = make_float2(0.f, 0.f);
+                    for (int rr = (tid + r * B1 + offn) & (L - 1); rr < (int)N_s; rr += L)
+                        acc = cadd(acc, cmul(__ldg(row + rr), __ldg(twr + rr)));
+                    v[r] = acc;
+                }
+            }
+            dft16(v);
+#pragma unroll
+            for (int r = 0; r < 16; ++r) buf[padi(tid * 16 + r)] = v[r];
+        }
+        __syncthreads();
+    };
+
+    for (int64_t K = Kl; K < Kb; ++K) {
+        const int64_t seg0 = K * N_s;
+        const float2 wseg = twiddle_N((bc * ((uint64_t)seg0 & mask)) & mask, N);
+        // a detector with no weight in the segment (all gaps) has F = 0
+        const float4 n0 = nt[K], nl = nt[(size_t)(Q - 1) * M + K];
+        const bool a0 = n0.x + n0.y > 0.f, al = nl.x + nl.y > 0.f;
+        float2 v[16];
+        if (Q > 1 && a0) {
+            first_pass(0, seg0, A);
+            stockham_pp_keep_t<L, 16>(A, Bf, tid, p.twL, sync, v);
+            if (tid < NSL) {
+#pragma unroll
+                for (int r = 0; r < SLP; ++r)
+                    if (tid + NSL * r <= lay.mmax) H[r * NSL + tid] = v[r];
+            }
+            if constexpr (KEEP_READS_A) __syncthreads();
+        }
+        if (al) {
+            first_pass(Q - 1, seg0, A);
+            stockham_pp_keep_t<L, 16>(A, Bf, tid, p.twL, sync, v);
+        }
+        if (tid < NSL) {
+            const float2 wc = make_float2(wseg.x, -wseg.y);
+            const bool acc_on = K >= Ka;
+#pragma unroll
+            for (int r = 0; r < SLP; ++r) {
+                const int m = tid + NSL * r;
+                if (m <= lay.mmax) {
+                    const float2 Fl = al ? v[r] : make_float2(0.f, 0.f);
+                    float2 F0 = Fl, F1 = make_float2(0.f, 0.f);
+                    if (Q > 1) {
+                        F0 = a0 ? H[r * NSL + tid] : make_float2(0.f, 0.f);
+                        F1 = Fl;
+                    }
+                    const float2 S = cadd(F0, F1);
+                    const float2 P = R > 0 ? cmul(prevP[r], wc) : make_float2(0.f, 0.f);
+                    const float term = p.pair_mode == CC_PAIRS_ALL_ORDERED ? fmaf(2.f, redot(S, P), redot(S, S))
+                                                                           : redot(S, P) + redot(F1, F0);
+                    if (acc_on) kahan_add(accP[r], cmpP[r], term);
+                    if (R > 0) prevP[r] = cmul(S, wseg);
+                }
+            }
+        }
+        // with no intermediate pass the register pass read buffer A, which the next
+        // segment's first pass rewrites
+        if constexpr (KEEP_READS_A) __syncthreads();
+    }
+    // partial sums of this (template, weight, chunk) row for the coset's bins
+    __syncthreads();
+    float* accm = (float*)A;
+    if (tid < NSL) {
+#pragma unroll
+        for (int r = 0; r < SLP; ++r)
+            if (tid + NSL * r <= lay.mmax) accm[tid + NSL * r] = accP[r];
+    }
+    __syncthreads();
+    float* outp = raw + ((size_t)t * 2 * lay.n_chunks + (size_t)w * lay.n_chunks + chunk) * p.N_f;
+    for (int i = tid; i < nbc; i += SP_THREADS) outp[bins[i].y] = accm[bins[i].x];
+}
+
+static size_t al16(size_t b) { return (b + 15) & ~(size_t)15; }
+static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Whether the plan fits the two-pass kernel: Q <= 2, R <= 1, no cross-only pair set,
+// coset length 64..4096, every bin in the lower half of its coset transform, FP32 series.
+bool segpair_layout(const cc_plan* plan, int64_t n_t, SegPairLayout* lay) {
+    const DevParams& p = plan->dp;
+    if (plan->cfg.store != CC_STORE_FP32) return false;
+    if (p.Q > 2 || p.R > 1 || p.pair_mode == CC_PAIRS_CROSS_ONLY) return false;
+    if (p.L < 64 || p.L > 4096 || plan->N_f < 1) return false;
+    lay->mmax = (int)((plan->kbar.back() - plan->k0) / p.C);
+    if (2 * lay->mmax >= p.L) return false;
+    int nb = 1;
+    for (int c = 0; c < p.C; ++c) nb = std::max(nb, plan->coset_off[c + 1] - plan->coset_off[c]);
+    lay->nb = nb;
+    size_t o = 0;
+    lay->off_fft = o;
+    o = al16(o + (size_t)2 * padded_len(p.L) * sizeof(float2));
+    lay->off_h = o;
+    o = al16(o + (size_t)(p.L / 2) * sizeof(float2));
+    lay->off_bins = o;
+    o = al16(o + (size_t)nb * sizeof(int2));
+    lay->bytes = o;
+    if (lay->bytes > 113 * 1024) return false;   // two CTAs per SM
+    // chunks: about ten waves of two CTAs per SM, each chunk at least 4R + 1 segments
+    const int64_t ctas = (int64_t)p.C * 2 * n_t;
+    const int64_t want = std::max<int64_t>(1, (10 * 2 * 152 + ctas - 1) / std::max<int64_t>(ctas, 1));
+    const int64_t maxch = std::max<int64_t>(1, p.M / (4 * p.R + 1));
+    const int64_t nch = std::min<int64_t>({want, maxch, 32767});
+    lay->chunk_len = (p.M + nch - 1) / nch;
+    lay->n_chunks = (int)((p.M + lay->chunk_len - 1) / lay->chunk_len);
+    return true;
+}
+
+template <int LT>
+static cudaError_t launch_segpair_lt(dim3 grid, size_t smem, cudaStream_t st, const DevParams& p,
+                                     const SegPairLayout& lay, const float2* ab, const float4* norm, float* raw) {
+    cudaError_t e = cudaFuncSetAttribute(segpair_kernel<LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    segpair_kernel<LT><<<grid, SP_THREADS, smem, st>>>(p, lay, ab, norm, raw);
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_segpair(const DevParams& p, const SegPairLayout& lay, int64_t n_t, const float2* ab,
+                                  const float4* norm, float* raw, cudaStream_t st) {
+    const dim3 grid((unsigned)p.C, (unsigned)(2 * lay.n_chunks), (unsigned)n_t);
+    switch (p.L) {
+        case 64: return launch_segpair_lt<64>(grid, lay.bytes, st, p, lay, ab, norm, raw);
+        case 128: return launch_segpair_lt<128>(grid, lay.bytes, st, p, lay, ab, norm, raw);
+        case 256: return launch_segpair_lt<256>(grid, lay.bytes, st, p, lay, ab, norm, raw);
+        case 512: return launch_segpair_lt<512>(grid, lay.bytes, st, p, lay, ab, norm, raw);
+        case 1024: return launch_segpair_lt<1024>(grid, lay.bytes, st, p, lay, ab, norm, raw);
+        case 2048: return launch_segpair_lt<2048>(grid, lay.bytes, st, p, lay, ab, norm, raw);
+        case 4096: return launch_segpair_lt<4096>(grid, lay.bytes, st, p, lay, ab, norm, raw);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// Template batch of the two-pass search and the workspace it needs.
+static void two_pass_batch(const cc_plan* plan, int64_t n_t, const SegPairLayout& lay, int64_t* batch,
+                           size_t* bytes) {
+    const size_t per_ab = (size_t)plan->Q * 2 * plan->N_tau * sizeof(float2);
+    int64_t b = (int64_t)std::max<size_t>(1, TWO_PASS_WS_BUDGET / per_ab);
+    b = std::min<int64_t>({b, n_t, 65535});
+    *batch = b;
+    *bytes = al256(per_ab * b) + al256((size_t)plan->Q * plan->M * sizeof(float4) * b) +
+             al256((size_t)b * sizeof(double)) + al256((size_t)b * 2 * lay.n_chunks * plan->N_f * sizeof(float));
+}
+
+bool two_pass_supported(const cc_plan* plan) {
+    SegPairLayout lay;
+    return segpair_layout(plan, 1, &lay);
+}
+
+cc_status search_two_pass(cc_plan* plan, const cc_template* t_dev, int64_t n_t, float* rho, cudaStream_t st) {
+    SegPairLayout lay;
+    const size_t per_ab = (size_t)plan->Q * 2 * plan->N_tau * sizeof(float2);
+    const int64_t b0 = std::min<int64_t>({(int64_t)std::max<size_t>(1, TWO_PASS_WS_BUDGET / per_ab), n_t, 65535});
+    if (!segpair_layout(plan, b0, &lay)) return fail(CC_ERR_UNSUPPORTED, "plan does not fit the two-pass kernel");
+    int64_t batch;
+    size_t bytes;
+    two_pass_batch(plan, n_t, lay, &batch, &bytes);
+    cc_status s = ensure_workspace(plan, bytes);
+    if (s != CC_OK) return s;
+    char* w = (char*)plan->ws;
+    float2* ab = (float2*)w;
+    w += al256(per_ab * batch);
+    float* nrm = (float*)w;
+    w += al256((size_t)plan->Q * plan->M * sizeof(float4) * batch);
+    double* D = (double*)w;
+    w += al256((size_t)batch * sizeof(double));
+    float* raw = (float*)w;
+    const DevParams& p = plan->dp;
+    for (int64_t t0 = 0; t0 < n_t; t0 += batch) {
+        const int64_t nb = std::min(batch, n_t - t0);
+        SegPairLayout lb;
+        segpair_layout(plan, nb, &lb);   // chunking for this batch size (workspace sized for the largest)
+        if (lb.n_chunks > lay.n_chunks) lb = lay;
+        if ((s = launch_resample(plan, t_dev + t0, nb, ab, nrm, st)) != CC_OK) return s;
+        if ((s = launch_norm(plan, nrm, nb, D, st)) != CC_OK) return s;
+        cudaEvent_t ev0, ev1;
+        timing_pair(plan, &ev0, &ev1);
+        if (ev0) cudaEventRecord(ev0, st);
+        cudaError_t e = launch_segpair(p, lb, nb, ab, (const float4*)nrm, raw, st);
+        count_launch();
+        if (ev1) cudaEventRecord(ev1, st);
+        if (e != cudaSuccess) return cuda_fail(e, "segpair launch");
+        if ((s = launch_pair_finalize(plan, raw, D, 2 * lb.n_chunks, nb, rho + t0 * plan->N_f, st)) != CC_OK)
+            return s;
+    }
+    return CC_OK;
+}
+
+}  // namespace cc

@@ -313,6 +313,32 @@ cc_status launch_norm_pairs(cc_plan* plan, const void* F, const float* norm, int
     return e == cudaSuccess ? CC_OK : cuda_fail(e, "pair launch");
 }
 
+// D per template from the segment norms (t_base.. t_base + n_t - 1 of `norm`)
+cc_status launch_norm(cc_plan* plan, const float* norm, int64_t n_t, double* Dws, cudaStream_t st) {
+    const DevParams& p = plan->dp;
+    for (int64_t t0 = 0; t0 < n_t; t0 += MAX_GRID_YZ) {
+        const int64_t nt = std::min<int64_t>(MAX_GRID_YZ, n_t - t0);
+        norm_kernel<<<(unsigned)nt, 256, 0, st>>>(p, (const float4*)norm, t0, Dws);
+        count_launch();
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? CC_OK : cuda_fail(e, "norm launch");
+}
+
+// rho = sqrt(2) (sum of n_rows partial rows per template) / sqrt(D)
+cc_status launch_pair_finalize(cc_plan* plan, const float* raw, const double* Dws, int n_rows, int64_t n_t,
+                               float* rho, cudaStream_t st) {
+    const DevParams& p = plan->dp;
+    for (int64_t t0 = 0; t0 < n_t; t0 += MAX_GRID_YZ) {
+        const int64_t nt = std::min<int64_t>(MAX_GRID_YZ, n_t - t0);
+        dim3 g2((unsigned)launch_blocks_for(p.N_f, 256), (unsigned)nt);
+        pair_finalize_kernel<<<g2, 256, 0, st>>>(raw, Dws, p.N_f, n_rows, t0, rho);
+        count_launch();
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? CC_OK : cuda_fail(e, "finalize launch");
+}
+
 size_t pair_workspace_bytes(const cc_plan* plan, int64_t n_t) {
     const int64_t nch = pair_chunks(plan->dp, n_t);
     const int64_t clen = (plan->M + nch - 1) / nch;

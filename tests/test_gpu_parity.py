@@ -95,6 +95,36 @@ def test_search_parity(name):
     assert_rho_close(got, ref)
 
 
+@pytest.mark.parametrize("name", ["default", "T_max0", "Q1", "all_ordered", "ragged", "L512", "L2048"])
+@pytest.mark.parametrize("path", ["fused", "two_pass", "staged"])
+def test_search_paths_parity(name, path):
+    """Every search path on plans that all three support, against the oracle."""
+    ds = case_ds(name)
+    ref = oracle.rho(ds)
+    with cc.CrossCorrPlan(ds.cfg, ds.dets) as plan:
+        assert plan.search_path == cc.PATH_TWO_PASS
+        plan.set_path({"fused": cc.PATH_FUSED, "two_pass": cc.PATH_TWO_PASS, "staged": cc.PATH_STAGED}[path])
+        x, tm = dev_inputs(ds)
+        got = plan.search(x, tm).cpu().numpy().astype(np.float64)
+    assert_rho_close(got, ref)
+
+
+def test_search_path_selection():
+    with cc.CrossCorrPlan(case_ds("Q3").cfg, case_ds("Q3").dets) as plan:
+        assert plan.search_path == cc.PATH_FUSED
+        with pytest.raises(cc.CrossCorrError) as e:
+            plan.set_path(cc.PATH_TWO_PASS)
+        assert e.value.status == 5
+        with pytest.raises(cc.CrossCorrError) as e:
+            plan.set_path(7)
+        assert e.value.status == 1
+        plan.set_path(cc.PATH_STAGED)
+        assert plan.search_path == cc.PATH_STAGED
+    ds = case_ds("default")
+    with cc.CrossCorrPlan(ds.cfg, ds.dets, store=cc.STORE_BF16) as plan:
+        assert plan.search_path == cc.PATH_STAGED
+
+
 def test_plan_bins_match_oracle():
     for name in ("default", "fband_005", "T_max0"):
         ds = case_ds(name)
@@ -300,8 +330,10 @@ def test_o1_band_full_size_injected_template():
     ref = oracle.rho(ds, templates=tm)
     with cc.CrossCorrPlan(ds.cfg, ds.dets) as plan:
         x = torch.from_numpy(ds.x64).to(DEV)
-        got = plan.search(x, torch.from_numpy(tm).to(DEV)).cpu().numpy().astype(np.float64)
-    assert_rho_close(got, ref)
+        for path in (cc.PATH_TWO_PASS, cc.PATH_FUSED):
+            plan.set_path(path)
+            got = plan.search(x, torch.from_numpy(tm).to(DEV)).cpu().numpy().astype(np.float64)
+            assert_rho_close(got, ref)
 
 
 def test_fused_search_is_deterministic_on_full_size_chunked_batch():
@@ -316,15 +348,18 @@ def test_fused_search_is_deterministic_on_full_size_chunked_batch():
     with cc.CrossCorrPlan(ds.cfg, ds.dets) as plan:
         x = torch.from_numpy(ds.x64).to(DEV)
         tmd = torch.from_numpy(tm).to(DEV)
-        runs = [plan.search(x, tmd).cpu().numpy() for _ in range(4)]
-        singles = np.stack([plan.search(x, tmd[i:i + 1]).cpu().numpy()[0] for i in range(3)])
         ab, nrm = plan.resample(x, tmd)
         staged = plan.pair_accumulate(plan.segment_fft(ab, 3), nrm, 3).cpu().numpy()
-    for r in runs[1:]:
-        assert np.array_equal(r, runs[0])
-    lim = 1e-5 * max(1.0, float(np.abs(staged).max()))
-    assert np.abs(runs[0] - staged).max() <= lim
-    assert np.abs(singles - staged).max() <= lim
+        del ab, nrm
+        lim = 1e-5 * max(1.0, float(np.abs(staged).max()))
+        for path in (cc.PATH_FUSED, cc.PATH_TWO_PASS):
+            plan.set_path(path)
+            runs = [plan.search(x, tmd).cpu().numpy() for _ in range(3)]
+            singles = np.stack([plan.search(x, tmd[i:i + 1]).cpu().numpy()[0] for i in range(3)])
+            for r in runs[1:]:
+                assert np.array_equal(r, runs[0]), path
+            assert np.abs(runs[0] - staged).max() <= lim, path
+            assert np.abs(singles - staged).max() <= lim, path
 
 
 def test_fused_kernel_timing_events():
