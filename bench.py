@@ -207,6 +207,7 @@ def run_gpu(args):
     learned = args.interp == "learned"
     plan = cc.CrossCorrPlan(ds.cfg, ds.dets, interp=cc.INTERP_LEARNED if learned else cc.INTERP_EXACT)
     Q, N_f = plan.Q, plan.N_f
+    path = plan.search_path
     x = torch.from_numpy(ds.x64).to(dev)
     tm = torch.from_numpy(tm_host).to(dev)
     rho = torch.empty((B, N_f), dtype=torch.float32, device=dev)
@@ -287,19 +288,26 @@ def run_gpu(args):
     out = None
     if rank == 0:
         costs = algorithmic_costs(info, Q, 1, ds.cfg.D, learned)
-        # the fused kernel dominates the step (the knot pre-pass and the final normalisation
-        # pass are the rest): its algorithmic flops over its own event-timed launches,
-        # against the FP32-ALU roofline from the SM count, FP32 lanes and the maximum SM clock
-        fl = costs["total_flops"] * B * args.steps
-        achieved = fl / (fused_ms / 1e3) / 1e12
+        # The dominant kernel of the step, timed with CUDA events around its own launches
+        # on the launching stream: on the two-pass path the segment-spectrum + pair-sum
+        # kernel (its algorithmic flops: FFT + pairs; resampling is the other kernel), on
+        # the fused path the one-pass kernel (all flops).  Against the FP32-ALU roofline
+        # from the SM count, FP32 lanes and the maximum SM clock.
+        if path == cc.PATH_TWO_PASS:
+            kname, kflops = "segpair_kernel", costs["fft_flops"] + costs["pair_flops"]
+        else:
+            kname, kflops = "fused_kernel", costs["total_flops"]
+        achieved = kflops * B * args.steps / (fused_ms / 1e3) / 1e12
         clk_max = float((clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0))
         peak = SM_COUNT * FP32_LANES * 2 * clk_max * 1e6 / 1e12
-        roof = {"bound": "alu", "kernel": "fused_kernel", "achieved": achieved, "peak": peak,
+        other_ms = max(0.0, 1e3 * elapsed - fused_ms) / (B * args.steps)
+        roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                 "peak_kind": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 flop x {clk_max:g} MHz",
-                "flops_per_template": costs["total_flops"],
+                "flops_per_template": kflops,
                 "kernel_ms_per_launch": fused_ms / max(fused_launches, 1),
                 "kernel_launches": fused_launches, "kernel_share_of_step": fused_ms / (1e3 * elapsed),
+                "other_kernels_ms_per_template": other_ms,
                 "staged_ms_per_template": stage_ms}
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -312,6 +320,9 @@ def run_gpu(args):
                        "N_f": N_f, "N_FFT": info["N_FFT"], "M": info["M"], "L": info["L"], "C": info["C"],
                        "l2": "inputs larger than L2 (2 x 83 MB complex64 series)",
                        "timing_precision": "f64 knots, f32 interpolation/FFT/pairs",
+                       "search_path": {cc.PATH_FUSED: "fused (one cluster kernel)",
+                                       cc.PATH_TWO_PASS: "two-pass (resample to HBM, then spectra + pairs)",
+                                       cc.PATH_STAGED: "staged"}[path],
                        "interp": ("learned 8-tap network (bf16 weights, tabulated taps)" if learned
                                   else f"windowed sinc, {2 * ds.cfg.D + 1} taps")},
             "roofline": roof,

@@ -115,6 +115,20 @@ knots_kernel(DevParams p, const cc_template* __restrict__ tm, int64_t t_base, in
 
 int64_t knot_rows(const cc_plan* plan) { return (plan->N_tau + KNOT - 1) / KNOT; }
 
+// Knot records of templates t_dev[0 .. n_t) into kn ([n_t][Q][knot_rows]).
+cc_status launch_knots(cc_plan* plan, const cc_template* t_dev, int64_t n_t, KnotRec* kn, cudaStream_t st) {
+    const DevParams& p = plan->dp;
+    const int64_t nkn = knot_rows(plan);
+    for (int64_t t0 = 0; t0 < n_t; t0 += 65535) {
+        const int64_t nt = std::min<int64_t>(65535, n_t - t0);
+        dim3 gk((unsigned)((nkn + 255) / 256), (unsigned)p.Q, (unsigned)nt);
+        knots_kernel<<<gk, 256, 0, st>>>(p, t_dev + t0, 0, nkn, kn + (size_t)t0 * p.Q * nkn);
+        count_launch();
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? CC_OK : cuda_fail(e, "knots launch");
+}
+
 #define CC_FOR_EACH_L(X) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096)
 
 CC_FOR_EACH_L(CC_FUSED_EXTERN)

@@ -6,7 +6,7 @@
 namespace cc {
 cc_status set_inputs(cc_plan* plan, const void* const* x_dev);
 cc_status launch_resample(cc_plan* plan, const cc_template* t_dev, int64_t n_t, void* ab, float* norm,
-                          cudaStream_t st);
+                          cudaStream_t st, const KnotRec* kn = nullptr, int64_t nkn = 0);
 cc_status launch_segfft(cc_plan* plan, const void* ab, int64_t n_t, void* F, cudaStream_t st);
 cc_status launch_norm_pairs(cc_plan* plan, const void* F, const float* norm, int64_t n_t, double* Dws,
                             float* rawws, float* rho, cudaStream_t st);

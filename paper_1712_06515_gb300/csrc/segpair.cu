@@ -20,8 +20,9 @@
 namespace cc {
 
 cc_status launch_resample(cc_plan* plan, const cc_template* t_dev, int64_t n_t, void* ab, float* norm,
-                          cudaStream_t st);
+                          cudaStream_t st, const KnotRec* kn = nullptr, int64_t nkn = 0);
 cc_status launch_norm(cc_plan* plan, const float* norm, int64_t n_t, double* Dws, cudaStream_t st);
+cc_status launch_knots(cc_plan* plan, const cc_template* t_dev, int64_t n_t, KnotRec* kn, cudaStream_t st);
 cc_status launch_pair_finalize(cc_plan* plan, const float* raw, const double* Dws, int n_rows, int64_t n_t,
                                float* rho, cudaStream_t st);
 
@@ -249,7 +250,8 @@ static void two_pass_batch(const cc_plan* plan, int64_t n_t, const SegPairLayout
     b = std::min<int64_t>({b, n_t, 65535});
     *batch = b;
     *bytes = al256(per_ab * b) + al256((size_t)plan->Q * plan->M * sizeof(float4) * b) +
-             al256((size_t)b * sizeof(double)) + al256((size_t)b * 2 * lay.n_chunks * plan->N_f * sizeof(float));
+             al256((size_t)b * sizeof(double)) + al256((size_t)b * 2 * lay.n_chunks * plan->N_f * sizeof(float)) +
+             al256((size_t)b * plan->Q * knot_rows(plan) * sizeof(KnotRec));
 }
 
 bool two_pass_supported(const cc_plan* plan) {
@@ -275,13 +277,17 @@ cc_status search_two_pass(cc_plan* plan, const cc_template* t_dev, int64_t n_t, 
     double* D = (double*)w;
     w += al256((size_t)batch * sizeof(double));
     float* raw = (float*)w;
+    w += al256((size_t)batch * 2 * lay.n_chunks * plan->N_f * sizeof(float));
+    KnotRec* kn = (KnotRec*)w;
+    const int64_t nkn = knot_rows(plan);
     const DevParams& p = plan->dp;
     for (int64_t t0 = 0; t0 < n_t; t0 += batch) {
         const int64_t nb = std::min(batch, n_t - t0);
         SegPairLayout lb;
         segpair_layout(plan, nb, &lb);   // chunking for this batch size (workspace sized for the largest)
         if (lb.n_chunks > lay.n_chunks) lb = lay;
-        if ((s = launch_resample(plan, t_dev + t0, nb, ab, nrm, st)) != CC_OK) return s;
+        if ((s = launch_knots(plan, t_dev + t0, nb, kn, st)) != CC_OK) return s;
+        if ((s = launch_resample(plan, t_dev + t0, nb, ab, nrm, st, kn, nkn)) != CC_OK) return s;
         if ((s = launch_norm(plan, nrm, nb, D, st)) != CC_OK) return s;
         cudaEvent_t ev0, ev1;
         timing_pair(plan, &ev0, &ev1);

@@ -50,41 +50,83 @@ __device__ __forceinline__ void segment_knot_range(const DevParams& p, int64_t s
     *kB = floor_div(seg0 + p.N_s - 1, KNOT) + 2;
 }
 
-// Stage 1: one block per (segment K, detector X, template t).
+// Stage 1: one block per (segment K, detector X, template t).  With `kn` (knot records
+// of the pre-pass, [n_t][Q][nkn]) the FP64 knots are not recomputed, and a segment whose
+// detector times all fall in gaps is skipped: its norms are written as zero and its
+// a_r, b_r are left unwritten (the two-pass search reads a segment only when its norms
+// are nonzero).  Without `kn` every sample is written.
 __global__ void __launch_bounds__(RS_THREADS)
 resample_kernel(DevParams p, const cc_template* __restrict__ tm, int64_t t_base, void* ab,
-                float4* __restrict__ norm) {
+                float4* __restrict__ norm, const KnotRec* __restrict__ kn, int64_t nkn) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float red[32];
+    __shared__ int active;
     const int64_t K = blockIdx.x;
     const int X = blockIdx.y;
     const int64_t t = t_base + blockIdx.z;
     const int64_t seg0 = K * p.N_s;
+    const int tid = threadIdx.x;
     int64_t kA, kB;
     segment_knot_range(p, seg0, &kA, &kB);
     const int nk = (int)(kB - kA + 1);
     KnotRec* rec = (KnotRec*)smem;
-    double* dk = (double*)(smem + sizeof(KnotRec) * nk);
+    const KnotRec* __restrict__ knX = kn ? kn + ((size_t)t * p.Q + X) * nkn : nullptr;
 
-    const cc_template T = tm[t];
-    const double tasc_rel = T.T_asc - p.t0;
-    const double invP = 1.0 / T.P;
-    for (int i = threadIdx.x; i < nk; i += blockDim.x)
-        dk[i] = knot_delay(p, X, T.a_p, tasc_rel, invP, (double)((kA + i) * KNOT) * p.dt);
-    __syncthreads();
-    for (int i = 1 + threadIdx.x; i < nk - 2; i += blockDim.x)
-        rec[i] = make_knot(p, dk[i - 1], dk[i], dk[i + 1], dk[i + 2], (double)((kA + i) * KNOT) * p.dt);
-    __syncthreads();
+    if (knX) {
+        // detector times of the segment lie within [seg0 - max d - 2, seg1 + 2 - min d]
+        // (d from the segment's knots; the cubic between knots stays within 1e-4 samples
+        // of them); weight only if a noise block there is locked
+        if (tid < 32) {
+            const int64_t ka = seg0 >> 7, kb = imin64(((seg0 + p.N_s - 1) >> 7) + 1, nkn - 1);
+            float dmin = 3.0e38f, dmax = -3.0e38f;
+            for (int64_t k = ka + tid; k <= kb; k += 32) {
+                const KnotRec kr = load_knot(knX + k);
+                const float d = (float)kr.N + kr.f;
+                dmin = fminf(dmin, d);
+                dmax = fmaxf(dmax, d);
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                dmin = fminf(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
+                dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+            }
+            if (tid == 0) {
+                const int tlo = (int)seg0 - (int)ceilf(dmax) - 2;
+                const int thi = (int)(seg0 + p.N_s) - (int)floorf(dmin) + 2;
+                int blo = floor_div32(tlo, p.nsft), bhi = floor_div32(thi, p.nsft);
+                const int ns = (int)p.n_sig[X];
+                blo = blo < 0 ? 0 : blo;
+                bhi = bhi > ns - 1 ? ns - 1 : bhi;
+                active = blo <= bhi && __ldg(p.lockc[X] + bhi + 1) - __ldg(p.lockc[X] + blo) > 0;
+            }
+        }
+        __syncthreads();
+        if (!active) {
+            if (tid == 0) norm[(t * p.Q + X) * p.M + K] = make_float4(0.f, 0.f, 0.f, 0.f);
+            return;
+        }
+    } else {
+        double* dk = (double*)(smem + sizeof(KnotRec) * nk);
+        const cc_template T = tm[t];
+        const double tasc_rel = T.T_asc - p.t0;
+        const double invP = 1.0 / T.P;
+        for (int i = tid; i < nk; i += blockDim.x)
+            dk[i] = knot_delay(p, X, T.a_p, tasc_rel, invP, (double)((kA + i) * KNOT) * p.dt);
+        __syncthreads();
+        for (int i = 1 + tid; i < nk - 2; i += blockDim.x)
+            rec[i] = make_knot(p, dk[i - 1], dk[i], dk[i + 1], dk[i + 2], (double)((kA + i) * KNOT) * p.dt);
+        __syncthreads();
+    }
 
     const float2* __restrict__ x = p.x[X];
     const int64_t sa = ((t * p.Q + X) * 2 + 0) * p.N_tau;
     const int64_t sb = sa + p.N_tau;
     float A = 0.f, B = 0.f, Cn = 0.f;
-    for (int64_t i = threadIdx.x; i < p.N_s; i += blockDim.x) {
-        const int64_t r = seg0 + i;
-        const int64_t k = r / KNOT;
-        const KnotRec kr = rec[k - kA];
-        const SampleTiming st = sample_timing(p, kr, (int)r, (int)(k * KNOT));
+    const int n_s = (int)p.N_s;
+    for (int i = tid; i < n_s; i += blockDim.x) {
+        const int r = (int)seg0 + i;
+        const int k = r >> 7;
+        const KnotRec kr = knX ? load_knot(knX + k) : rec[k - kA];
+        const SampleTiming st = sample_timing(p, kr, r, k * KNOT);
         const float2 xv = interp_sample(p, x, st.jstar, st.delta);
         float sn, cs;
         sincospif(2.0f * st.psi, &sn, &cs);
@@ -99,7 +141,7 @@ resample_kernel(DevParams p, const cc_template* __restrict__ tm, int64_t t_base,
     A = block_sum(A, red);
     B = block_sum(B, red);
     Cn = block_sum(Cn, red);
-    if (threadIdx.x == 0) norm[(t * p.Q + X) * p.M + K] = make_float4(A, B, Cn, 0.f);
+    if (tid == 0) norm[(t * p.Q + X) * p.M + K] = make_float4(A, B, Cn, 0.f);
 }
 
 // Stage 2: one block per (coset c, segment K, series s = (t*Q + X)*2 + w).
@@ -258,7 +300,7 @@ size_t resample_smem_bytes(const DevParams& p) {
 }
 
 cc_status launch_resample(cc_plan* plan, const cc_template* t_dev, int64_t n_t, void* ab,
-                          float* norm, cudaStream_t st) {
+                          float* norm, cudaStream_t st, const KnotRec* kn, int64_t nkn) {
     const DevParams& p = plan->dp;
     const size_t sm = resample_smem_bytes(p);
     if (sm > 48 * 1024) {
@@ -269,7 +311,7 @@ cc_status launch_resample(cc_plan* plan, const cc_template* t_dev, int64_t n_t, 
     for (int64_t t0 = 0; t0 < n_t; t0 += MAX_GRID_YZ) {
         const int64_t nt = std::min<int64_t>(MAX_GRID_YZ, n_t - t0);
         dim3 grid((unsigned)p.M, (unsigned)p.Q, (unsigned)nt);
-        resample_kernel<<<grid, RS_THREADS, sm, st>>>(p, t_dev, t0, ab, (float4*)norm);
+        resample_kernel<<<grid, RS_THREADS, sm, st>>>(p, t_dev, t0, ab, (float4*)norm, kn, nkn);
         count_launch();
     }
     cudaError_t e = cudaGetLastError();
@@ -372,7 +414,7 @@ cc_status crosscorr_resample(cc_plan* plan, const void* const* x_dev, const cc_t
     if (!t_dev || !ab_dev || !norm_dev) return fail(CC_ERR_INVALID, "null device pointer");
     cc_status s = set_inputs(plan, x_dev);
     if (s != CC_OK) return s;
-    return launch_resample(plan, t_dev, n_t, ab_dev, norm_dev, (cudaStream_t)stream);
+    return launch_resample(plan, t_dev, n_t, ab_dev, norm_dev, (cudaStream_t)stream, nullptr, 0);
 }
 
 cc_status crosscorr_segment_fft(cc_plan* plan, const void* ab_dev, int64_t n_t, void* F_dev,
