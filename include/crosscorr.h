@@ -236,10 +236,11 @@ cc_status crosscorr_search_noalloc(cc_plan* plan, const void* const* x_dev, cons
  *   CC_PATH_FUSED     one kernel per template batch: a thread-block cluster resamples
  *                     each segment into shared memory and transforms it on chip; needs
  *                     a few MB of workspace (FP32 storage, coset length <= 4096);
- *   CC_PATH_TWO_PASS  a_r, b_r of a template batch written to HBM (up to 24 GB of
- *                     workspace), then one CTA per (coset, weight) transforms each
- *                     segment and folds it into the pair sum on chip (FP32 storage,
- *                     Q <= 2, R <= 1, not CC_PAIRS_CROSS_ONLY, coset length <= 4096);
+ *   CC_PATH_TWO_PASS  a_r, b_r of a template batch written to HBM in the plan's
+ *                     storage type (up to 24 GB of workspace), then one CTA per
+ *                     (coset, weight) transforms each segment and folds it into the
+ *                     pair sum on chip (Q <= 2, R <= 1, not CC_PAIRS_CROSS_ONLY, coset
+ *                     length >= 64, output bins in the lower half of each coset);
  *   CC_PATH_STAGED    the three stage kernels with spectra in HBM (any plan). */
 enum { CC_PATH_AUTO = 0, CC_PATH_FUSED = 1, CC_PATH_TWO_PASS = 2, CC_PATH_STAGED = 3 };
 

@@ -20,7 +20,7 @@ constexpr int MAX_D = 32;
 constexpr int MAX_TAPS = 2 * MAX_D + 1;
 constexpr int N_BIN_ITER = 4;   // fixed-point steps of the binary delay b = a_p sin(Omega (tau + b - T_asc))
 constexpr int N_SSB_ITER = 4;   // fixed-point steps of t = u - Delta(t)
-constexpr int MAX_L = 8192;     // largest on-chip coset FFT
+constexpr int MAX_L = 4096;     // largest coset FFT: 256 threads, one radix-16 butterfly each per pass
 
 // Learned interpolator: 8 taps from a 2 -> 64 -> 64 -> 8 tanh network, tabulated at
 // LEARNED_NODES offsets u = i / (LEARNED_NODES - 1) and interpolated linearly in u.
@@ -290,6 +290,22 @@ __device__ __forceinline__ SampleTiming sample_timing(const DevParams& p, const 
     return s;
 }
 
+// Windowed-sinc taps on xp[0 .. 2D] (sample j* - D first) at offset delta != 0: the sum
+// of xp[n] w_n sinc(delta - (n - D)), with sin(pi (delta - m)) = (-1)^m sin(pi delta).
+__device__ __forceinline__ float2 sinc_taps(const DevParams& p, const float2* __restrict__ xp, float delta) {
+    const int D = p.D;
+    const float s = sinpif(delta) * 0.318309886183790672f;   // sin(pi delta)/pi
+    float2 acc = make_float2(0.f, 0.f);
+    for (int n = 0; n <= 2 * D; ++n) {
+        const float dj = delta - (float)(n - D);              // (t - t_j)/dt
+        const float c = p.ham[n] * __fdividef(((n - D) & 1) ? -s : s, dj);
+        const float2 xv = xp[n];
+        acc.x = fmaf(c, xv.x, acc.x);
+        acc.y = fmaf(c, xv.y, acc.y);
+    }
+    return acc;
+}
+
 // Windowed-sinc interpolation (2D+1 taps) at t/dt = j* + delta of a complex series.
 __device__ __forceinline__ float2 interp_sinc(const DevParams& p, const float2* __restrict__ x,
                                               int jstar, float delta) {
@@ -298,30 +314,38 @@ __device__ __forceinline__ float2 interp_sinc(const DevParams& p, const float2* 
         return (jstar >= 0 && jstar < N) ? __ldg(x + jstar) : make_float2(0.f, 0.f);
     }
     const int D = p.D;
-    float s = sinpif(delta) * 0.318309886183790672f;   // sin(pi delta)/pi
-    float2 acc = make_float2(0.f, 0.f);
     const int j0 = jstar - D;
-    const float2* __restrict__ xp = x + j0;
-    if (j0 >= 0 && j0 + 2 * D < N) {
-        for (int n = 0; n <= 2 * D; ++n) {
-            float dj = delta - (float)(n - D);              // (t - t_j)/dt
-            float c = p.ham[n] * __fdividef(((n - D) & 1) ? -s : s, dj);
-            float2 xv = __ldg(xp + n);
-            acc.x = fmaf(c, xv.x, acc.x);
-            acc.y = fmaf(c, xv.y, acc.y);
-        }
-    } else {
-        for (int n = 0; n <= 2 * D; ++n) {
-            const int j = j0 + n;
-            if (j < 0 || j >= N) continue;
-            float dj = delta - (float)(n - D);
-            float c = p.ham[n] * __fdividef(((n - D) & 1) ? -s : s, dj);
-            float2 xv = __ldg(x + j);
-            acc.x = fmaf(c, xv.x, acc.x);
-            acc.y = fmaf(c, xv.y, acc.y);
-        }
+    if (j0 >= 0 && j0 + 2 * D < N) return sinc_taps(p, x + j0, delta);
+    const float s = sinpif(delta) * 0.318309886183790672f;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int n = 0; n <= 2 * D; ++n) {
+        const int j = j0 + n;
+        if (j < 0 || j >= N) continue;
+        const float dj = delta - (float)(n - D);
+        const float c = p.ham[n] * __fdividef(((n - D) & 1) ? -s : s, dj);
+        const float2 xv = __ldg(x + j);
+        acc.x = fmaf(c, xv.x, acc.x);
+        acc.y = fmaf(c, xv.y, acc.y);
     }
     return acc;
+}
+
+// Learned taps at offset u in [0, 1) from the tabulated network (linear in u).
+__device__ __forceinline__ void learned_coeffs(const DevParams& p, float u, float (&c)[LEARNED_TAPS]) {
+    const float fu = u * (float)(LEARNED_NODES - 1);
+    int i = (int)fu;
+    i = i > LEARNED_NODES - 2 ? LEARNED_NODES - 2 : i;
+    const float f = fu - (float)i;
+    const float4* tb = (const float4*)(p.ltaps + i * LEARNED_TAPS);
+    const float4 a0 = __ldg(tb), a1 = __ldg(tb + 1), n0 = __ldg(tb + 2), n1 = __ldg(tb + 3);
+    c[0] = fmaf(f, n0.x - a0.x, a0.x);
+    c[1] = fmaf(f, n0.y - a0.y, a0.y);
+    c[2] = fmaf(f, n0.z - a0.z, a0.z);
+    c[3] = fmaf(f, n0.w - a0.w, a0.w);
+    c[4] = fmaf(f, n1.x - a1.x, a1.x);
+    c[5] = fmaf(f, n1.y - a1.y, a1.y);
+    c[6] = fmaf(f, n1.z - a1.z, a1.z);
+    c[7] = fmaf(f, n1.w - a1.w, a1.w);
 }
 
 // Learned 8-tap interpolation at t/dt = j* + delta: taps from the tabulated network at
@@ -331,34 +355,17 @@ __device__ __forceinline__ float2 interp_learned(const DevParams& p, const float
     const int N = (int)p.N_t;
     const bool neg = delta < 0.0f;
     const int j0 = jstar - (neg ? 1 : 0) - LEARNED_TAP_OFFSET;
-    const float u = neg ? delta + 1.0f : delta;
-    const float fu = u * (float)(LEARNED_NODES - 1);
-    int i = (int)fu;
-    i = i > LEARNED_NODES - 2 ? LEARNED_NODES - 2 : i;
-    const float f = fu - (float)i;
-    const float4* tb = (const float4*)(p.ltaps + i * LEARNED_TAPS);
-    const float4 a0 = __ldg(tb), a1 = __ldg(tb + 1), n0 = __ldg(tb + 2), n1 = __ldg(tb + 3);
-    const float c[LEARNED_TAPS] = {fmaf(f, n0.x - a0.x, a0.x), fmaf(f, n0.y - a0.y, a0.y),
-                                   fmaf(f, n0.z - a0.z, a0.z), fmaf(f, n0.w - a0.w, a0.w),
-                                   fmaf(f, n1.x - a1.x, a1.x), fmaf(f, n1.y - a1.y, a1.y),
-                                   fmaf(f, n1.z - a1.z, a1.z), fmaf(f, n1.w - a1.w, a1.w)};
+    float c[LEARNED_TAPS];
+    learned_coeffs(p, neg ? delta + 1.0f : delta, c);
     float2 acc = make_float2(0.f, 0.f);
-    if (j0 >= 0 && j0 + LEARNED_TAPS <= N) {
+    const bool inside = j0 >= 0 && j0 + LEARNED_TAPS <= N;
 #pragma unroll
-        for (int n = 0; n < LEARNED_TAPS; ++n) {
-            const float2 xv = __ldg(x + j0 + n);
-            acc.x = fmaf(c[n], xv.x, acc.x);
-            acc.y = fmaf(c[n], xv.y, acc.y);
-        }
-    } else {
-#pragma unroll
-        for (int n = 0; n < LEARNED_TAPS; ++n) {
-            const int j = j0 + n;
-            if (j < 0 || j >= N) continue;
-            const float2 xv = __ldg(x + j);
-            acc.x = fmaf(c[n], xv.x, acc.x);
-            acc.y = fmaf(c[n], xv.y, acc.y);
-        }
+    for (int n = 0; n < LEARNED_TAPS; ++n) {
+        const int j = j0 + n;
+        if (!inside && (j < 0 || j >= N)) continue;
+        const float2 xv = __ldg(x + j);
+        acc.x = fmaf(c[n], xv.x, acc.x);
+        acc.y = fmaf(c[n], xv.y, acc.y);
     }
     return acc;
 }
@@ -368,6 +375,32 @@ __device__ __forceinline__ float2 interp_sample(const DevParams& p, const float2
                                                 int jstar, float delta) {
     return p.interp == CC_INTERP_LEARNED ? interp_learned(p, x, jstar, delta)
                                          : interp_sinc(p, x, jstar, delta);
+}
+
+// As interp_sample, reading from a shared-memory copy xs of samples [w0, w0 + nw) of the
+// series (zero outside [0, N_t)) when every tap falls inside it, else from x.
+__device__ __forceinline__ float2 interp_sample_window(const DevParams& p, const float2* __restrict__ x,
+                                                       const float2* xs, int w0, int nw, int jstar,
+                                                       float delta) {
+    if (p.interp == CC_INTERP_LEARNED) {
+        const bool neg = delta < 0.0f;
+        const int j0 = jstar - (neg ? 1 : 0) - LEARNED_TAP_OFFSET;
+        if (j0 < w0 || j0 + LEARNED_TAPS > w0 + nw) return interp_learned(p, x, jstar, delta);
+        float c[LEARNED_TAPS];
+        learned_coeffs(p, neg ? delta + 1.0f : delta, c);
+        const float2* xp = xs + (j0 - w0);
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int n = 0; n < LEARNED_TAPS; ++n) {
+            acc.x = fmaf(c[n], xp[n].x, acc.x);
+            acc.y = fmaf(c[n], xp[n].y, acc.y);
+        }
+        return acc;
+    }
+    const int j0 = jstar - p.D;
+    if (j0 < w0 || j0 + 2 * p.D >= w0 + nw) return interp_sinc(p, x, jstar, delta);
+    if (delta == 0.0f) return xs[jstar - w0];
+    return sinc_taps(p, xs + (j0 - w0), delta);
 }
 
 // Weights at detector time t/dt = j* + delta: alpha = a/sigma^2, beta = b/sigma^2,

@@ -13,6 +13,15 @@ namespace cc {
 __device__ __forceinline__ int padi(int p) { return p + (p >> 4); }
 __host__ __device__ constexpr int padded_len(int L) { return L + L / 16; }
 
+// Padded distance of S consecutive elements when S is a multiple of 16:
+// padi(a + r S) = padi(a) + r pstride<S>().
+template <int S>
+__host__ __device__ constexpr int pstride() {
+    static_assert(S % 16 == 0, "padded stride needs a multiple of 16");
+    return S + S / 16;
+}
+
+
 // cos(pi/8), sin(pi/8), sqrt(1/2)
 constexpr float kC8 = 0.923879532511286756f;
 constexpr float kS8 = 0.382683432365089772f;
@@ -190,16 +199,28 @@ __device__ __forceinline__ void stockham_pass_t(float2* buf, int j, const float2
     const bool act = j < B;
     const int k = j & (NS - 1);
     if (act) {
+        if constexpr (B % 16 == 0) {
+            const float2* s = buf + padi(j);
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = buf[padi(j + r * B)];
+            for (int r = 0; r < R; ++r) v[r] = s[r * pstride<B>()];
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = buf[padi(j + r * B)];
+        }
         if constexpr (NS > 1) apply_twiddles<R>(v, twL, k * (L / (NS * R)), L - 1);
         dft_r<R>(v);
     }
     sync();
     if (act) {
         const int idxD = (j - k) * R + k;
+        if constexpr (NS % 16 == 0) {
+            float2* d = buf + padi(idxD);
 #pragma unroll
-        for (int r = 0; r < R; ++r) buf[padi(idxD + r * NS)] = v[r];
+            for (int r = 0; r < R; ++r) d[r * pstride<NS>()] = v[r];
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) buf[padi(idxD + r * NS)] = v[r];
+        }
     }
     sync();
 }
@@ -266,13 +287,14 @@ __device__ __forceinline__ void stockham_pass_oop_t(const float2* src, float2* d
     if (j < B) {
         float2 v[16];
         const int k = j & (NS - 1);
+        const float2* s = src + padi(j);
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = src[padi(j + r * B)];
+        for (int r = 0; r < R; ++r) v[r] = s[r * pstride<B>()];
         if constexpr (NS > 1) apply_twiddles<R>(v, twL, k * (L / (NS * R)), L - 1);
         dft_r<R>(v);
-        const int idxD = (j - k) * R + k;
+        float2* d = dst + padi((j - k) * R + k);
 #pragma unroll
-        for (int r = 0; r < R; ++r) dst[padi(idxD + r * NS)] = v[r];
+        for (int r = 0; r < R; ++r) d[r * pstride<NS>()] = v[r];
     }
 }
 
@@ -291,8 +313,9 @@ __device__ __forceinline__ void stockham_pp_keep_t(float2* a, float2* b, int j, 
         constexpr int R = 1 << rem;
         static_assert(NS * R == L, "last pass");
         if (j < NS) {
+            const float2* s = a + padi(j);
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[r] = a[padi(j + r * NS)];
+            for (int r = 0; r < R; ++r) v[r] = s[r * pstride<NS>()];
             apply_twiddles<R>(v, twL, j, L - 1);
             dft_r<R>(v);
         }

@@ -42,11 +42,11 @@ struct SegPairLayout {
 };
 
 // grid: x = coset c, y = weight w * n_chunks + chunk, z = template within the batch.
-// ab: [n_t][Q][2][N_tau] complex64, norm: [n_t][Q][M] (hat-A, hat-B, hat-C, 0),
+// ab: [n_t][Q][2][N_tau] complex64 (bf16 pairs with BF16 storage), norm: [n_t][Q][M] (hat-A, hat-B, hat-C, 0),
 // raw: [n_t][2 * n_chunks][N_f] partial pair sums.
 template <int LT>
 __global__ void __launch_bounds__(SP_THREADS, 2)
-segpair_kernel(DevParams p, SegPairLayout lay, const float2* __restrict__ ab, const float4* __restrict__ norm,
+segpair_kernel(DevParams p, SegPairLayout lay, const void* __restrict__ ab, const float4* __restrict__ norm,
                float* __restrict__ raw) {
     extern __shared__ __align__(16) unsigned char sm[];
     constexpr int L = LT;
@@ -86,24 +86,30 @@ segpair_kernel(DevParams p, SegPairLayout lay, const float2* __restrict__ ab, co
     const uint64_t bc = ((uint64_t)p.b0 + (uint64_t)c) & mask;
     const float2* __restrict__ twr = p.twc + (size_t)c * N_s;
     const float4* __restrict__ nt = norm + (size_t)t * Q * M;
-    const float2* __restrict__ abt = ab + (size_t)t * Q * 2 * N_tau;
+    const size_t abt = (size_t)t * Q * 2 * N_tau;   // element offset of this template's rows
+    const bool bf16 = p.store == CC_STORE_BF16;
+    auto load_ab = [&](size_t i) -> float2 {
+        return bf16 ? __bfloat1622float2(((const __nv_bfloat162*)ab)[i]) : __ldg((const float2*)ab + i);
+    };
     auto sync = []() { __syncthreads(); };
 
     // segment of detector X, weight w: sample r - seg0 goes to position (r - seg0 + seg0) mod L
     // (absolute r: the segment-start phase is part of the transform) times the coset
     // twiddle; first radix-16 pass in registers, stored to buf
     auto first_pass = [&](int X, int64_t seg0, float2* buf) {
-        const float2* __restrict__ row = abt + ((size_t)X * 2 + w) * N_tau + seg0;
+        const size_t row = abt + ((size_t)X * 2 + w) * N_tau + seg0;
         const int offn = (int)((-seg0) & (int64_t)(L - 1));
         if (tid < B1) {
             float2 v[16];
             if (N_s <= L) {
                 float2 vv[16], tw[16];
+                const float2* rowf = (const float2*)ab + row;
+                const __nv_bfloat162* rowh = (const __nv_bfloat162*)ab + row;
 #pragma unroll
                 for (int r = 0; r < 16; ++r) {
                     const int rr = (tid + r * B1 + offn) & (L - 1);
                     const bool in = rr < (int)N_s;
-                    vv[r] = in ? __ldg(row + rr) : make_float2(0.f, 0.f);
+                    vv[r] = !in ? make_float2(0.f, 0.f) : bf16 ? __bfloat1622float2(rowh[rr]) : __ldg(rowf + rr);
                     tw[r] = in ? __ldg(twr + rr) : make_float2(0.f, 0.f);
                 }
 #pragma unroll
@@ -113,13 +119,14 @@ segpair_kernel(DevParams p, SegPairLayout lay, const float2* __restrict__ ab, co
                 for (int r = 0; r < 16; ++r) {
                     float2 acc = make_float2(0.f, 0.f);
                     for (int rr = (tid + r * B1 + offn) & (L - 1); rr < (int)N_s; rr += L)
-                        acc = cadd(acc, cmul(__ldg(row + rr), __ldg(twr + rr)));
+                        acc = cadd(acc, cmul(load_ab(row + rr), __ldg(twr + rr)));
                     v[r] = acc;
                 }
             }
             dft16(v);
+            float2* d = buf + 17 * tid;   // padi(16 tid + r) = 17 tid + r
 #pragma unroll
-            for (int r = 0; r < 16; ++r) buf[padi(tid * 16 + r)] = v[r];
+            for (int r = 0; r < 16; ++r) d[r] = v[r];
         }
         __syncthreads();
     };
@@ -188,10 +195,9 @@ static size_t al16(size_t b) { return (b + 15) & ~(size_t)15; }
 static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // Whether the plan fits the two-pass kernel: Q <= 2, R <= 1, no cross-only pair set,
-// coset length 64..4096, every bin in the lower half of its coset transform, FP32 series.
+// coset length 64..4096, every bin in the lower half of its coset transform.
 bool segpair_layout(const cc_plan* plan, int64_t n_t, SegPairLayout* lay) {
     const DevParams& p = plan->dp;
-    if (plan->cfg.store != CC_STORE_FP32) return false;
     if (p.Q > 2 || p.R > 1 || p.pair_mode == CC_PAIRS_CROSS_ONLY) return false;
     if (p.L < 64 || p.L > 4096 || plan->N_f < 1) return false;
     lay->mmax = (int)((plan->kbar.back() - plan->k0) / p.C);
@@ -220,14 +226,14 @@ bool segpair_layout(const cc_plan* plan, int64_t n_t, SegPairLayout* lay) {
 
 template <int LT>
 static cudaError_t launch_segpair_lt(dim3 grid, size_t smem, cudaStream_t st, const DevParams& p,
-                                     const SegPairLayout& lay, const float2* ab, const float4* norm, float* raw) {
+                                     const SegPairLayout& lay, const void* ab, const float4* norm, float* raw) {
     cudaError_t e = cudaFuncSetAttribute(segpair_kernel<LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     segpair_kernel<LT><<<grid, SP_THREADS, smem, st>>>(p, lay, ab, norm, raw);
     return cudaGetLastError();
 }
 
-static cudaError_t launch_segpair(const DevParams& p, const SegPairLayout& lay, int64_t n_t, const float2* ab,
+static cudaError_t launch_segpair(const DevParams& p, const SegPairLayout& lay, int64_t n_t, const void* ab,
                                   const float4* norm, float* raw, cudaStream_t st) {
     const dim3 grid((unsigned)p.C, (unsigned)(2 * lay.n_chunks), (unsigned)n_t);
     switch (p.L) {
@@ -245,7 +251,7 @@ static cudaError_t launch_segpair(const DevParams& p, const SegPairLayout& lay, 
 // Template batch of the two-pass search and the workspace it needs.
 static void two_pass_batch(const cc_plan* plan, int64_t n_t, const SegPairLayout& lay, int64_t* batch,
                            size_t* bytes) {
-    const size_t per_ab = (size_t)plan->Q * 2 * plan->N_tau * sizeof(float2);
+    const size_t per_ab = (size_t)plan->Q * 2 * plan->N_tau * (plan->cfg.store == CC_STORE_BF16 ? 4 : 8);
     int64_t b = (int64_t)std::max<size_t>(1, TWO_PASS_WS_BUDGET / per_ab);
     b = std::min<int64_t>({b, n_t, 65535});
     *batch = b;
@@ -261,7 +267,7 @@ bool two_pass_supported(const cc_plan* plan) {
 
 cc_status search_two_pass(cc_plan* plan, const cc_template* t_dev, int64_t n_t, float* rho, cudaStream_t st) {
     SegPairLayout lay;
-    const size_t per_ab = (size_t)plan->Q * 2 * plan->N_tau * sizeof(float2);
+    const size_t per_ab = (size_t)plan->Q * 2 * plan->N_tau * (plan->cfg.store == CC_STORE_BF16 ? 4 : 8);
     const int64_t b0 = std::min<int64_t>({(int64_t)std::max<size_t>(1, TWO_PASS_WS_BUDGET / per_ab), n_t, 65535});
     if (!segpair_layout(plan, b0, &lay)) return fail(CC_ERR_UNSUPPORTED, "plan does not fit the two-pass kernel");
     int64_t batch;
@@ -270,7 +276,7 @@ cc_status search_two_pass(cc_plan* plan, const cc_template* t_dev, int64_t n_t, 
     cc_status s = ensure_workspace(plan, bytes);
     if (s != CC_OK) return s;
     char* w = (char*)plan->ws;
-    float2* ab = (float2*)w;
+    void* ab = w;
     w += al256(per_ab * batch);
     float* nrm = (float*)w;
     w += al256((size_t)plan->Q * plan->M * sizeof(float4) * batch);

@@ -50,6 +50,12 @@ __device__ __forceinline__ void segment_knot_range(const DevParams& p, int64_t s
     *kB = floor_div(seg0 + p.N_s - 1, KNOT) + 2;
 }
 
+// Longest shared-memory window of x a resampling block stages: the segment, the drift
+// of the delay across it (|d'| < 2.5e-4 for the Earth and a binary orbit) and the taps.
+__host__ __device__ inline int resample_window_len(const DevParams& p) {
+    return (int)(p.N_s + p.N_s / 512 + 2 * (p.D > 4 ? p.D : 4) + 48);
+}
+
 // Stage 1: one block per (segment K, detector X, template t).  With `kn` (knot records
 // of the pre-pass, [n_t][Q][nkn]) the FP64 knots are not recomputed, and a segment whose
 // detector times all fall in gaps is skipped: its norms are written as zero and its
@@ -57,7 +63,7 @@ __device__ __forceinline__ void segment_knot_range(const DevParams& p, int64_t s
 // are nonzero).  Without `kn` every sample is written.
 __global__ void __launch_bounds__(RS_THREADS)
 resample_kernel(DevParams p, const cc_template* __restrict__ tm, int64_t t_base, void* ab,
-                float4* __restrict__ norm, const KnotRec* __restrict__ kn, int64_t nkn) {
+                float4* __restrict__ norm, const KnotRec* __restrict__ kn, int64_t nkn, int use_window) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float red[32];
     __shared__ int active;
@@ -70,7 +76,10 @@ resample_kernel(DevParams p, const cc_template* __restrict__ tm, int64_t t_base,
     segment_knot_range(p, seg0, &kA, &kB);
     const int nk = (int)(kB - kA + 1);
     KnotRec* rec = (KnotRec*)smem;
+    float2* xs = (float2*)smem;   // with knot records: the segment's window of x
+    __shared__ int win[2];        // first sample and length of the window
     const KnotRec* __restrict__ knX = kn ? kn + ((size_t)t * p.Q + X) * nkn : nullptr;
+    const float2* __restrict__ x = p.x[X];
 
     if (knX) {
         // detector times of the segment lie within [seg0 - max d - 2, seg1 + 2 - min d]
@@ -97,6 +106,10 @@ resample_kernel(DevParams p, const cc_template* __restrict__ tm, int64_t t_base,
                 blo = blo < 0 ? 0 : blo;
                 bhi = bhi > ns - 1 ? ns - 1 : bhi;
                 active = blo <= bhi && __ldg(p.lockc[X] + bhi + 1) - __ldg(p.lockc[X] + blo) > 0;
+                // stencil centres lie in [tlo + 1, thi - 1]; taps reach max(D, 4) + 1 beyond
+                const int margin = (p.D > 4 ? p.D : 4) + 2;
+                win[0] = tlo - margin;
+                win[1] = use_window ? min(thi + margin - win[0], resample_window_len(p)) : 0;
             }
         }
         __syncthreads();
@@ -104,6 +117,13 @@ resample_kernel(DevParams p, const cc_template* __restrict__ tm, int64_t t_base,
             if (tid == 0) norm[(t * p.Q + X) * p.M + K] = make_float4(0.f, 0.f, 0.f, 0.f);
             return;
         }
+        // the segment's window of the series, zero outside [0, N_t)
+        const int w0 = win[0], nw = win[1], N = (int)p.N_t;
+        for (int i = tid; i < nw; i += blockDim.x) {
+            const int j = w0 + i;
+            xs[i] = (j >= 0 && j < N) ? __ldg(x + j) : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
     } else {
         double* dk = (double*)(smem + sizeof(KnotRec) * nk);
         const cc_template T = tm[t];
@@ -117,7 +137,6 @@ resample_kernel(DevParams p, const cc_template* __restrict__ tm, int64_t t_base,
         __syncthreads();
     }
 
-    const float2* __restrict__ x = p.x[X];
     const int64_t sa = ((t * p.Q + X) * 2 + 0) * p.N_tau;
     const int64_t sb = sa + p.N_tau;
     float A = 0.f, B = 0.f, Cn = 0.f;
@@ -127,7 +146,8 @@ resample_kernel(DevParams p, const cc_template* __restrict__ tm, int64_t t_base,
         const int k = r >> 7;
         const KnotRec kr = knX ? load_knot(knX + k) : rec[k - kA];
         const SampleTiming st = sample_timing(p, kr, r, k * KNOT);
-        const float2 xv = interp_sample(p, x, st.jstar, st.delta);
+        const float2 xv = use_window ? interp_sample_window(p, x, xs, win[0], win[1], st.jstar, st.delta)
+                              : interp_sample(p, x, st.jstar, st.delta);
         float sn, cs;
         sincospif(2.0f * st.psi, &sn, &cs);
         const float2 xr = cmul(xv, make_float2(cs, sn));
@@ -294,7 +314,8 @@ int64_t pair_chunks(const DevParams& p, int64_t n_t) {
     return nch;
 }
 
-size_t resample_smem_bytes(const DevParams& p) {
+size_t resample_smem_bytes(const DevParams& p, bool window) {
+    if (window) return (size_t)resample_window_len(p) * sizeof(float2);
     const int64_t nk = p.N_s / KNOT + 5;
     return (size_t)nk * (sizeof(KnotRec) + sizeof(double));
 }
@@ -302,7 +323,10 @@ size_t resample_smem_bytes(const DevParams& p) {
 cc_status launch_resample(cc_plan* plan, const cc_template* t_dev, int64_t n_t, void* ab,
                           float* norm, cudaStream_t st, const KnotRec* kn, int64_t nkn) {
     const DevParams& p = plan->dp;
-    const size_t sm = resample_smem_bytes(p);
+    // with knot records, the segment's window of x is staged in shared memory when it
+    // leaves room for several blocks per SM
+    const int use_window = kn && resample_smem_bytes(p, true) <= 96 * 1024;
+    const size_t sm = kn ? (use_window ? resample_smem_bytes(p, true) : 0) : resample_smem_bytes(p, false);
     if (sm > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(resample_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)sm);
@@ -311,7 +335,7 @@ cc_status launch_resample(cc_plan* plan, const cc_template* t_dev, int64_t n_t, 
     for (int64_t t0 = 0; t0 < n_t; t0 += MAX_GRID_YZ) {
         const int64_t nt = std::min<int64_t>(MAX_GRID_YZ, n_t - t0);
         dim3 grid((unsigned)p.M, (unsigned)p.Q, (unsigned)nt);
-        resample_kernel<<<grid, RS_THREADS, sm, st>>>(p, t_dev, t0, ab, (float4*)norm, kn, nkn);
+        resample_kernel<<<grid, RS_THREADS, sm, st>>>(p, t_dev, t0, ab, (float4*)norm, kn, nkn, use_window);
         count_launch();
     }
     cudaError_t e = cudaGetLastError();

@@ -122,7 +122,10 @@ def test_search_path_selection():
         assert plan.search_path == cc.PATH_STAGED
     ds = case_ds("default")
     with cc.CrossCorrPlan(ds.cfg, ds.dets, store=cc.STORE_BF16) as plan:
-        assert plan.search_path == cc.PATH_STAGED
+        assert plan.search_path == cc.PATH_TWO_PASS
+        with pytest.raises(cc.CrossCorrError) as e:
+            plan.set_path(cc.PATH_FUSED)      # the fused kernel stores nothing: FP32 only
+        assert e.value.status == 5
 
 
 def test_plan_bins_match_oracle():
@@ -219,10 +222,12 @@ def test_staged_equals_search():
     assert_rho_close(fused.astype(np.float64), staged.astype(np.float64))
 
 
-def test_bf16_storage_parity():
+@pytest.mark.parametrize("path", ["two_pass", "staged"])
+def test_bf16_storage_parity(path):
     ds = case_ds("default")
     ref = oracle.rho(ds)
     with cc.CrossCorrPlan(ds.cfg, ds.dets, store=cc.STORE_BF16) as plan:
+        plan.set_path(cc.PATH_TWO_PASS if path == "two_pass" else cc.PATH_STAGED)
         x, tm = dev_inputs(ds)
         got = plan.search(x, tm).cpu().numpy().astype(np.float64)
     assert_rho_close(got, ref, TOL16)
@@ -376,3 +381,26 @@ def test_fused_kernel_timing_events():
         ms, n = plan.kernel_time()
         assert n == 2 and ms > 0.0
         assert plan.kernel_time() == (0.0, 0)       # cleared by the read
+
+
+def test_o1_band_long_lag_full_size():
+    """The long-lag precision variant: T_max = T_short = 36000 s (N_FFT = 2^18, coset
+    length 4096 with 36000 samples folded onto it, 123564 bins), the injected template.
+    FP32 storage at the FP32 bar, BF16 storage of the resampled series at the BF16 bar;
+    the per-template error is printed for the record."""
+    ds = synth.o1_band(T_max=36000.0, n_ap=1, n_tasc=1)
+    inj = ds.injection
+    tm = np.array([[inj.a_p, inj.T_asc, inj.P]])
+    ref = oracle.rho(ds, templates=tm)
+    x = torch.from_numpy(ds.x64).to(DEV)
+    tmd = torch.from_numpy(tm).to(DEV)
+    for store, path, tol in ((cc.STORE_FP32, cc.PATH_TWO_PASS, TOL32), (cc.STORE_BF16, cc.PATH_TWO_PASS, TOL16),
+                             (cc.STORE_BF16, cc.PATH_STAGED, TOL16)):
+        with cc.CrossCorrPlan(ds.cfg, ds.dets, store=store) as plan:
+            assert plan.info["L"] == 4096 and plan.info["N_FFT"] == 262144
+            plan.set_path(path)
+            got = plan.search(x, tmd).cpu().numpy().astype(np.float64)
+        err = np.abs(got - ref).max(axis=1)
+        print(f"store {store} path {path}: max|rho| {np.abs(ref).max():.2f}, per-template max error {err}")
+        assert_rho_close(got, ref, tol)
+        assert int(got[0].argmax()) == int(ref[0].argmax())
