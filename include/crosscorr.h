@@ -251,6 +251,29 @@ cc_status crosscorr_plan_set_path(cc_plan* plan, int path);
 /* The path crosscorr_search takes for this plan (never CC_PATH_AUTO). */
 cc_status crosscorr_plan_search_path(const cc_plan* plan, int* path);
 
+/* Device workspace.  crosscorr_search keeps its scratch (knot records, partial sums, and
+ * on the two-pass and staged paths the resampled series) in a workspace that the plan
+ * allocates and grows on demand.  crosscorr_plan_set_workspace hands it caller-owned
+ * device memory instead (ws_dev 256-byte aligned, kept until replaced; NULL returns to
+ * plan-owned memory): a search that needs more than ws_bytes fails with CC_ERR_OOM and
+ * allocates nothing, which makes crosscorr_search capturable in a CUDA graph.  Plans
+ * whose searches run one after another on one stream may share one workspace.
+ * crosscorr_plan_workspace_size gives the bytes a search of n_t templates needs on the
+ * path crosscorr_search takes, with the plan's current tuning. */
+cc_status crosscorr_plan_set_workspace(cc_plan* plan, void* ws_dev, size_t ws_bytes);
+cc_status crosscorr_plan_workspace_size(const cc_plan* plan, int64_t n_t, size_t* bytes);
+
+/* Work-split tuning of crosscorr_search (results do not depend on it). */
+typedef struct {
+    int64_t batch_templates;  /* two-pass: templates per resample/spectrum batch
+                                 (0: as many as 24 GB of resampled series hold) */
+    int32_t chunk_waves;      /* fused and two-pass: split each template's segments into
+                                 chunks until the launch has about this many CTA waves
+                                 (0: 4 for fused, 10 for two-pass) */
+    int32_t reserved;         /* 0 */
+} cc_tuning;
+cc_status crosscorr_plan_set_tuning(cc_plan* plan, const cc_tuning* tuning);
+
 /* The k largest rho over (template, bin) of a device float[n_t][N_f] array,
  * descending, ties by (template, bin) ascending; hits_host receives
  * min(k, n_t*N_f) records.  Synchronises the stream.  1 <= k <= 4096. */

@@ -15,7 +15,7 @@ from typing import Optional, Sequence
 import numpy as np
 
 from . import _lib
-from ._lib import CcConfig, CcDetector, CcHit, CcLearnedInterp, CcPlanInfo, CrossCorrError, check
+from ._lib import CcConfig, CcDetector, CcHit, CcLearnedInterp, CcPlanInfo, CcTuning, CrossCorrError, check
 
 __all__ = ["CrossCorrPlan", "CrossCorrError", "PAIR_UNORDERED", "PAIR_CROSS_ONLY",
            "PAIR_ALL_ORDERED", "STORE_FP32", "STORE_BF16", "build", "load"]
@@ -213,6 +213,31 @@ class CrossCorrPlan:
         v = ctypes.c_int()
         check("crosscorr_plan_search_path", self._lib.crosscorr_plan_search_path(self._h, byref(v)))
         return v.value
+
+    def workspace_size(self, n_t: int) -> int:
+        """Device bytes search() needs for n_t templates on its current path and tuning."""
+        v = ctypes.c_size_t()
+        check("crosscorr_plan_workspace_size", self._lib.crosscorr_plan_workspace_size(self._h, int(n_t), byref(v)))
+        return v.value
+
+    def set_workspace(self, ws=None):
+        """Use a caller-owned device buffer (a CUDA uint8 tensor, kept alive here) as the
+        search workspace; None returns to plan-owned memory."""
+        import torch
+        if ws is None:
+            check("crosscorr_plan_set_workspace", self._lib.crosscorr_plan_set_workspace(self._h, None, 0))
+            self._ws = None
+            return
+        _check_tensor("workspace", ws, torch.uint8)
+        check("crosscorr_plan_set_workspace",
+              self._lib.crosscorr_plan_set_workspace(self._h, c_void_p(_dptr(ws)), ws.numel()))
+        self._ws = ws
+
+    def set_tuning(self, batch_templates: int = 0, chunk_waves: int = 0):
+        """Work split of search(): templates per two-pass batch, target CTA waves of the
+        segment-chunk split (0: defaults)."""
+        t = CcTuning(int(batch_templates), int(chunk_waves), 0)
+        check("crosscorr_plan_set_tuning", self._lib.crosscorr_plan_set_tuning(self._h, byref(t)))
 
     def set_kernel_timing(self, on: bool = True):
         """Diagnostic: bracket each fused-kernel launch with CUDA events on its stream."""

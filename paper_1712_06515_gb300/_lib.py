@@ -109,6 +109,10 @@ class CcLearnedInterp(ctypes.Structure):
                 ("nu_lo", c_double), ("nu_hi", c_double), ("nu_c", c_double)]
 
 
+class CcTuning(ctypes.Structure):
+    _fields_ = [("batch_templates", c_int64), ("chunk_waves", c_int32), ("reserved", c_int32)]
+
+
 # every symbol the header declares, with its signature
 SIGNATURES = {
     "crosscorr_plan": (c_int, [POINTER(CcConfig), POINTER(CcDetector), POINTER(c_void_p)]),
@@ -128,6 +132,9 @@ SIGNATURES = {
     "crosscorr_kernel_launches": (ctypes.c_uint64, []),
     "crosscorr_plan_set_kernel_timing": (c_int, [c_void_p, c_int]),
     "crosscorr_plan_set_path": (c_int, [c_void_p, c_int]),
+    "crosscorr_plan_set_workspace": (c_int, [c_void_p, c_void_p, c_size_t]),
+    "crosscorr_plan_workspace_size": (c_int, [c_void_p, c_int64, POINTER(c_size_t)]),
+    "crosscorr_plan_set_tuning": (c_int, [c_void_p, POINTER(CcTuning)]),
     "crosscorr_plan_search_path": (c_int, [c_void_p, POINTER(c_int)]),
     "crosscorr_plan_kernel_time": (c_int, [c_void_p, POINTER(c_double), POINTER(c_int64)]),
 }

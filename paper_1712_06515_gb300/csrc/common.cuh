@@ -124,6 +124,8 @@ struct cc_plan {
     uint16_t* learned_w = nullptr;
     float* learned_taps = nullptr;
     int search_path = CC_PATH_AUTO;           // crosscorr_plan_set_path
+    cc_tuning tuning = {0, 0, 0};             // crosscorr_plan_set_tuning
+    bool ws_external = false;                 // ws is caller memory (crosscorr_plan_set_workspace)
     // diagnostic event pairs around fused-kernel launches (crosscorr_plan_set_kernel_timing)
     bool kernel_timing = false;
     std::vector<cudaEvent_t> timing_events;   // [2 * n] start, stop

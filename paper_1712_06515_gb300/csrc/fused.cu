@@ -84,7 +84,8 @@ bool fused_layout(const cc_plan* plan, int64_t n_t, FusedLayout* lay) {
     if ((int64_t)(p.R + 1) * p.Q > FUSED_THREADS) return false;
     // chunks: enough CTAs to fill the GPU, each chunk at least 4R + 1 segments
     int64_t ctas = (int64_t)C / (C / CL) * n_t;   // = CL * n_t clusters' CTAs
-    int64_t want = std::max<int64_t>(1, (4 * 152 + ctas - 1) / std::max<int64_t>(ctas, 1));
+    const int64_t waves = plan->tuning.chunk_waves > 0 ? plan->tuning.chunk_waves : 4;
+    int64_t want = std::max<int64_t>(1, (waves * 152 + ctas - 1) / std::max<int64_t>(ctas, 1));
     int64_t maxch = std::max<int64_t>(1, p.M / (4 * p.R + 1));
     int64_t nch = std::min(want, maxch);
     lay->chunk_len = (p.M + nch - 1) / nch;

@@ -64,6 +64,9 @@ cc_status cuda_fail(cudaError_t e, const char* what) {
 
 cc_status ensure_workspace(cc_plan* p, size_t bytes) {
     if (p->ws_bytes >= bytes) return CC_OK;
+    if (p->ws_external)
+        return fail(CC_ERR_OOM, "caller workspace of " + std::to_string(p->ws_bytes) + " bytes; this call needs " +
+                                    std::to_string(bytes));
     if (p->ws) {
         cudaFree(p->ws);
         p->ws = nullptr;
@@ -121,6 +124,24 @@ const char* crosscorr_last_error(void) { return g_last_error.c_str(); }
 
 uint64_t crosscorr_kernel_launches(void) { return cc::g_launches.load(); }
 
+cc_status crosscorr_plan_set_workspace(cc_plan* plan, void* ws_dev, size_t ws_bytes) {
+    if (!plan) return cc::fail(CC_ERR_INVALID, "plan is null");
+    if (ws_dev && ((uintptr_t)ws_dev & 255)) return cc::fail(CC_ERR_INVALID, "workspace must be 256-byte aligned");
+    if (plan->ws && !plan->ws_external) cudaFree(plan->ws);
+    plan->ws = ws_dev;
+    plan->ws_bytes = ws_dev ? ws_bytes : 0;
+    plan->ws_external = ws_dev != nullptr;
+    return CC_OK;
+}
+
+cc_status crosscorr_plan_set_tuning(cc_plan* plan, const cc_tuning* tuning) {
+    if (!plan || !tuning) return cc::fail(CC_ERR_INVALID, "null argument to crosscorr_plan_set_tuning");
+    if (tuning->batch_templates < 0 || tuning->chunk_waves < 0 || tuning->chunk_waves > 1000 || tuning->reserved)
+        return cc::fail(CC_ERR_INVALID, "batch_templates >= 0, 0 <= chunk_waves <= 1000, reserved = 0");
+    plan->tuning = *tuning;
+    return CC_OK;
+}
+
 cc_status crosscorr_plan_set_kernel_timing(cc_plan* plan, int on) {
     if (!plan) return cc::fail(CC_ERR_INVALID, "plan is null");
     plan->kernel_timing = on != 0;
@@ -147,7 +168,7 @@ cc_status crosscorr_plan_kernel_time(cc_plan* plan, double* ms, int64_t* launche
 void crosscorr_plan_destroy(cc_plan* p) {
     if (!p) return;
     for (void* d : p->dev_allocs) cudaFree(d);
-    if (p->ws) cudaFree(p->ws);
+    if (p->ws && !p->ws_external) cudaFree(p->ws);
     for (cudaEvent_t e : p->timing_events) cudaEventDestroy(e);
     if (p->learned_w) cudaFree(p->learned_w);
     if (p->learned_taps) cudaFree(p->learned_taps);

@@ -12,6 +12,7 @@ cc_status launch_norm_pairs(cc_plan* plan, const void* F, const float* norm, int
                             float* rawws, float* rho, cudaStream_t st);
 size_t pair_workspace_bytes(const cc_plan* plan, int64_t n_t);
 bool two_pass_supported(const cc_plan* plan);
+size_t two_pass_workspace_bytes(const cc_plan* plan, int64_t n_t);
 cc_status search_two_pass(cc_plan* plan, const cc_template* t_dev, int64_t n_t, float* rho, cudaStream_t st);
 
 constexpr size_t STAGED_WS_BUDGET = (size_t)6 << 30;
@@ -30,6 +31,19 @@ static void staged_batch(const cc_plan* p, int64_t n_t, int64_t* batch, size_t* 
     b = std::min<int64_t>(b, n_t);
     *batch = b;
     *bytes = (align256(ab * b) + align256(F * b) + align256(nm * b) + align256(pair_workspace_bytes(p, b)));
+}
+
+// Fused path: layout for a batch of templates, knot-record batch and workspace bytes
+// (FP64 partial normalisations, FP32 partial sums when a template is split into chunks,
+// knot records of one batch).
+static bool fused_plan(const cc_plan* plan, int64_t n_t, FusedLayout* lay, int64_t* kbatch, size_t* bytes) {
+    const size_t krow = (size_t)plan->Q * knot_rows(plan) * sizeof(KnotRec);
+    *kbatch = std::max<int64_t>(1, std::min<int64_t>(n_t, (int64_t)(KNOT_WS_BUDGET / krow)));
+    if (plan->cfg.store != CC_STORE_FP32 || !fused_layout(plan, *kbatch, lay)) return false;
+    const size_t dbytes = align256((size_t)n_t * lay->n_chunks * sizeof(double));
+    const size_t rbytes = lay->n_chunks > 1 ? align256((size_t)n_t * lay->n_chunks * plan->N_f * sizeof(float)) : 0;
+    *bytes = dbytes + rbytes + krow * *kbatch;
+    return true;
 }
 
 static bool fused_supported(const cc_plan* plan) {
@@ -58,6 +72,21 @@ extern "C" cc_status crosscorr_plan_set_path(cc_plan* plan, int path) {
     return CC_OK;
 }
 
+extern "C" cc_status crosscorr_plan_workspace_size(const cc_plan* plan, int64_t n_t, size_t* bytes) {
+    using namespace cc;
+    if (!plan || !bytes) return fail(CC_ERR_INVALID, "null argument to crosscorr_plan_workspace_size");
+    if (n_t < 0) return fail(CC_ERR_INVALID, "n_t must be >= 0");
+    *bytes = 0;
+    if (n_t == 0) return CC_OK;
+    const int path = resolve_path(plan);
+    FusedLayout lay;
+    int64_t kbatch, batch;
+    if (path == CC_PATH_TWO_PASS) *bytes = two_pass_workspace_bytes(plan, n_t);
+    else if (path == CC_PATH_FUSED && fused_plan(plan, n_t, &lay, &kbatch, bytes)) {
+    } else staged_batch(plan, n_t, &batch, bytes);
+    return CC_OK;
+}
+
 extern "C" cc_status crosscorr_plan_search_path(const cc_plan* plan, int* path) {
     using namespace cc;
     if (!plan || !path) return fail(CC_ERR_INVALID, "null argument to crosscorr_plan_search_path");
@@ -78,15 +107,14 @@ extern "C" cc_status crosscorr_search(cc_plan* plan, const void* const* x_dev, c
     const int path = resolve_path(plan);
     if (path == CC_PATH_TWO_PASS) return search_two_pass(plan, t_dev, n_t, rho_dev, st);
     FusedLayout lay;
-    // knot records from the pre-pass, up to KNOT_WS_BUDGET bytes of them per batch
-    const size_t krow = (size_t)plan->Q * knot_rows(plan) * sizeof(KnotRec);
-    const int64_t kbatch = std::max<int64_t>(1, std::min<int64_t>(n_t, (int64_t)(KNOT_WS_BUDGET / krow)));
-    if (path == CC_PATH_FUSED && fused_layout(plan, kbatch, &lay)) {
+    int64_t kbatch;
+    size_t fbytes;
+    if (path == CC_PATH_FUSED && fused_plan(plan, n_t, &lay, &kbatch, &fbytes)) {
+        // knot records from the pre-pass, up to KNOT_WS_BUDGET bytes of them per batch;
         // raw partial sums go straight into rho when there is one chunk per template
+        if ((s = ensure_workspace(plan, fbytes)) != CC_OK) return s;
         const size_t dbytes = align256((size_t)n_t * lay.n_chunks * sizeof(double));
         const size_t rbytes = lay.n_chunks > 1 ? align256((size_t)n_t * lay.n_chunks * plan->N_f * sizeof(float)) : 0;
-        const size_t kbytes = krow * kbatch;
-        if ((s = ensure_workspace(plan, dbytes + rbytes + kbytes)) != CC_OK) return s;
         double* dpart = (double*)plan->ws;
         float* raw = lay.n_chunks > 1 ? (float*)((char*)plan->ws + dbytes) : rho_dev;
         KnotRec* kn = (KnotRec*)((char*)plan->ws + dbytes + rbytes);

@@ -44,7 +44,7 @@ struct SegPairLayout {
 // grid: x = coset c, y = weight w * n_chunks + chunk, z = template within the batch.
 // ab: [n_t][Q][2][N_tau] complex64 (bf16 pairs with BF16 storage), norm: [n_t][Q][M] (hat-A, hat-B, hat-C, 0),
 // raw: [n_t][2 * n_chunks][N_f] partial pair sums.
-template <int LT>
+template <int LT, bool BF16>
 __global__ void __launch_bounds__(SP_THREADS, 2)
 segpair_kernel(DevParams p, SegPairLayout lay, const void* __restrict__ ab, const float4* __restrict__ norm,
                float* __restrict__ raw) {
@@ -87,9 +87,9 @@ segpair_kernel(DevParams p, SegPairLayout lay, const void* __restrict__ ab, cons
     const float2* __restrict__ twr = p.twc + (size_t)c * N_s;
     const float4* __restrict__ nt = norm + (size_t)t * Q * M;
     const size_t abt = (size_t)t * Q * 2 * N_tau;   // element offset of this template's rows
-    const bool bf16 = p.store == CC_STORE_BF16;
     auto load_ab = [&](size_t i) -> float2 {
-        return bf16 ? __bfloat1622float2(((const __nv_bfloat162*)ab)[i]) : __ldg((const float2*)ab + i);
+        if constexpr (BF16) return __bfloat1622float2(((const __nv_bfloat162*)ab)[i]);
+        else return __ldg((const float2*)ab + i);
     };
     auto sync = []() { __syncthreads(); };
 
@@ -103,13 +103,11 @@ segpair_kernel(DevParams p, SegPairLayout lay, const void* __restrict__ ab, cons
             float2 v[16];
             if (N_s <= L) {
                 float2 vv[16], tw[16];
-                const float2* rowf = (const float2*)ab + row;
-                const __nv_bfloat162* rowh = (const __nv_bfloat162*)ab + row;
 #pragma unroll
                 for (int r = 0; r < 16; ++r) {
                     const int rr = (tid + r * B1 + offn) & (L - 1);
                     const bool in = rr < (int)N_s;
-                    vv[r] = !in ? make_float2(0.f, 0.f) : bf16 ? __bfloat1622float2(rowh[rr]) : __ldg(rowf + rr);
+                    vv[r] = in ? load_ab(row + rr) : make_float2(0.f, 0.f);
                     tw[r] = in ? __ldg(twr + rr) : make_float2(0.f, 0.f);
                 }
 #pragma unroll
@@ -216,7 +214,8 @@ bool segpair_layout(const cc_plan* plan, int64_t n_t, SegPairLayout* lay) {
     if (lay->bytes > 113 * 1024) return false;   // two CTAs per SM
     // chunks: about ten waves of two CTAs per SM, each chunk at least 4R + 1 segments
     const int64_t ctas = (int64_t)p.C * 2 * n_t;
-    const int64_t want = std::max<int64_t>(1, (10 * 2 * 152 + ctas - 1) / std::max<int64_t>(ctas, 1));
+    const int64_t waves = plan->tuning.chunk_waves > 0 ? plan->tuning.chunk_waves : 10;
+    const int64_t want = std::max<int64_t>(1, (waves * 2 * 152 + ctas - 1) / std::max<int64_t>(ctas, 1));
     const int64_t maxch = std::max<int64_t>(1, p.M / (4 * p.R + 1));
     const int64_t nch = std::min<int64_t>({want, maxch, 32767});
     lay->chunk_len = (p.M + nch - 1) / nch;
@@ -224,13 +223,21 @@ bool segpair_layout(const cc_plan* plan, int64_t n_t, SegPairLayout* lay) {
     return true;
 }
 
+template <int LT, bool BF16>
+static cudaError_t launch_segpair_t(dim3 grid, size_t smem, cudaStream_t st, const DevParams& p,
+                                    const SegPairLayout& lay, const void* ab, const float4* norm, float* raw) {
+    cudaError_t e = cudaFuncSetAttribute(segpair_kernel<LT, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    segpair_kernel<LT, BF16><<<grid, SP_THREADS, smem, st>>>(p, lay, ab, norm, raw);
+    return cudaGetLastError();
+}
+
 template <int LT>
 static cudaError_t launch_segpair_lt(dim3 grid, size_t smem, cudaStream_t st, const DevParams& p,
                                      const SegPairLayout& lay, const void* ab, const float4* norm, float* raw) {
-    cudaError_t e = cudaFuncSetAttribute(segpair_kernel<LT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    segpair_kernel<LT><<<grid, SP_THREADS, smem, st>>>(p, lay, ab, norm, raw);
-    return cudaGetLastError();
+    if (p.store == CC_STORE_BF16) return launch_segpair_t<LT, true>(grid, smem, st, p, lay, ab, norm, raw);
+    return launch_segpair_t<LT, false>(grid, smem, st, p, lay, ab, norm, raw);
 }
 
 static cudaError_t launch_segpair(const DevParams& p, const SegPairLayout& lay, int64_t n_t, const void* ab,
@@ -249,11 +256,17 @@ static cudaError_t launch_segpair(const DevParams& p, const SegPairLayout& lay, 
 }
 
 // Template batch of the two-pass search and the workspace it needs.
+static int64_t two_pass_batch_templates(const cc_plan* plan, int64_t n_t) {
+    const size_t per_ab = (size_t)plan->Q * 2 * plan->N_tau * (plan->cfg.store == CC_STORE_BF16 ? 4 : 8);
+    int64_t b = plan->tuning.batch_templates > 0 ? plan->tuning.batch_templates
+                                                 : (int64_t)std::max<size_t>(1, TWO_PASS_WS_BUDGET / per_ab);
+    return std::max<int64_t>(1, std::min<int64_t>({b, n_t, 65535}));
+}
+
 static void two_pass_batch(const cc_plan* plan, int64_t n_t, const SegPairLayout& lay, int64_t* batch,
                            size_t* bytes) {
     const size_t per_ab = (size_t)plan->Q * 2 * plan->N_tau * (plan->cfg.store == CC_STORE_BF16 ? 4 : 8);
-    int64_t b = (int64_t)std::max<size_t>(1, TWO_PASS_WS_BUDGET / per_ab);
-    b = std::min<int64_t>({b, n_t, 65535});
+    const int64_t b = two_pass_batch_templates(plan, n_t);
     *batch = b;
     *bytes = al256(per_ab * b) + al256((size_t)plan->Q * plan->M * sizeof(float4) * b) +
              al256((size_t)b * sizeof(double)) + al256((size_t)b * 2 * lay.n_chunks * plan->N_f * sizeof(float)) +
@@ -265,10 +278,19 @@ bool two_pass_supported(const cc_plan* plan) {
     return segpair_layout(plan, 1, &lay);
 }
 
+size_t two_pass_workspace_bytes(const cc_plan* plan, int64_t n_t) {
+    SegPairLayout lay;
+    if (n_t < 1 || !segpair_layout(plan, two_pass_batch_templates(plan, n_t), &lay)) return 0;
+    int64_t batch;
+    size_t bytes;
+    two_pass_batch(plan, n_t, lay, &batch, &bytes);
+    return bytes;
+}
+
 cc_status search_two_pass(cc_plan* plan, const cc_template* t_dev, int64_t n_t, float* rho, cudaStream_t st) {
     SegPairLayout lay;
     const size_t per_ab = (size_t)plan->Q * 2 * plan->N_tau * (plan->cfg.store == CC_STORE_BF16 ? 4 : 8);
-    const int64_t b0 = std::min<int64_t>({(int64_t)std::max<size_t>(1, TWO_PASS_WS_BUDGET / per_ab), n_t, 65535});
+    const int64_t b0 = two_pass_batch_templates(plan, n_t);
     if (!segpair_layout(plan, b0, &lay)) return fail(CC_ERR_UNSUPPORTED, "plan does not fit the two-pass kernel");
     int64_t batch;
     size_t bytes;

@@ -330,6 +330,41 @@ def o1_band(seed: int = 1002, T_max: float = 3600.0, n_ap: int = 40, n_tasc: int
                                      f"{n_ap}x{n_tasc} templates")
 
 
+def multiband_band(b: int, seed: int = 1003, n_bands: int = 32, days: float = 10.0,
+                   template_scale: float = 1.0, noise: bool = True,
+                   max_templates: Optional[int] = None) -> Dataset:
+    """Band b of the batched multi-band workload: 0.5 Hz at f0_b = 20 + 230 b/31 Hz
+    sampled at 1 s, T_sft = T_short = T_max = 60 round(4 * 15^(b/31)) s (240 s at 20 Hz
+    to 3600 s at 250 Hz), N_b = round(1e3 * 50^(b/31)) templates (about 4.2e5 over the
+    32 bands) times template_scale, on an a_p x T_asc grid; T_obs = 10 d at 60 % duty
+    with each band's gaps drawn from its own seed; an injection 0.0731 Hz above f0_b."""
+    x = b / (n_bands - 1)
+    f0 = 20.0 + 230.0 * x
+    T = 60.0 * round(4.0 * 15.0 ** x)
+    n_b = max(1, int(round(1e3 * 50.0 ** x * template_scale)))
+    if max_templates is not None:
+        n_b = min(n_b, max_templates)
+    cfg = SearchConfig(t0=T0_GPS, dt=1.0, n_samples=int(round(days * 86400.0)), f_h=f0, f_band=0.5,
+                       T_sft=T, T_max=T, T_short=T)
+    rng = np.random.default_rng(seed + 101 * b)
+    tasc = T_ASC_O1 + rng.uniform(-100.0, 100.0)
+    inj = Injection(h0=0.1, f0=f0 + 0.0731, a_p=1.44, T_asc=tasc, P=SCO_X1_P, cosi=0.6, psi=0.3, phi0=0.7)
+    n_ap = max(1, int(round(math.sqrt(n_b / 5.0))))
+    n_tasc = max(1, int(round(n_b / n_ap)))
+    tm = template_grid(np.linspace(1.36, 1.52, n_ap), tasc + np.linspace(-300.0, 300.0, n_tasc), [SCO_X1_P])
+    tm = tm[:n_b] if len(tm) >= n_b else tm
+    return build_dataset(cfg, tm, seed + 101 * b, duty=0.6, injection=inj, noise=noise,
+                         description=f"band {b}: 0.5 Hz at {f0:.1f} Hz, T_max={T:g} s, {len(tm)} templates")
+
+
+def multiband(seed: int = 1003, n_bands: int = 32, days: float = 10.0, template_scale: float = 1.0,
+              bands: Optional[Sequence[int]] = None, noise: bool = True,
+              max_templates: Optional[int] = None) -> List[Dataset]:
+    """The batched multi-band workload: one Dataset per band (see multiband_band)."""
+    idx = range(n_bands) if bands is None else bands
+    return [multiband_band(b, seed, n_bands, days, template_scale, noise, max_templates) for b in idx]
+
+
 def tiny(seed: int = 7, n_samples: int = 4096, T_sft: float = 64.0, T_max: float = 128.0,
          T_short: float = 128.0, f_h: float = 120.0, f_band: float = 0.5, D: int = 8,
          n_templates: int = 4, duty: float = 0.85, noise: bool = True,
