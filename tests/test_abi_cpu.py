@@ -50,6 +50,8 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(_lib.CcDetector) == 11 * 8
     assert ctypes.sizeof(_lib.CcHit) == 32
     assert ctypes.sizeof(_lib.CcPlanInfo) == 9 * 8 + 7 * 8 + 8
+    assert ctypes.sizeof(_lib.CcTuning) == 16
+    assert ctypes.sizeof(_lib.CcLearnedInterp) == 40
 
 
 def _cfg(**kw):
@@ -139,6 +141,14 @@ def test_entry_points_reject_null_plan(lib):
     hits = (_lib.CcHit * 1)()
     assert lib.crosscorr_rho_topk(None, None, 1, 1, hits, None) == CC_ERR_INVALID
     assert lib.crosscorr_plan_set_kernel_timing(None, 1) == CC_ERR_INVALID
+    assert lib.crosscorr_plan_set_path(None, 0) == CC_ERR_INVALID
+    assert lib.crosscorr_plan_set_workspace(None, None, 0) == CC_ERR_INVALID
+    t = _lib.CcTuning(0, 0, 0)
+    assert lib.crosscorr_plan_set_tuning(None, ctypes.byref(t)) == CC_ERR_INVALID
+    nb = ctypes.c_size_t()
+    assert lib.crosscorr_plan_workspace_size(None, 1, ctypes.byref(nb)) == CC_ERR_INVALID
+    pth = ctypes.c_int()
+    assert lib.crosscorr_plan_search_path(None, ctypes.byref(pth)) == CC_ERR_INVALID
     ms, n = ctypes.c_double(), ctypes.c_int64()
     assert lib.crosscorr_plan_kernel_time(None, ctypes.byref(ms), ctypes.byref(n)) == CC_ERR_INVALID
     lib.crosscorr_plan_destroy(None)
