@@ -34,6 +34,11 @@ sys.path.insert(0, ROOT)
 METRIC = "CrossCorr rho templates*freq-bins/sec on 1 GB300 (+% HBM roofline) vs plain FP32 at stated rho error"
 UNIT = "template*bins/s"
 GRID_TEMPLATES = 8000
+# DRAM bytes read + written per template by segpair_kernel<4096> on this workload, from
+# the ncu capture summarised in profiles/segpair_kernel_o1_band_64_templates.md (64
+# templates in one launch; traffic grows with the templates of a launch).  None once
+# the kernel changes.
+SEGPAIR_DRAM_BYTES_PER_TEMPLATE = (14.939288e9 + 25.929216e6) / 64
 SM_COUNT = 152
 FP32_LANES = 128
 
@@ -306,8 +311,12 @@ def run_gpu(args):
         clk_max = float((clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0))
         peak = SM_COUNT * FP32_LANES * 2 * clk_max * 1e6 / 1e12
         other_ms = max(0.0, 1e3 * elapsed - fused_ms) / (B * args.steps)
+        traffic = None
+        if path == cc.PATH_TWO_PASS and SEGPAIR_DRAM_BYTES_PER_TEMPLATE is not None and fused_launches:
+            traffic = SEGPAIR_DRAM_BYTES_PER_TEMPLATE * B * args.steps / fused_launches
         roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                "traffic_unit": "bytes per launch (ncu capture, scaled by templates per launch)",
                 "peak_kind": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 flop x {clk_max:g} MHz",
                 "flops_per_template": kflops,
                 "kernel_ms_per_launch": fused_ms / max(fused_launches, 1),

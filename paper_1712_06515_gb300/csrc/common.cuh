@@ -46,6 +46,9 @@ struct DevParams {
     int Q, D, pair_mode, store;
     int L, C, log2L, nsft;
     int n_ab_step, interp;           // interp: CC_INTERP_EXACT or CC_INTERP_LEARNED
+    // floor division of non-negative ints by nsft and n_ab_step: q = (a * m) >> s
+    uint32_t nsft_m, ab_m;
+    int nsft_s, ab_s;
     int64_t N_t, N_s, M, R, N_tau, N_FFT, N_f;
     int64_t b0;      // (k0 - N_FFT/2) mod N_FFT: FFT bin of output k = 0
     int64_t ab_j0;   // ab_t0 / dt
@@ -58,7 +61,7 @@ struct DevParams {
     const float* atab[CC_MAX_DET];
     const float* btab[CC_MAX_DET];
     int64_t n_ab[CC_MAX_DET];
-    const float* sig2[CC_MAX_DET];   // sigma^2 per T_sft block, 0 in gaps
+    const float2* sigw[CC_MAX_DET];  // (sigma^2, 1/sigma^2) per T_sft block, (0, 0) in gaps
     int64_t n_sig[CC_MAX_DET];
     const int* lockc[CC_MAX_DET];    // [n_sig + 1] number of locked (sigma > 0) blocks before each block
     const int* coset_off;            // [C+1]
@@ -180,6 +183,25 @@ __host__ __device__ __forceinline__ int64_t imax64(int64_t a, int64_t b) { retur
 __device__ __forceinline__ int floor_div32(int a, int b) {
     int q = a / b;
     return (q * b > a) ? q - 1 : q;
+}
+
+// floor(a / b) with the magic pair (m, s) of b (0 <= a < 2^31 exactly; negative a
+// through the integer division).
+__device__ __forceinline__ int floor_div_magic(int a, int b, uint32_t m, int s) {
+    if (a < 0) return floor_div32(a, b);
+    return (int)(((uint64_t)(uint32_t)a * m) >> s);
+}
+
+// Magic pair for floor division of 0 <= a < 2^31 by 1 <= b < 2^31: with l = ceil(log2 b),
+// m = ceil(2^(31 + l) / b) < 2^32 and floor(a / b) = (a m) >> (31 + l) (Granlund and
+// Montgomery, "Division by invariant integers using multiplication", Thm. 4.2 with a
+// 31-bit dividend).
+inline void magic_for(uint32_t b, uint32_t* m, int* s) {
+    int l = 0;
+    while ((1ull << l) < b) ++l;
+    const uint64_t num = (uint64_t)1 << (31 + l);   // l <= 31
+    *m = (uint32_t)((num + b - 1) / b);
+    *s = 31 + l;
 }
 
 __device__ __forceinline__ int64_t floor_div(int64_t a, int64_t b) {
@@ -308,6 +330,27 @@ __device__ __forceinline__ float2 sinc_taps(const DevParams& p, const float2* __
     return acc;
 }
 
+// sinc_taps for a compile-time half width D, the taps taken in pairs j* -+ k: with
+// q = (sin(pi delta)/pi) / (delta^2 - k^2), the coefficients are q (delta -+ k) times the
+// signed window (-1)^k w_{D-+k}, so one reciprocal serves two taps.
+template <int D>
+__device__ __forceinline__ float2 sinc_taps_t(const DevParams& p, const float2* __restrict__ xp, float delta) {
+    const float s = sinpif(delta) * 0.318309886183790672f;
+    const float c0 = p.ham[D] * __fdividef(s, delta);
+    float2 acc = make_float2(c0 * xp[D].x, c0 * xp[D].y);
+#pragma unroll
+    for (int k = 1; k <= D; ++k) {
+        const float q = __fdividef(s, fmaf(delta, delta, -(float)(k * k)));
+        const float sg = (k & 1) ? -1.0f : 1.0f;
+        const float cm = sg * p.ham[D - k] * q * (delta - (float)k);   // tap j* - k: 1/(delta + k)
+        const float cp = sg * p.ham[D + k] * q * (delta + (float)k);   // tap j* + k: 1/(delta - k)
+        const float2 xm = xp[D - k], xq = xp[D + k];
+        acc.x = fmaf(cm, xm.x, fmaf(cp, xq.x, acc.x));
+        acc.y = fmaf(cm, xm.y, fmaf(cp, xq.y, acc.y));
+    }
+    return acc;
+}
+
 // Windowed-sinc interpolation (2D+1 taps) at t/dt = j* + delta of a complex series.
 __device__ __forceinline__ float2 interp_sinc(const DevParams& p, const float2* __restrict__ x,
                                               int jstar, float delta) {
@@ -380,7 +423,9 @@ __device__ __forceinline__ float2 interp_sample(const DevParams& p, const float2
 }
 
 // As interp_sample, reading from a shared-memory copy xs of samples [w0, w0 + nw) of the
-// series (zero outside [0, N_t)) when every tap falls inside it, else from x.
+// series (zero outside [0, N_t)) when every tap falls inside it, else from x.  DT > 0:
+// the windowed sinc's half width D is DT at compile time.
+template <int DT = 0>
 __device__ __forceinline__ float2 interp_sample_window(const DevParams& p, const float2* __restrict__ x,
                                                        const float2* xs, int w0, int nw, int jstar,
                                                        float delta) {
@@ -399,10 +444,12 @@ __device__ __forceinline__ float2 interp_sample_window(const DevParams& p, const
         }
         return acc;
     }
-    const int j0 = jstar - p.D;
-    if (j0 < w0 || j0 + 2 * p.D >= w0 + nw) return interp_sinc(p, x, jstar, delta);
+    const int D = DT > 0 ? DT : p.D;
+    const int j0 = jstar - D;
+    if (j0 < w0 || j0 + 2 * D >= w0 + nw) return interp_sinc(p, x, jstar, delta);
     if (delta == 0.0f) return xs[jstar - w0];
-    return sinc_taps(p, xs + (j0 - w0), delta);
+    if constexpr (DT > 0) return sinc_taps_t<DT>(p, xs + (j0 - w0), delta);
+    else return sinc_taps(p, xs + (j0 - w0), delta);
 }
 
 // Weights at detector time t/dt = j* + delta: alpha = a/sigma^2, beta = b/sigma^2,
@@ -414,14 +461,15 @@ struct SampleWeights {
 __device__ __forceinline__ SampleWeights sample_weights(const DevParams& p, int X, int jstar,
                                                         float delta) {
     SampleWeights w{0.f, 0.f, 0.f};
-    const int q = floor_div32(jstar, p.nsft);
+    const int q = floor_div_magic(jstar, p.nsft, p.nsft_m, p.nsft_s);
     const int rem = jstar - q * p.nsft;
     const int blk = (rem == 0 && delta < 0.f) ? q - 1 : q;
     if (blk < 0 || blk >= (int)p.n_sig[X]) return w;
-    const float s2 = __ldg(p.sig2[X] + blk);
+    const float2 sw = __ldg(p.sigw[X] + blk);
+    const float s2 = sw.x;
     if (!(s2 > 0.f)) return w;
     const int ja = jstar - (int)p.ab_j0;
-    const int ia = floor_div32(ja, p.n_ab_step);
+    const int ia = floor_div_magic(ja, p.n_ab_step, p.ab_m, p.ab_s);
     const int nab = (int)p.n_ab[X];
     const int ic = ia < 0 ? 0 : (ia > nab - 2 ? nab - 2 : ia);
     // the linear interpolant is continuous, so the interval chosen at a node does not matter
@@ -430,9 +478,8 @@ __device__ __forceinline__ SampleWeights sample_weights(const DevParams& p, int 
     const float b0 = __ldg(p.btab[X] + ic), b1 = __ldg(p.btab[X] + ic + 1);
     const float a = fmaf(fr, a1 - a0, a0);
     const float b = fmaf(fr, b1 - b0, b0);
-    const float inv = 1.0f / s2;
-    w.alpha = a * inv;
-    w.beta = b * inv;
+    w.alpha = a * sw.y;
+    w.beta = b * sw.y;
     w.s2 = s2;
     return w;
 }

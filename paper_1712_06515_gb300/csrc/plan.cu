@@ -310,18 +310,23 @@ cc_status crosscorr_plan(const cc_config* cfg, const cc_detector* dets, cc_plan*
     for (int q = 0; q < p->Q; ++q) {
         const cc_detector& d = dets[q];
         std::vector<float> a(d.n_ab), b(d.n_ab), s2(d.n_sigma);
+        std::vector<float2> sw(d.n_sigma);
         for (int64_t i = 0; i < d.n_ab; ++i) {
             a[i] = (float)d.a_tab[i];
             b[i] = (float)d.b_tab[i];
         }
-        for (int64_t i = 0; i < d.n_sigma; ++i) s2[i] = (float)(d.sigma[i] * d.sigma[i]);
+        for (int64_t i = 0; i < d.n_sigma; ++i) {
+            const double v = d.sigma[i] * d.sigma[i];
+            s2[i] = (float)v;
+            sw[i] = s2[i] > 0.f ? make_float2((float)v, (float)(1.0 / v)) : make_float2(0.f, 0.f);
+        }
         std::vector<int> lc(d.n_sigma + 1, 0);
         for (int64_t i = 0; i < d.n_sigma; ++i) lc[i + 1] = lc[i] + (s2[i] > 0.f ? 1 : 0);
         cc_status st;
         if ((st = upload(p, d.ssb_delay, (size_t)d.n_eph, &dp.ssb[q])) != CC_OK ||
             (st = upload(p, a.data(), a.size(), &dp.atab[q])) != CC_OK ||
             (st = upload(p, b.data(), b.size(), &dp.btab[q])) != CC_OK ||
-            (st = upload(p, s2.data(), s2.size(), &dp.sig2[q])) != CC_OK ||
+            (st = upload(p, sw.data(), sw.size(), &dp.sigw[q])) != CC_OK ||
             (st = upload(p, lc.data(), lc.size(), &dp.lockc[q])) != CC_OK) {
             crosscorr_plan_destroy(p);
             return st;
@@ -384,6 +389,8 @@ cc_status crosscorr_plan(const cc_config* cfg, const cc_detector* dets, cc_plan*
     dp.C = (int)C;
     dp.log2L = log2L;
     dp.nsft = (int)nsft;
+    cc::magic_for((uint32_t)nsft, &dp.nsft_m, &dp.nsft_s);
+    cc::magic_for((uint32_t)std::max(1, dp.n_ab_step), &dp.ab_m, &dp.ab_s);
     dp.N_t = c.n_samples;
     dp.N_s = p->N_s;
     dp.M = p->M;

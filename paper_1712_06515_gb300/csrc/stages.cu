@@ -61,6 +61,7 @@ __host__ __device__ inline int resample_window_len(const DevParams& p) {
 // detector times all fall in gaps is skipped: its norms are written as zero and its
 // a_r, b_r are left unwritten (the two-pass search reads a segment only when its norms
 // are nonzero).  Without `kn` every sample is written.
+template <int DT>
 __global__ void __launch_bounds__(RS_THREADS)
 resample_kernel(DevParams p, const cc_template* __restrict__ tm, int64_t t_base, void* ab,
                 float4* __restrict__ norm, const KnotRec* __restrict__ kn, int64_t nkn, int use_window) {
@@ -146,7 +147,7 @@ resample_kernel(DevParams p, const cc_template* __restrict__ tm, int64_t t_base,
         const int k = r >> 7;
         const KnotRec kr = knX ? load_knot(knX + k) : rec[k - kA];
         const SampleTiming st = sample_timing(p, kr, r, k * KNOT);
-        const float2 xv = use_window ? interp_sample_window(p, x, xs, win[0], win[1], st.jstar, st.delta)
+        const float2 xv = use_window ? interp_sample_window<DT>(p, x, xs, win[0], win[1], st.jstar, st.delta)
                               : interp_sample(p, x, st.jstar, st.delta);
         float sn, cs;
         sincospif(2.0f * st.psi, &sn, &cs);
@@ -327,15 +328,17 @@ cc_status launch_resample(cc_plan* plan, const cc_template* t_dev, int64_t n_t, 
     // leaves room for several blocks per SM
     const int use_window = kn && resample_smem_bytes(p, true) <= 96 * 1024;
     const size_t sm = kn ? (use_window ? resample_smem_bytes(p, true) : 0) : resample_smem_bytes(p, false);
+    // compile-time half width for the common stencils of the exact interpolator
+    const int DT = p.interp == CC_INTERP_EXACT && (p.D == 8 || p.D == 16) ? p.D : 0;
+    auto kern = DT == 8 ? resample_kernel<8> : DT == 16 ? resample_kernel<16> : resample_kernel<0>;
     if (sm > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(resample_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sm);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return cuda_fail(e, "resample smem attribute");
     }
     for (int64_t t0 = 0; t0 < n_t; t0 += MAX_GRID_YZ) {
         const int64_t nt = std::min<int64_t>(MAX_GRID_YZ, n_t - t0);
         dim3 grid((unsigned)p.M, (unsigned)p.Q, (unsigned)nt);
-        resample_kernel<<<grid, RS_THREADS, sm, st>>>(p, t_dev, t0, ab, (float4*)norm, kn, nkn, use_window);
+        kern<<<grid, RS_THREADS, sm, st>>>(p, t_dev, t0, ab, (float4*)norm, kn, nkn, use_window);
         count_launch();
     }
     cudaError_t e = cudaGetLastError();
