@@ -314,6 +314,16 @@ def run_gpu(args):
         traffic = None
         if path == cc.PATH_TWO_PASS and SEGPAIR_DRAM_BYTES_PER_TEMPLATE is not None and fused_launches:
             traffic = SEGPAIR_DRAM_BYTES_PER_TEMPLATE * B * args.steps / fused_launches
+        # the staged stage kernels are HBM-bound: algorithmic bytes (input read once,
+        # output written once) over their event-timed duration, against the measured copy peak
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        sbytes = {"resample": costs["resample_bytes"] + Q * ds.cfg.n_samples * 8,
+                  "segment_fft": costs["segfft_bytes"], "pair_accumulate": costs["pair_bytes"]}
+        staged_hbm = {k: {"GB/s": sbytes[k] / (stage_ms[k] / 1e3) / 1e9,
+                          "frac": sbytes[k] / (stage_ms[k] / 1e3) / 1e9 / hbm,
+                          "bytes_per_template": sbytes[k]} for k in sbytes}
+        staged_hbm["peak_GB/s"] = hbm
+        staged_hbm["peak_kind"] = f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind
         roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                 "traffic_unit": "bytes per launch (ncu capture, scaled by templates per launch)",
@@ -322,7 +332,7 @@ def run_gpu(args):
                 "kernel_ms_per_launch": fused_ms / max(fused_launches, 1),
                 "kernel_launches": fused_launches, "kernel_share_of_step": fused_ms / (1e3 * elapsed),
                 "other_kernels_ms_per_template": other_ms,
-                "staged_ms_per_template": stage_ms}
+                "staged_ms_per_template": stage_ms, "staged_hbm": staged_hbm}
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * elapsed / args.steps,

@@ -6,6 +6,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "fft_reg.cuh"
 
 namespace cc {
 
@@ -198,6 +199,48 @@ segfft_kernel(DevParams p, const void* ab, int64_t s_base, float2* __restrict__ 
         Fo[__ldg(p.coset_k + i)] = res[__ldg(p.coset_m + i)];
 }
 
+// Stage 2 for coset lengths 64..4096: the radix-16 register/shared-memory transform of
+// the fused kernels (first pass straight from the series with the coset twiddle, later
+// passes in padded shared memory), then the coset's output bins scattered to F.
+template <int LT>
+__global__ void __launch_bounds__(FFT_THREADS, 2)
+segfft_kernel_t(DevParams p, const void* ab, int64_t s_base, float2* __restrict__ F) {
+    extern __shared__ __align__(16) float2 buf[];
+    constexpr int L = LT, B1 = L / 16;
+    const int c = blockIdx.x;
+    const int64_t K = blockIdx.y;
+    const int64_t s = s_base + blockIdx.z;
+    const int tid = threadIdx.x;
+    const int64_t seg0 = K * p.N_s;
+    const int N_s = (int)p.N_s;
+    const size_t row = (size_t)s * p.N_tau + seg0;
+    const float2* __restrict__ twr = p.twc + (size_t)c * p.N_s;
+    const int offn = (int)((-seg0) & (int64_t)(L - 1));
+    auto sync = []() { __syncthreads(); };
+    if (tid < B1) {
+        float2 v[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            float2 acc = make_float2(0.f, 0.f);
+            for (int rr = (tid + r * B1 + offn) & (L - 1); rr < N_s; rr += L)
+                acc = cadd(acc, cmul(load_series(ab, p.store, row + rr), __ldg(twr + rr)));
+            v[r] = acc;
+        }
+        dft16(v);
+        float2* d = buf + 17 * tid;   // padi(16 tid + r)
+#pragma unroll
+        for (int r = 0; r < 16; ++r) d[r] = v[r];
+    }
+    __syncthreads();
+    stockham_rest_t<L, 16>(buf, tid, p.twL, sync);
+    const int64_t tX = s >> 1;
+    const int w = (int)(s & 1);
+    float2* Fo = F + ((tX * p.M + K) * 2 + w) * p.N_f;
+    const int e = __ldg(p.coset_off + c + 1);
+    for (int i = __ldg(p.coset_off + c) + tid; i < e; i += FFT_THREADS)
+        Fo[__ldg(p.coset_k + i)] = buf[padi(__ldg(p.coset_m + i))];
+}
+
 // Sum over the pair set of (A_i A_j + B_i B_j + 2 C_i C_j), one block per template.
 __device__ __forceinline__ double nn(float4 a, float4 b) {
     return (double)a.x * b.x + (double)a.y * b.y + 2.0 * (double)a.z * b.z;
@@ -292,6 +335,72 @@ pair_kernel(DevParams p, const float2* __restrict__ F, int64_t t_base, int64_t c
     raw[((size_t)t * gridDim.y + blockIdx.y) * Nf + k] = sum;
 }
 
+// Stage 3 for R <= 1: each segment's spectra are read once; the previous segment's stay
+// in registers.  Same pair terms and order as pair_kernel.  Four segments per step so
+// 4 x 2 x Q loads are in flight per thread.
+template <int U, int QT>
+__global__ void __launch_bounds__(PAIR_THREADS)
+pair_kernel_r1(DevParams p, const float2* __restrict__ F, int64_t t_base, int64_t chunk_len,
+               float* __restrict__ raw) {
+    const int64_t t = t_base + blockIdx.z;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= p.N_f) return;
+    constexpr int Q = QT;
+    const int64_t M = p.M, Nf = p.N_f;
+    const int mode = p.pair_mode;
+    const bool lag = p.R > 0;
+    const int64_t Ka = (int64_t)blockIdx.y * chunk_len;
+    const int64_t Kb = Ka + chunk_len < M ? Ka + chunk_len : M;
+    const float2* __restrict__ Ft = F + (size_t)t * Q * M * 2 * Nf + k;
+    auto Fat = [&](int X, int64_t K, int w) -> float2 {
+        return __ldg(Ft + (((size_t)X * M + K) * 2 + w) * Nf);
+    };
+    float2 prev[2][QT];
+#pragma unroll
+    for (int w = 0; w < 2; ++w)
+#pragma unroll
+        for (int X = 0; X < QT; ++X)
+            prev[w][X] = (lag && Ka > 0) ? Fat(X, Ka - 1, w) : make_float2(0.f, 0.f);
+    float sum = 0.f, comp = 0.f;
+    for (int64_t K0 = Ka; K0 < Kb; K0 += U) {
+        float2 cur[U][2][QT];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int w = 0; w < 2; ++w)
+#pragma unroll
+                for (int X = 0; X < QT; ++X)
+                    cur[u][w][X] = (K0 + u < Kb) ? Fat(X, K0 + u, w) : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (K0 + u >= Kb) break;
+            float term = 0.f;
+#pragma unroll
+            for (int w = 0; w < 2; ++w) {
+                float2 win = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int X = 0; X < QT; ++X) win = cadd(win, prev[w][X]);
+                float2 same = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int Y = 0; Y < QT; ++Y) {
+                    const float2 h = cadd(same, mode == CC_PAIRS_CROSS_ONLY ? csub(win, prev[w][Y]) : win);
+                    float tY = redot(cur[u][w][Y], h);
+                    if (mode == CC_PAIRS_ALL_ORDERED) tY = fmaf(2.f, tY, redot(cur[u][w][Y], cur[u][w][Y]));
+                    term += tY;
+                    same = cadd(same, cur[u][w][Y]);
+                }
+            }
+            kahan_add(sum, comp, term);
+#pragma unroll
+            for (int w = 0; w < 2; ++w)
+#pragma unroll
+                for (int X = 0; X < QT; ++X)
+                    if (lag) prev[w][X] = cur[u][w][X];
+        }
+    }
+    raw[((size_t)t * gridDim.y + blockIdx.y) * Nf + k] = sum;
+}
+
 __global__ void pair_finalize_kernel(const float* __restrict__ raw, const double* __restrict__ Dn,
                                      int64_t N_f, int n_chunks, int64_t t_base, float* __restrict__ rho) {
     const int64_t t = t_base + blockIdx.y;
@@ -345,8 +454,29 @@ cc_status launch_resample(cc_plan* plan, const cc_template* t_dev, int64_t n_t, 
     return e == cudaSuccess ? CC_OK : cuda_fail(e, "resample launch");
 }
 
+template <int LT>
+static const void* segfft_t_ptr() { return (const void*)segfft_kernel_t<LT>; }
+
 cc_status launch_segfft(cc_plan* plan, const void* ab, int64_t n_t, void* F, cudaStream_t st) {
     const DevParams& p = plan->dp;
+    const void* kt = p.L == 64 ? segfft_t_ptr<64>() : p.L == 128 ? segfft_t_ptr<128>() : p.L == 256 ? segfft_t_ptr<256>()
+                   : p.L == 512 ? segfft_t_ptr<512>() : p.L == 1024 ? segfft_t_ptr<1024>()
+                   : p.L == 2048 ? segfft_t_ptr<2048>() : p.L == 4096 ? segfft_t_ptr<4096>() : nullptr;
+    if (kt) {
+        const size_t smt = (size_t)padded_len(p.L) * sizeof(float2);
+        cudaError_t e = cudaFuncSetAttribute(kt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smt);
+        if (e != cudaSuccess) return cuda_fail(e, "segment fft smem attribute");
+        const int64_t ns = n_t * p.Q * 2;
+        for (int64_t s0 = 0; s0 < ns; s0 += MAX_GRID_YZ) {
+            const int64_t n = std::min<int64_t>(MAX_GRID_YZ, ns - s0);
+            dim3 grid((unsigned)p.C, (unsigned)p.M, (unsigned)n);
+            void* args[] = {(void*)&p, (void*)&ab, (void*)&s0, (void*)&F};
+            e = cudaLaunchKernel(kt, grid, dim3(FFT_THREADS), args, smt, st);
+            count_launch();
+            if (e != cudaSuccess) return cuda_fail(e, "segment fft launch");
+        }
+        return CC_OK;
+    }
     const size_t sm = (size_t)2 * p.L * sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(segfft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return cuda_fail(e, "segment fft smem attribute");
@@ -372,7 +502,16 @@ cc_status launch_norm_pairs(cc_plan* plan, const void* F, const float* norm, int
         norm_kernel<<<(unsigned)nt, 256, 0, st>>>(p, (const float4*)norm, t0, Dws);
         count_launch();
         dim3 grid((unsigned)launch_blocks_for(p.N_f, PAIR_THREADS), (unsigned)nchr, (unsigned)nt);
-        pair_kernel<<<grid, PAIR_THREADS, 0, st>>>(p, (const float2*)F, t0, clen, rawws);
+        if (p.R <= 1 && p.Q == 1)
+            pair_kernel_r1<4, 1><<<grid, PAIR_THREADS, 0, st>>>(p, (const float2*)F, t0, clen, rawws);
+        else if (p.R <= 1 && p.Q == 2)
+            pair_kernel_r1<4, 2><<<grid, PAIR_THREADS, 0, st>>>(p, (const float2*)F, t0, clen, rawws);
+        else if (p.R <= 1 && p.Q == 3)
+            pair_kernel_r1<4, 3><<<grid, PAIR_THREADS, 0, st>>>(p, (const float2*)F, t0, clen, rawws);
+        else if (p.R <= 1)
+            pair_kernel_r1<4, 4><<<grid, PAIR_THREADS, 0, st>>>(p, (const float2*)F, t0, clen, rawws);
+        else
+            pair_kernel<<<grid, PAIR_THREADS, 0, st>>>(p, (const float2*)F, t0, clen, rawws);
         count_launch();
         dim3 g2((unsigned)launch_blocks_for(p.N_f, 256), (unsigned)nt);
         pair_finalize_kernel<<<g2, 256, 0, st>>>(rawws, Dws, p.N_f, (int)nchr, t0, rho);
