@@ -233,12 +233,16 @@ segfft_kernel_t(DevParams p, const void* ab, int64_t s_base, float2* __restrict_
     }
     __syncthreads();
     stockham_rest_t<L, 16>(buf, tid, p.twL, sync);
+    // the segment-relative twiddles leave out the segment-start phase W_N^((b0 + c) seg0)
+    const uint64_t N = (uint64_t)p.N_FFT, mask = N - 1;
+    const uint64_t bc = ((uint64_t)p.b0 + (uint64_t)c) & mask;
+    const float2 wseg = twiddle_N((bc * ((uint64_t)seg0 & mask)) & mask, N);
     const int64_t tX = s >> 1;
     const int w = (int)(s & 1);
     float2* Fo = F + ((tX * p.M + K) * 2 + w) * p.N_f;
     const int e = __ldg(p.coset_off + c + 1);
     for (int i = __ldg(p.coset_off + c) + tid; i < e; i += FFT_THREADS)
-        Fo[__ldg(p.coset_k + i)] = buf[padi(__ldg(p.coset_m + i))];
+        Fo[__ldg(p.coset_k + i)] = cmul(buf[padi(__ldg(p.coset_m + i))], wseg);
 }
 
 // Sum over the pair set of (A_i A_j + B_i B_j + 2 C_i C_j), one block per template.
