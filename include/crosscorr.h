@@ -274,6 +274,24 @@ typedef struct {
 } cc_tuning;
 cc_status crosscorr_plan_set_tuning(cc_plan* plan, const cc_tuning* tuning);
 
+/* Detector-frame ("demodulation") CrossCorr, the statistic the resampled method replaces
+ * (Sec. II: Eqs. fourier-transform-def, normalized-z-bin, total-data-eq, geometric-filter,
+ * norm-cc, textbook-cc-rho), at the plan's output frequencies on the same data, for
+ * comparison.  SFTs are the locked T_sft blocks (T_sft / dt in 2..16384 samples);
+ * Gamma^ave_KL pairs every two distinct SFTs whose mid-times differ by at most T_max
+ * (each unordered pair once); n_bin = 2 sinc-weighted bins per SFT; each pair is
+ * weighted by Xi_K Xi_L and N normalises rho to unit variance in noise.
+ *
+ * crosscorr_demod_prepare computes the SFT bins a signal of the band can reach for
+ * Doppler factors |dtau/dt - 1| <= doppler_max (0 selects 5e-4) from x_dev (Q device
+ * pointers to complex64[N_t], as for crosscorr_search) into plan-owned device memory,
+ * asynchronously on `stream`; crosscorr_demod_search then writes rho to
+ * rho_dev[n_t][N_f] (device) for device templates t_dev[n_t], asynchronously. */
+cc_status crosscorr_demod_prepare(cc_plan* plan, const void* const* x_dev, int32_t n_bin, double doppler_max,
+                                  void* stream);
+cc_status crosscorr_demod_search(cc_plan* plan, const cc_template* t_dev, int64_t n_t, float* rho_dev,
+                                 void* stream);
+
 /* The k largest rho over (template, bin) of a device float[n_t][N_f] array,
  * descending, ties by (template, bin) ascending; hits_host receives
  * min(k, n_t*N_f) records.  Synchronises the stream.  1 <= k <= 4096. */

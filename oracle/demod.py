@@ -150,11 +150,13 @@ def demod_rho(ds, tmpl, freqs: Optional[np.ndarray] = None, n_bin: int = 2, T_ma
     AH, BH = np.concatenate(AH), np.concatenate(BH)
     raw = np.zeros(len(f))
     den = np.zeros(len(f))
+    order = np.argsort(T, kind="stable")        # each unordered pair once, visited in time order
+    T, Y, XI, AH, BH = T[order], Y[order], XI[order], AH[order], BH[order]
     n = len(T)
     for K in range(n):
         for L in range(K + 1, n):
-            if abs(T[K] - T[L]) > T_max + 1e-9:
-                continue
+            if T[L] - T[K] > T_max + 1e-9:
+                break
             g = (AH[K] * AH[L] + BH[K] * BH[L]) / 10.0
             # Xi_K Xi_L (e^{i(Phi_K - Phi_L)} z_K* z_L + c.c.) = 2 Re(conj(Y_K) Y_L)
             raw += g * 2.0 * np.real(np.conj(Y[K]) * Y[L])

@@ -239,6 +239,23 @@ class CrossCorrPlan:
         t = CcTuning(int(batch_templates), int(chunk_waves), 0)
         check("crosscorr_plan_set_tuning", self._lib.crosscorr_plan_set_tuning(self._h, byref(t)))
 
+    def demod_prepare(self, x, n_bin: int = 2, doppler_max: float = 0.0, stream=None):
+        """Detector-frame (demodulation) search, step 1: SFTs of the locked T_sft blocks."""
+        xp, self._demod_x = self._xptrs(x)
+        check("crosscorr_demod_prepare", self._lib.crosscorr_demod_prepare(
+            self._h, xp, int(n_bin), float(doppler_max), _stream_handle(stream)))
+
+    def demod_search(self, templates, rho=None, stream=None):
+        """Detector-frame (demodulation) rho [n_t, N_f] at the plan's output frequencies."""
+        import torch
+        n_t = self._templates(templates)
+        if rho is None:
+            rho = torch.empty((n_t, self.N_f), dtype=torch.float32, device=templates.device)
+        _check_tensor("rho", rho, torch.float32)
+        check("crosscorr_demod_search", self._lib.crosscorr_demod_search(
+            self._h, _dptr(templates), n_t, _dptr(rho), _stream_handle(stream)))
+        return rho
+
     def set_kernel_timing(self, on: bool = True):
         """Diagnostic: bracket each fused-kernel launch with CUDA events on its stream."""
         check("crosscorr_plan_set_kernel_timing", self._lib.crosscorr_plan_set_kernel_timing(self._h, int(on)))

@@ -133,6 +133,14 @@ struct cc_plan {
     bool kernel_timing = false;
     std::vector<cudaEvent_t> timing_events;   // [2 * n] start, stop
     size_t timing_used = 0;                   // pairs recorded since the last read
+    // detector-frame (demodulation) search: SFT bins and weights, twiddles, bin tables
+    void* demod_z = nullptr;                  // [Q][n_blk][nbins] float2
+    void* demod_w = nullptr;                  // [Q][n_blk] float4 (a^, b^, locked, 0)
+    void* demod_tw = nullptr;                 // [nsft] float2
+    void* demod_df = nullptr;                 // [N_f] double: f - f_h of the output bins
+    void* demod_kbar = nullptr;               // [N_f] int64
+    bool demod_ready = false;
+    int demod_nsft = 0, demod_m_lo = 0, demod_nbins = 0, demod_nblk = 0;
     // workspace (grown on demand by staged/fused paths)
     void* ws = nullptr;
     size_t ws_bytes = 0;

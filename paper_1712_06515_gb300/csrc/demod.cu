@@ -1,0 +1,349 @@
+// Detector-frame ("demodulation") CrossCorr: the statistic the resampled method
+// replaces (Sec. II: Eqs. fourier-transform-def, normalized-z-bin, total-data-eq,
+// geometric-filter, norm-cc, textbook-cc-rho), evaluated at the plan's output
+// frequencies on the same data, so the two methods can be compared on one GPU.
+//
+//   crosscorr_demod_prepare: short Fourier transforms of every locked T_sft block, only
+//     the bins a signal in the band can reach (direct DFT with an exact integer twiddle
+//     index), normalised to unit variance, and per SFT the filter weights
+//     a^ = sqrt(2 T_sft / S) a(t_K), b^ likewise (S = 2 sigma^2 dt);
+//   crosscorr_demod_search: per template an FP64 pass gives, per SFT, the signal's bin
+//     position and phase as linear functions of the output bin; one thread per
+//     (template, output bin) then walks the SFTs in time order, forms
+//     y_K = sum_m (-1)^m sinc(kappa_Km) z_Km exp(-i Phi_K) (= Xi_K z_K exp(-i Phi_K)) and
+//     sums Gamma_KL 2 Re(conj(y_K) y_L) over every earlier SFT L within T_max (the pair
+//     loop of the method, each unordered pair once), with the normalisation
+//     sum (Xi_K Xi_L Gamma_KL)^2 alongside; rho = raw / sqrt(2 den).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+
+namespace cc {
+cc_status set_inputs(cc_plan* plan, const void* const* x_dev);
+
+namespace {
+
+constexpr int SFT_THREADS = 256;
+constexpr int DM_MAX_SFT_SAMPLES = 16384;   // T_sft / dt staged in shared memory
+constexpr size_t DM_RING_BUDGET = 160 * 1024;
+
+struct DemodTiming {   // per (template, detector, SFT block): 32 bytes
+    float A0, A1;       // signal bin position x = A0 + df A1 (df = f - f_h of the output bin)
+    float C0, C1;       // heterodyned phase (cycles) = C0 + kbar C1 with kbar = 128 kh + kl:
+    float C128, pad0;   //   C0 + kh C128 + kl C1 (mod 1)
+    float pad1, pad2;
+};
+
+// DFT bins m_lo .. m_lo + nbins - 1 of one T_sft block of detector X, normalised to unit
+// variance; zero for gaps.  Also the block's filter weights (a^, b^, locked).
+__global__ void __launch_bounds__(SFT_THREADS)
+sft_kernel(DevParams p, int nsft, int m_lo, int nbins, int n_blk, const float2* __restrict__ tw,
+           float2* __restrict__ z, float4* __restrict__ wts) {
+    extern __shared__ __align__(16) float2 xs[];
+    const int l = blockIdx.x, X = blockIdx.y;
+    float2* zo = z + ((size_t)X * n_blk + l) * nbins;
+    const float2 sw = (l < (int)p.n_sig[X]) ? __ldg(p.sigw[X] + l) : make_float2(0.f, 0.f);
+    const bool locked = sw.x > 0.f;
+    if (threadIdx.x == 0) {
+        float ah = 0.f, bh = 0.f;
+        if (locked) {
+            // a, b at the mid-time (linear in the table, end intervals extrapolated)
+            const double tm = (double)l * nsft + 0.5 * nsft;
+            const double fr = (tm - (double)p.ab_j0) / (double)p.n_ab_step;
+            int64_t i = (int64_t)floor(fr);
+            const int64_t nab = p.n_ab[X];
+            i = i < 0 ? 0 : (i > nab - 2 ? nab - 2 : i);
+            const double f = fr - (double)i;
+            const double a = __ldg(p.atab[X] + i) + f * (__ldg(p.atab[X] + i + 1) - __ldg(p.atab[X] + i));
+            const double b = __ldg(p.btab[X] + i) + f * (__ldg(p.btab[X] + i + 1) - __ldg(p.btab[X] + i));
+            const double sc = sqrt((double)nsft * (double)sw.y);   // sqrt(2 T_sft / S) = sqrt(nsft / sigma^2)
+            ah = (float)(sc * a);
+            bh = (float)(sc * b);
+        }
+        wts[(size_t)X * n_blk + l] = make_float4(ah, bh, locked ? 1.f : 0.f, 0.f);
+    }
+    if (!locked) {
+        for (int i = threadIdx.x; i < nbins; i += blockDim.x) zo[i] = make_float2(0.f, 0.f);
+        return;
+    }
+    const float2* __restrict__ x = p.x[X] + (size_t)l * nsft;
+    for (int j = threadIdx.x; j < nsft; j += blockDim.x) xs[j] = __ldg(x + j);
+    __syncthreads();
+    const float norm = sqrtf(sw.y / (float)nsft);   // dt sqrt(2 / (T_sft S)) = 1 / (sigma sqrt(nsft))
+    for (int i = threadIdx.x; i < nbins; i += blockDim.x) {
+        const int m = m_lo + i;
+        const int step = ((m % nsft) + nsft) % nsft;     // exp(-2 pi i j m / nsft) = tw[(j m) mod nsft]
+        int idx = 0;
+        float2 acc = make_float2(0.f, 0.f);
+        for (int j = 0; j < nsft; ++j) {
+            const float2 w = tw[idx];
+            const float2 v = xs[j];
+            acc.x = fmaf(v.x, w.x, fmaf(-v.y, w.y, acc.x));
+            acc.y = fmaf(v.x, w.y, fmaf(v.y, w.x, acc.y));
+            idx += step;
+            idx -= idx >= nsft ? nsft : 0;
+        }
+        zo[i] = make_float2(acc.x * norm, acc.y * norm);
+    }
+}
+
+// Per (template, detector, SFT block): the signal's heterodyned bin position and phase as
+// functions of the output bin, in FP64 reduced to FP32 pieces.
+__global__ void demod_timing_kernel(DevParams p, const cc_template* __restrict__ tm, int nsft, int n_blk,
+                                    double df0, double dK, DemodTiming* __restrict__ out) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    const int X = blockIdx.y;
+    const int64_t t = blockIdx.z;
+    if (l >= n_blk) return;
+    const cc_template T = tm[t];
+    const double tmid = ((double)l * nsft + 0.5 * nsft) * p.dt;   // relative to t0
+    // Delta_X(t) and its slope (linear interpolation of the table)
+    const double u = (tmid - p.eph_t0[X]) * p.inv_eph_dt[X];
+    int64_t i = (int64_t)floor(u);
+    const int64_t n = p.n_eph[X];
+    i = i < 0 ? 0 : (i > n - 2 ? n - 2 : i);
+    const double d0 = __ldg(p.ssb[X] + i), d1 = __ldg(p.ssb[X] + i + 1);
+    const double dl = d0 + (u - (double)i) * (d1 - d0);
+    const double ddl = (d1 - d0) * p.inv_eph_dt[X];
+    // binary delay at t_SSB and dtau/dt (Eqs. t-ssb-equation, tau-equation)
+    const double invP = 1.0 / T.P;
+    double s, c;
+    sincospi(2.0 * ((tmid + dl - (T.T_asc - p.t0)) * invP), &s, &c);
+    const double d = dl - T.a_p * s;                                   // tau - t
+    const double dtau = (1.0 + ddl) * (1.0 - T.a_p * 6.283185307179586 * invP * c);
+    const double Tsft = nsft * p.dt;
+    DemodTiming r;
+    // x = (f (dtau - 1) + df) T_sft with f = f_h + df
+    r.A0 = (float)(p.f_h * (dtau - 1.0) * Tsft);
+    r.A1 = (float)(dtau * Tsft);
+    // phase f tau - f_h t = f_h d + df (t + d), df = df0 + kbar dK
+    const double tau = tmid + d;
+    const double c0 = p.f_h * d + df0 * tau;
+    const double c1 = dK * tau, c128 = 128.0 * dK * tau;
+    r.C0 = (float)(c0 - floor(c0));
+    r.C1 = (float)(c1 - floor(c1));
+    r.C128 = (float)(c128 - floor(c128));
+    r.pad0 = r.pad1 = r.pad2 = 0.f;
+    out[((size_t)t * p.Q + X) * n_blk + l] = r;
+}
+
+// One thread per (template, output bin): the pair loop over time-ordered SFTs.  The ring
+// holds the last (R_s + 1) blocks' y and Xi^2 per thread (thread-private columns of
+// shared memory) and the blocks' filter weights (shared by the CTA).
+__global__ void demod_pair_kernel(DevParams p, int nsft, int m_lo, int nbins, int n_blk, int Rs,
+                                  const float2* __restrict__ z, const float4* __restrict__ wts,
+                                  const DemodTiming* __restrict__ tq, const double* __restrict__ dfreq,
+                                  const int64_t* __restrict__ kbar, int64_t t_base, float* __restrict__ rho) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int nthr = blockDim.x, tid = threadIdx.x;
+    const int Q = p.Q;
+    const int W = (Rs + 1) * Q;                        // ring slots: block l at slots (l mod (Rs+1)) Q + X
+    float2* ry = (float2*)sm;                          // [W][nthr]
+    float* rx = (float*)(ry + (size_t)W * nthr);       // [W][nthr] Xi^2
+    float2* rab = (float2*)(rx + (size_t)W * nthr);    // [W] (a^, b^)
+    int* rblk = (int*)(rab + W);                       // [W] block index held, -1 empty
+    const int64_t t = t_base + blockIdx.y;
+    const int k = blockIdx.x * nthr + tid;
+    const bool act = k < (int)p.N_f;
+    for (int j = tid; j < W; j += nthr) rblk[j] = -1;
+    const float df = act ? (float)__ldg(dfreq + k) : 0.f;
+    const int64_t kb = act ? __ldg(kbar + k) : 0;
+    const float kh = (float)(kb >> 7), kl = (float)(kb & 127);
+    float raw = 0.f, rawc = 0.f, den = 0.f, denc = 0.f;
+    __syncthreads();
+    for (int l = 0; l < n_blk; ++l) {
+        const int base = (l % (Rs + 1)) * Q;
+        for (int X = 0; X < Q; ++X) {
+            const float4 wk = __ldg(wts + (size_t)X * n_blk + l);
+            const int slot = base + X;
+            if (wk.z == 0.f) {                          // gap: no SFT (uniform across the CTA)
+                __syncthreads();
+                if (tid == 0) rblk[slot] = -1;
+                __syncthreads();
+                continue;
+            }
+            const DemodTiming tr = tq[((size_t)(t - t_base) * Q + X) * n_blk + l];
+            const float x = fmaf(df, tr.A1, tr.A0);
+            const float fm = floorf(x);
+            const float k0 = fm - x;                   // kappa of bin floor(x), in (-1, 0]
+            float s0, s1;
+            if (k0 == 0.f) {
+                s0 = 1.f;
+                s1 = 0.f;
+            } else {
+                const float sp = sinpif(k0) * 0.318309886183790672f;   // sin(pi kappa)/pi
+                s0 = __fdividef(sp, k0);
+                s1 = -__fdividef(sp, k0 + 1.f);        // sin(pi (kappa + 1)) = -sin(pi kappa)
+            }
+            const int m0 = (int)fm;
+            const int idx = m0 - m_lo;
+            float2 y = make_float2(0.f, 0.f);
+            if (act && idx >= 0 && idx + 1 < nbins) {
+                const float2* zk = z + ((size_t)X * n_blk + l) * nbins + idx;
+                const float2 z0 = __ldg(zk), z1 = __ldg(zk + 1);
+                const float sg = (m0 & 1) ? -1.f : 1.f;
+                const float2 u = make_float2(sg * (s0 * z0.x - s1 * z1.x), sg * (s0 * z0.y - s1 * z1.y));
+                float cyc = fmaf(kl, tr.C1, fmaf(kh, tr.C128, tr.C0));
+                cyc -= floorf(cyc);
+                float sn, cs;
+                sincospif(2.0f * cyc, &sn, &cs);
+                y = make_float2(fmaf(u.x, cs, u.y * sn), fmaf(u.y, cs, -u.x * sn));   // u exp(-2 pi i cyc)
+            }
+            const float xi2 = s0 * s0 + s1 * s1;
+            // partners: the blocks l - Rs .. l - 1 (every detector) and block l's earlier detectors
+            float pr = 0.f, pd = 0.f;
+            for (int j = 0; j < W; ++j) {
+                const int bj = rblk[j];
+                if (bj < 0 || l - bj > Rs) continue;
+                if (bj == l && j - base >= X) continue;
+                const float2 ab = rab[j];
+                const float g = 0.1f * fmaf(wk.x, ab.x, wk.y * ab.y);
+                const float2 yl = ry[(size_t)j * nthr + tid];
+                pr = fmaf(g, 2.f * fmaf(y.x, yl.x, y.y * yl.y), pr);
+                const float q = g * g * rx[(size_t)j * nthr + tid];
+                pd = fmaf(xi2, q, pd);
+            }
+            kahan_add(raw, rawc, pr);
+            kahan_add(den, denc, pd);
+            __syncthreads();                            // every thread is done with the old slot
+            ry[(size_t)slot * nthr + tid] = y;
+            rx[(size_t)slot * nthr + tid] = xi2;
+            if (tid == 0) {
+                rab[slot] = make_float2(wk.x, wk.y);
+                rblk[slot] = l;
+            }
+            __syncthreads();
+        }
+    }
+    if (act) rho[(size_t)t * p.N_f + k] = den > 0.f ? raw / sqrtf(2.f * den) : 0.f;
+}
+
+}  // namespace
+}  // namespace cc
+
+using namespace cc;
+
+extern "C" cc_status crosscorr_demod_prepare(cc_plan* plan, const void* const* x_dev, int32_t n_bin,
+                                             double doppler_max, void* stream) {
+    if (!plan) return fail(CC_ERR_INVALID, "plan is null");
+    if (n_bin != 2) return fail(CC_ERR_UNSUPPORTED, "demodulation search implemented for n_bin = 2");
+    if (!(doppler_max >= 0) || doppler_max > 0.01) return fail(CC_ERR_INVALID, "doppler_max must be in [0, 0.01]");
+    if (doppler_max == 0) doppler_max = 5e-4;
+    int64_t nsft = 0;
+    {
+        const double r = plan->cfg.T_sft / plan->cfg.dt;
+        nsft = (int64_t)llround(r);
+    }
+    if (nsft < 2 || nsft > DM_MAX_SFT_SAMPLES) return fail(CC_ERR_UNSUPPORTED, "T_sft / dt must be 2..16384");
+    cc_status s = set_inputs(plan, x_dev);
+    if (s != CC_OK) return s;
+    const DevParams& p = plan->dp;
+    const int64_t n_blk = p.N_t / nsft;
+    if (n_blk < 1) return fail(CC_ERR_INVALID, "series shorter than one SFT");
+    // bins a signal of the band can reach: |f - f_h| <= max |df| plus Doppler and the kernel
+    double dmin = 1e300, dmax = -1e300;
+    for (double f : plan->freq) {
+        dmin = std::min(dmin, f - plan->cfg.f_h);
+        dmax = std::max(dmax, f - plan->cfg.f_h);
+    }
+    const double Tsft = nsft * plan->cfg.dt;
+    const double wing = doppler_max * (plan->cfg.f_h + std::max(std::fabs(dmin), std::fabs(dmax))) * Tsft;
+    const int m_lo = (int)std::floor(dmin * Tsft - wing) - 2;
+    const int m_hi = (int)std::ceil(dmax * Tsft + wing) + 2;
+    const int nbins = m_hi - m_lo + 1;
+    if (nbins > nsft) return fail(CC_ERR_UNSUPPORTED, "band plus Doppler wider than an SFT");
+    // device arrays (plan-owned; replaced on a new prepare)
+    cudaError_t e;
+    for (void* ptr : {plan->demod_z, plan->demod_w, plan->demod_tw})
+        if (ptr) cudaFree(ptr);
+    plan->demod_z = plan->demod_w = plan->demod_tw = nullptr;
+    plan->demod_ready = false;
+    std::vector<float2> tw(nsft);
+    for (int64_t j = 0; j < nsft; ++j) {
+        const double a = -2.0 * M_PI * (double)j / (double)nsft;
+        tw[j] = make_float2((float)cos(a), (float)sin(a));
+    }
+    if ((e = cudaMalloc(&plan->demod_tw, sizeof(float2) * nsft)) != cudaSuccess ||
+        (e = cudaMalloc(&plan->demod_z, sizeof(float2) * (size_t)p.Q * n_blk * nbins)) != cudaSuccess ||
+        (e = cudaMalloc(&plan->demod_w, sizeof(float4) * (size_t)p.Q * n_blk)) != cudaSuccess)
+        return cuda_fail(e, "demodulation SFT allocation");
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((e = cudaMemcpyAsync(plan->demod_tw, tw.data(), sizeof(float2) * nsft, cudaMemcpyHostToDevice, st)) !=
+        cudaSuccess)
+        return cuda_fail(e, "demodulation twiddles");
+    const size_t smem = sizeof(float2) * nsft;
+    if (smem > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(sft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+        return cuda_fail(e, "sft smem attribute");
+    sft_kernel<<<dim3((unsigned)n_blk, (unsigned)p.Q), SFT_THREADS, smem, st>>>(
+        p, (int)nsft, m_lo, nbins, (int)n_blk, (const float2*)plan->demod_tw, (float2*)plan->demod_z,
+        (float4*)plan->demod_w);
+    count_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "sft_kernel launch");
+    // host copies the search needs: output bins' df (FP64) and kbar
+    if (!plan->demod_df) {
+        if ((e = cudaMalloc(&plan->demod_df, sizeof(double) * plan->N_f)) != cudaSuccess ||
+            (e = cudaMalloc(&plan->demod_kbar, sizeof(int64_t) * plan->N_f)) != cudaSuccess)
+            return cuda_fail(e, "demodulation bin tables");
+        std::vector<double> df(plan->N_f);
+        for (int64_t i = 0; i < plan->N_f; ++i)
+            df[i] = (plan->f_r - 0.5 / plan->cfg.dt) + (double)plan->kbar[i] / plan->T_FFT;
+        if ((e = cudaMemcpy(plan->demod_df, df.data(), sizeof(double) * plan->N_f, cudaMemcpyHostToDevice)) !=
+                cudaSuccess ||
+            (e = cudaMemcpy(plan->demod_kbar, plan->kbar.data(), sizeof(int64_t) * plan->N_f,
+                            cudaMemcpyHostToDevice)) != cudaSuccess)
+            return cuda_fail(e, "demodulation bin tables");
+    }
+    plan->demod_nsft = (int)nsft;
+    plan->demod_m_lo = m_lo;
+    plan->demod_nbins = nbins;
+    plan->demod_nblk = (int)n_blk;
+    plan->demod_ready = true;
+    return CC_OK;
+}
+
+extern "C" cc_status crosscorr_demod_search(cc_plan* plan, const cc_template* t_dev, int64_t n_t, float* rho_dev,
+                                            void* stream) {
+    if (!plan) return fail(CC_ERR_INVALID, "plan is null");
+    if (n_t < 0) return fail(CC_ERR_INVALID, "n_t must be >= 0");
+    if (!plan->demod_ready) return fail(CC_ERR_INVALID, "call crosscorr_demod_prepare first");
+    if (n_t == 0) return CC_OK;
+    if (!t_dev || !rho_dev) return fail(CC_ERR_INVALID, "null device pointer");
+    const DevParams& p = plan->dp;
+    const int n_blk = plan->demod_nblk, nsft = plan->demod_nsft;
+    const double Tsft = nsft * plan->cfg.dt;
+    const int Rs = (int)std::floor(plan->cfg.T_max / Tsft + 1e-9);
+    const int W = (Rs + 1) * p.Q;
+    int nthr = 256;
+    auto ring_bytes = [&](int nt) { return (size_t)W * nt * 12 + (size_t)W * 12 + 64; };
+    while (nthr > 32 && ring_bytes(nthr) > DM_RING_BUDGET) nthr /= 2;
+    if (ring_bytes(nthr) > DM_RING_BUDGET) return fail(CC_ERR_UNSUPPORTED, "T_max / T_sft too large for the pair ring");
+    // timing records for a batch of templates
+    const size_t per_t = sizeof(DemodTiming) * (size_t)p.Q * n_blk;
+    const int64_t batch = std::max<int64_t>(1, std::min<int64_t>({n_t, (int64_t)((size_t)2 << 30) / (int64_t)per_t, 65535}));
+    cc_status s = ensure_workspace(plan, per_t * batch);
+    if (s != CC_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    const size_t smem = ring_bytes(nthr);
+    if (smem > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(demod_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+        return cuda_fail(e, "demodulation smem attribute");
+    const double df0 = plan->f_r - 0.5 / plan->cfg.dt, dK = 1.0 / plan->T_FFT;
+    for (int64_t t0 = 0; t0 < n_t; t0 += batch) {
+        const int64_t nb = std::min(batch, n_t - t0);
+        demod_timing_kernel<<<dim3((unsigned)((n_blk + 127) / 128), (unsigned)p.Q, (unsigned)nb), 128, 0, st>>>(
+            p, t_dev + t0, nsft, n_blk, df0, dK, (DemodTiming*)plan->ws);
+        count_launch();
+        demod_pair_kernel<<<dim3((unsigned)((plan->N_f + nthr - 1) / nthr), (unsigned)nb), nthr, smem, st>>>(
+            p, nsft, plan->demod_m_lo, plan->demod_nbins, n_blk, Rs, (const float2*)plan->demod_z,
+            (const float4*)plan->demod_w, (const DemodTiming*)plan->ws, (const double*)plan->demod_df,
+            (const int64_t*)plan->demod_kbar, t0, rho_dev);
+        count_launch();
+    }
+    e = cudaGetLastError();
+    return e == cudaSuccess ? CC_OK : cuda_fail(e, "demodulation launch");
+}

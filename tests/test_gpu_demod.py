@@ -1,0 +1,85 @@
+"""The detector-frame ("demodulation") CrossCorr on the GPU, through the C ABI, against
+the FP64 oracle (oracle/demod.py): per template max |drho| <= 1e-4 max(1, max|rho|)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import demod
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU hosts too
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1712_06515_gb300 as cc  # noqa: E402
+from paper_1712_06515_gb300 import _lib  # noqa: E402
+
+DEV = torch.device("cuda:0")
+TOL = 1e-4
+INJ = synth.Injection(h0=0.4, f0=120.1, a_p=1.44, T_asc=synth.T_ASC_O1, P=synth.SCO_X1_P)
+
+
+def assert_close(got, ref, tol=TOL):
+    for t in range(ref.shape[0]):
+        err = float(np.abs(got[t] - ref[t]).max())
+        lim = tol * max(1.0, float(np.abs(ref[t]).max()))
+        assert err <= lim, f"template {t}: max |drho| = {err:.3e} > {lim:.3e}"
+
+
+def gpu_demod(ds, templates=None):
+    tm = ds.templates if templates is None else templates
+    with cc.CrossCorrPlan(ds.cfg, ds.dets) as plan:
+        x = torch.from_numpy(ds.x64).to(DEV)
+        plan.demod_prepare(x)
+        return plan.demod_search(torch.from_numpy(np.ascontiguousarray(tm)).to(DEV)).cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(T_max=0.0, T_short=64.0), dict(T_max=256.0, T_short=128.0),
+                                dict(n_det=1), dict(n_det=3), dict(n_samples=4096 + 77),
+                                dict(T_sft=32.0, T_max=160.0, T_short=160.0)])
+def test_demod_parity(kw):
+    ds = synth.tiny(seed=33, n_templates=3, injection=INJ, **kw)
+    ref = np.stack([demod.demod_rho(ds, t) for t in ds.templates])
+    got = gpu_demod(ds)
+    assert got.shape == ref.shape
+    assert_close(got, ref)
+
+
+def test_demod_injection_argmax_matches_oracle():
+    ds = synth.tiny(seed=41, n_templates=3, injection=INJ, noise=False)
+    ref = np.stack([demod.demod_rho(ds, t) for t in ds.templates])
+    got = gpu_demod(ds)
+    assert_close(got, ref)
+    assert np.unravel_index(got.argmax(), got.shape) == np.unravel_index(ref.argmax(), ref.shape)
+
+
+def test_demod_o1_band_30_days_injected_template():
+    """30 days of the O1-shaped band (T_sft = 360 s SFTs, T_max = 3600 s: ten SFT lags)."""
+    ds = synth.o1_band(n_ap=1, n_tasc=1, days=30)
+    inj = ds.injection
+    tm = np.array([[inj.a_p, inj.T_asc, inj.P]])
+    ref = np.stack([demod.demod_rho(ds, t) for t in tm])
+    got = gpu_demod(ds, tm)
+    assert_close(got, ref)
+    assert int(got[0].argmax()) == int(ref[0].argmax())
+
+
+def test_demod_argument_errors():
+    ds = synth.tiny(seed=33, n_templates=1)
+    lib = _lib.load()
+    with cc.CrossCorrPlan(ds.cfg, ds.dets) as plan:
+        tm = torch.from_numpy(ds.templates).to(DEV)
+        rho = torch.empty((1, plan.N_f), dtype=torch.float32, device=DEV)
+        st = lib.crosscorr_demod_search(plan._h, ctypes.c_void_p(int(tm.data_ptr())), 1,
+                                        ctypes.c_void_p(int(rho.data_ptr())), None)
+        assert st == 1                          # not prepared
+        x = torch.from_numpy(ds.x64).to(DEV)
+        with pytest.raises(cc.CrossCorrError) as e:
+            plan.demod_prepare(x, n_bin=3)
+        assert e.value.status == 5
+        with pytest.raises(cc.CrossCorrError) as e:
+            plan.demod_prepare(x, doppler_max=0.5)
+        assert e.value.status == 1
