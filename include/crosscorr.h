@@ -292,6 +292,20 @@ cc_status crosscorr_demod_prepare(cc_plan* plan, const void* const* x_dev, int32
 cc_status crosscorr_demod_search(cc_plan* plan, const cc_template* t_dev, int64_t n_t, float* rho_dev,
                                  void* stream);
 
+/* Input preparation (Appendix B): the heterodyned, downsampled series the search starts
+ * from, built from short Fourier transforms.  band_dev: device complex64 [n_sft][n_prime],
+ * the SFT bins k_h - n_prime/2 .. k_h + n_prime/2 - 1 of each SFT (DFT times dt, Eq.
+ * fourier-transform-def) around the heterodyne bin k_h = f_h T_sft (f_h on a bin);
+ * block_sft_dev: device int64 [n_blocks], the SFT of T_sft block b (block b starts at
+ * b T_sft after the series origin), -1 for a gap.  x_dev: device complex64
+ * [n_blocks * n_prime] at dt' = T_sft / n_prime:
+ *   x(b T_sft + j dt') = exp(-2 pi i f_h b T_sft) (-1)^j
+ *                        sum_{m < n_prime} exp(2 pi i j m / n_prime) band[b][m] / T_sft
+ * (Eqs. shifted-for-fft, long-time-series-het-corrected), zero in gaps.  Asynchronous on
+ * `stream` (a small twiddle table is allocated stream-ordered).  1 <= n_prime <= 16384. */
+cc_status crosscorr_sfts_to_series(const void* band_dev, const int64_t* block_sft_dev, int64_t n_blocks,
+                                   int64_t n_prime, double T_sft, double f_h, void* x_dev, void* stream);
+
 /* The k largest rho over (template, bin) of a device float[n_t][N_f] array,
  * descending, ties by (template, bin) ascending; hits_host receives
  * min(k, n_t*N_f) records.  Synchronises the stream.  1 <= k <= 4096. */

@@ -17,7 +17,7 @@ import numpy as np
 from . import _lib
 from ._lib import CcConfig, CcDetector, CcHit, CcLearnedInterp, CcPlanInfo, CcTuning, CrossCorrError, check
 
-__all__ = ["CrossCorrPlan", "CrossCorrError", "PAIR_UNORDERED", "PAIR_CROSS_ONLY",
+__all__ = ["CrossCorrPlan", "CrossCorrError", "sfts_to_series", "PAIR_UNORDERED", "PAIR_CROSS_ONLY",
            "PAIR_ALL_ORDERED", "STORE_FP32", "STORE_BF16", "build", "load"]
 
 PAIR_UNORDERED, PAIR_CROSS_ONLY, PAIR_ALL_ORDERED = 0, 1, 2
@@ -50,6 +50,24 @@ def _check_tensor(name, t, dtype, device_required=True):
         raise ValueError(f"{name} must have dtype {dtype}, got {t.dtype}")
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
+
+
+def sfts_to_series(band, block_sft, T_sft: float, f_h: float, stream=None):
+    """Heterodyned, downsampled series [n_blocks * N'] (CUDA complex64) from SFT bands
+    band [n_sft, N'] (CUDA complex64) and block_sft [n_blocks] (CUDA int64, -1 = gap):
+    the input preparation of Appendix B, in the CUDA library."""
+    import torch
+    lib = _lib.load()
+    _check_tensor("band", band, torch.complex64)
+    _check_tensor("block_sft", block_sft, torch.int64)
+    if band.dim() != 2:
+        raise ValueError("band must be [n_sft, N']")
+    n_blocks, n_prime = block_sft.numel(), band.shape[1]
+    x = torch.empty(n_blocks * n_prime, dtype=torch.complex64, device=band.device)
+    check("crosscorr_sfts_to_series", lib.crosscorr_sfts_to_series(
+        _dptr(band), _dptr(block_sft), n_blocks, n_prime, float(T_sft), float(f_h), _dptr(x),
+        _stream_handle(stream)))
+    return x
 
 
 class CrossCorrPlan:
