@@ -216,7 +216,8 @@ def run_gpu(args):
     B = args.templates
     grid = ds.templates
     idx = (np.arange(B) + rank * B) % grid.shape[0]
-    tm_host = np.ascontiguousarray(grid[idx])
+    # template rows (a_p, T_asc, P, e, omega): the circular grid with e = omega = 0
+    tm_host = np.ascontiguousarray(np.concatenate([grid[idx], np.zeros((B, 2))], axis=1))
     learned = args.interp == "learned"
     plan = cc.CrossCorrPlan(ds.cfg, ds.dets, interp=cc.INTERP_LEARNED if learned else cc.INTERP_EXACT)
     Q, N_f = plan.Q, plan.N_f
@@ -460,7 +461,7 @@ def run_demod(args):
     dev = torch.device("cuda", 0)
     ds = synth.o1_band(seed=1002)
     B = args.templates
-    tm = torch.from_numpy(np.ascontiguousarray(ds.templates[:B])).to(dev)
+    tm = cc.templates5(torch.from_numpy(np.ascontiguousarray(ds.templates[:B])).to(dev))
     plan = cc.CrossCorrPlan(ds.cfg, ds.dets)
     x = torch.from_numpy(ds.x64).to(dev)
     stream = torch.cuda.current_stream()

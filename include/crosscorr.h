@@ -102,11 +102,17 @@ typedef struct {
     int64_t n_sigma;
 } cc_detector;
 
-/* One orbital template (circular orbit, Sec. II A 2). */
+/* One orbital template (Sec. II A 2, Eqs. solve-for-E, Kepler-equation).  The binary
+ * Roemer delay at SSB time u is R/c = a_p [sin w (cos E - e) + cos w sqrt(1 - e^2) sin E]
+ * with E - e sin E = 2 pi (u - T_p) / P, the periapsis time T_p placed so that the
+ * ascending node (true anomaly -w) falls at T_asc.  e = 0 is the circular orbit
+ * R/c = a_p sin(2 pi (u - T_asc) / P) (w then has no effect).  0 <= e < 0.95. */
 typedef struct {
     double a_p;    /* projected semi-major axis a sin i / c [s] */
     double T_asc;  /* time of ascension, GPS [s] */
     double P;      /* orbital period [s] */
+    double e;      /* eccentricity */
+    double omega;  /* argument of periapsis w [rad] */
 } cc_template;
 
 /* One top-k record. */

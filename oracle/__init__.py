@@ -16,6 +16,7 @@ from . import learned  # noqa: F401
 from .crosscorr import (  # noqa: F401
     PAIR_UNORDERED, PAIR_CROSS_ONLY, PAIR_ALL_ORDERED,
     Plan, make_plan, ssb_delay, delay, stencil_position, interpolate, hamming, timing,
+    periapsis_time, kepler_E, binary_delay, orbit,
     resample, noise_block,
     weights, spectra_direct, spectra_fft, segment_norms, pair_list,
     normalization, pair_sum, rho_template, rho, topk, detector_frame_rho,

@@ -147,26 +147,68 @@ def ssb_delay(det, t: np.ndarray) -> np.ndarray:
     return _lerp(det.eph_t0, det.eph_dt, det.ssb_delay, t)
 
 
-def delay(det, a_p: float, tasc_rel: float, P: float, tau: np.ndarray) -> np.ndarray:
+def periapsis_time(tasc_rel: float, P: float, e: float, omega: float) -> float:
+    """T_p from the time of ascension T_asc (relative to t0): at the ascending node the
+    argument of latitude omega + nu vanishes, so the true anomaly there is -omega; its
+    eccentric and mean anomalies (Eq. solve-for-E) fix T_p = T_asc - M_asc / Omega.
+    For e = 0 this is T_asc + omega / Omega, and the orbit is the circular one."""
+    nu = -omega
+    E = 2.0 * math.atan2(math.sqrt(1.0 - e) * math.sin(0.5 * nu), math.sqrt(1.0 + e) * math.cos(0.5 * nu))
+    M = E - e * math.sin(E)
+    return tasc_rel - M * P / (2.0 * math.pi)
+
+
+def kepler_E(M: np.ndarray, e: float) -> np.ndarray:
+    """Eccentric anomaly: the root of E - e sin E = M (Eq. solve-for-E), by Newton's
+    method from E = M + e sin M, to FP64 precision."""
+    M = np.asarray(M, np.float64)
+    E = M + e * np.sin(M)
+    for _ in range(50):
+        dE = (E - e * np.sin(E) - M) / (1.0 - e * np.cos(E))
+        E = E - dE
+        if np.all(np.abs(dE) < 1e-15 * np.maximum(1.0, np.abs(E))):
+            break
+    return E
+
+
+def binary_delay(a_p: float, tasc_rel: float, P: float, u: np.ndarray, e: float = 0.0,
+                 omega: float = 0.0) -> np.ndarray:
+    """R/c at SSB time u (relative to t0): a_p [sin w (cos E - e) + cos w sqrt(1 - e^2) sin E]
+    (Eq. Kepler-equation) with E from the mean anomaly Omega (u - T_p) (Eq. solve-for-E;
+    the anomaly taken at t_SSB as in reading 1).  e = 0: a_p sin(Omega (u - T_asc))."""
+    u = np.asarray(u, np.float64)
+    if e == 0.0:
+        return a_p * np.sin(2.0 * np.pi * ((u - tasc_rel) / P))
+    Tp = periapsis_time(tasc_rel, P, e, omega)
+    E = kepler_E(2.0 * np.pi * ((u - Tp) / P), e)
+    return a_p * (math.sin(omega) * (np.cos(E) - e) + math.cos(omega) * math.sqrt(1.0 - e * e) * np.sin(E))
+
+
+def delay(det, a_p: float, tasc_rel: float, P: float, tau: np.ndarray, e: float = 0.0,
+          omega: float = 0.0) -> np.ndarray:
     """d(tau) = tau - t(tau): detector time t whose source time tau(t) is tau.
 
-    tau(t) = t_SSB - a_p sin(Omega (t_SSB - T_asc)), t_SSB = t + Delta_X(t)
-    (Eq. tau-equation with the circular R/c; reading 1: the orbital phase is
-    taken at t_SSB, as Eq. tau-equation writes it, not at detector t).
-    Inversion by the two fixed points u = tau + a_p sin(Omega (u - T_asc)) and
-    t = u - Delta_X(t), iterated on the small quantities b = u - tau and
-    Delta = u - t so that d = Delta - b keeps FP64 precision (~1e-13 s).
-    All times are relative to t0.
+    tau(t) = t_SSB - R(t_SSB)/c, t_SSB = t + Delta_X(t) (Eqs. t-ssb-equation,
+    tau-equation; R/c the Roemer delay of binary_delay, circular for e = 0; reading 1:
+    the orbital anomaly is taken at t_SSB, as Eq. tau-equation writes it).  Inversion by
+    the two fixed points u = tau + R(u)/c and t = u - Delta_X(t), iterated on the small
+    quantities b = u - tau and Delta = u - t so that d = Delta - b keeps FP64 precision
+    (~1e-13 s).  All times are relative to t0.
     """
     tau = np.asarray(tau, np.float64)
-    omega_over_2pi = 1.0 / P
     b = np.zeros_like(tau)
     for _ in range(N_FIXED_POINT):
-        b = a_p * np.sin(2.0 * np.pi * (((tau + b) - tasc_rel) * omega_over_2pi))
+        b = binary_delay(a_p, tasc_rel, P, tau + b, e, omega)
     dl = ssb_delay(det, tau)
     for _ in range(N_FIXED_POINT):
         dl = ssb_delay(det, (tau + b) - dl)
     return dl - b
+
+
+def orbit(tmpl):
+    """(a_p, T_asc, P, e, omega) of a template row; three-element rows are circular."""
+    t = [float(v) for v in tmpl]
+    return (t[0], t[1], t[2], t[3], t[4]) if len(t) >= 5 else (t[0], t[1], t[2], 0.0, 0.0)
 
 
 # ---------------------------------------------------------------------------
@@ -213,10 +255,10 @@ def interpolate(x: np.ndarray, jstar: np.ndarray, delta: np.ndarray, D: int) -> 
 def timing(det, cfg, plan: Plan, tmpl):
     """(j*, delta, d) for every source sample r = 0..M N_s - 1 of one detector and
     one template (a_p, T_asc, P)."""
-    a_p, tasc, P = float(tmpl[0]), float(tmpl[1]), float(tmpl[2])
+    a_p, tasc, P, e, omega = orbit(tmpl)
     n = plan.M * plan.N_s
     r = np.arange(n, dtype=np.int64)
-    d = delay(det, a_p, tasc - cfg.t0, P, r * plan.dt)
+    d = delay(det, a_p, tasc - cfg.t0, P, r * plan.dt, e, omega)
     jstar, delta = stencil_position(d / plan.dt, r)
     return jstar, delta, d
 
@@ -418,7 +460,10 @@ def detector_frame_rho(ds, tmpl, plan: Optional[Plan] = None, mode: Optional[int
     cfg = ds.cfg
     plan = plan or make_plan(cfg)
     mode = cfg.pair_mode if mode is None else mode
-    a_p, tasc, P = float(tmpl[0]), float(tmpl[1]) - cfg.t0, float(tmpl[2])
+    a_p, tasc, P, e, _ = orbit(tmpl)
+    tasc -= cfg.t0
+    if e != 0.0:
+        raise ValueError("the detector-frame brute force is written for circular orbits")
     Fa, Fb, norms = [], [], []
     for q, det in enumerate(ds.dets):
         _, jr, dr = resample(ds.x[q], det, cfg, plan, tmpl)

@@ -41,7 +41,7 @@ from typing import List, Optional
 
 import numpy as np
 
-from .crosscorr import make_plan, ssb_delay
+from .crosscorr import kepler_E, make_plan, orbit, periapsis_time, ssb_delay
 
 
 def sfts(ds):
@@ -65,24 +65,35 @@ def sfts(ds):
     return out
 
 
-def source_time(det, a_p: float, tasc_rel: float, P: float, t: np.ndarray):
-    """tau(t) - t = Delta_X(t) - a_p sin(Omega (t + Delta_X(t) - T_asc)) and dtau/dt at
-    detector times t (relative to t0; Eqs. t-ssb-equation, tau-equation)."""
+def source_time(det, a_p: float, tasc_rel: float, P: float, t: np.ndarray, e: float = 0.0, omega: float = 0.0):
+    """tau(t) - t = Delta_X(t) - R(t_SSB)/c and dtau/dt at detector times t (relative to
+    t0; Eqs. t-ssb-equation, tau-equation, Kepler-equation with the anomaly at t_SSB):
+    dtau/dt = (1 + Delta') (1 - dR/du / c), dE/du = Omega / (1 - e cos E)."""
     t = np.asarray(t, np.float64)
     dl = ssb_delay(det, t)
-    ph = 2.0 * np.pi * ((t + dl - tasc_rel) / P)
-    u = (t - det.eph_t0) / det.eph_dt
-    i = np.clip(np.floor(u), 0, len(det.ssb_delay) - 2).astype(np.int64)
+    u = t + dl
+    u_i = (t - det.eph_t0) / det.eph_dt
+    i = np.clip(np.floor(u_i), 0, len(det.ssb_delay) - 2).astype(np.int64)
     ddl = (det.ssb_delay[i + 1] - det.ssb_delay[i]) / det.eph_dt
-    dtau = (1.0 + ddl) * (1.0 - a_p * (2.0 * np.pi / P) * np.cos(ph))
-    return dl - a_p * np.sin(ph), dtau
+    Om = 2.0 * np.pi / P
+    if e == 0.0:
+        ph = Om * (u - tasc_rel)
+        R, dR = a_p * np.sin(ph), a_p * Om * np.cos(ph)
+    else:
+        Tp = periapsis_time(tasc_rel, P, e, omega)
+        E = kepler_E(Om * (u - Tp), e)
+        q = math.sqrt(1.0 - e * e)
+        R = a_p * (math.sin(omega) * (np.cos(E) - e) + math.cos(omega) * q * np.sin(E))
+        dR = a_p * (-math.sin(omega) * np.sin(E) + math.cos(omega) * q * np.cos(E)) * Om / (1.0 - e * np.cos(E))
+    return dl - R, (1.0 + ddl) * (1.0 - dR)
 
 
-def signal_bins(det, cfg, a_p: float, tasc_rel: float, P: float, tmid: np.ndarray, f: np.ndarray):
+def signal_bins(det, cfg, a_p: float, tasc_rel: float, P: float, tmid: np.ndarray, f: np.ndarray,
+                e: float = 0.0, omega: float = 0.0):
     """(x, cyc): the signal's heterodyned bin position x = (f_K - f_h) T_sft with
     f_K = f dtau/dt(t_K), and its heterodyned phase in cycles, f tau(t_K) - f_h t_K
     reduced mod 1, for SFT mid-times t_K [n_sft] and frequencies f [n_f]."""
-    d, dtau = source_time(det, a_p, tasc_rel, P, tmid)
+    d, dtau = source_time(det, a_p, tasc_rel, P, tmid, e, omega)
     dfreq = np.asarray(f, np.float64) - cfg.f_h
     # f tau - f_h t = f (tau - t) + (f - f_h) t, and its time derivative
     x = (np.outer(dtau - 1.0, f) + dfreq[None, :]) * cfg.T_sft
@@ -127,13 +138,14 @@ def demod_rho(ds, tmpl, freqs: Optional[np.ndarray] = None, n_bin: int = 2, T_ma
         dfreq = np.asarray(freqs, np.float64) - cfg.f_h
     f = cfg.f_h + dfreq
     T_max = cfg.T_max if T_max is None else T_max
-    a_p, tasc_rel, P = float(tmpl[0]), float(tmpl[1]) - cfg.t0, float(tmpl[2])
+    a_p, tasc, P, e, omega = orbit(tmpl)
+    tasc_rel = tasc - cfg.t0
     sft_list = sfts(ds) if sft_list is None else sft_list
     T, Y, AH, BH, XI, DET = [], [], [], [], [], []
     for q, (det, (ks, tmid, z, sig)) in enumerate(zip(ds.dets, sft_list)):
         if len(ks) == 0:
             continue
-        x, cyc = signal_bins(det, cfg, a_p, tasc_rel, P, tmid, f)
+        x, cyc = signal_bins(det, cfg, a_p, tasc_rel, P, tmid, f, e, omega)
         zK, xi = sft_data_vector(z, x, n_bin)
         Y.append(xi * zK * np.exp(-2j * np.pi * cyc))      # Xi_K z_K exp(-i Phi_K)
         XI.append(xi)

@@ -52,6 +52,16 @@ def _check_tensor(name, t, dtype, device_required=True):
         raise ValueError(f"{name} must be contiguous")
 
 
+def templates5(templates):
+    """Template rows as the C ABI's cc_template (a_p, T_asc, P, e, omega): [n, 3]
+    circular rows get e = omega = 0; [n, 5] rows are returned as they are."""
+    import torch
+    if templates.shape[-1] == 5:
+        return templates
+    z = torch.zeros((templates.shape[0], 2), dtype=templates.dtype, device=templates.device)
+    return torch.cat([templates, z], dim=1).contiguous()
+
+
 def sfts_to_series(band, block_sft, T_sft: float, f_h: float, stream=None):
     """Heterodyned, downsampled series [n_blocks * N'] (CUDA complex64) from SFT bands
     band [n_sft, N'] (CUDA complex64) and block_sft [n_blocks] (CUDA int64, -1 = gap):
@@ -166,17 +176,19 @@ class CrossCorrPlan:
         return arr, xs
 
     def _templates(self, templates):
+        """(n_t, device templates [n_t, 5]): rows (a_p, T_asc, P, e, omega); [n_t, 3]
+        circular rows are widened with e = omega = 0 (a device copy, ordered on the stream)."""
         import torch
         _check_tensor("templates", templates, torch.float64)
-        if templates.dim() != 2 or templates.shape[1] != 3:
-            raise ValueError("templates must be [n_t, 3] (a_p, T_asc, P)")
-        return templates.shape[0]
+        if templates.dim() != 2 or templates.shape[1] not in (3, 5):
+            raise ValueError("templates must be [n_t, 5] (a_p, T_asc, P, e, omega) or [n_t, 3] (circular)")
+        return templates.shape[0], templates5(templates)
 
     # -- the C ABI calls -------------------------------------------------------
     def resample(self, x, templates, ab=None, norm=None, stream=None):
         """Stage 1: a_r, b_r series [n_t, Q, 2, N_tau] and segment norms [n_t, Q, M, 4]."""
         import torch
-        n_t = self._templates(templates)
+        n_t, templates = self._templates(templates)
         xp, _ = self._xptrs(x)
         dev = templates.device
         if ab is None:
@@ -211,7 +223,7 @@ class CrossCorrPlan:
     def search(self, x, templates, rho=None, stream=None):
         """The whole path: rho [n_t, N_f] float32."""
         import torch
-        n_t = self._templates(templates)
+        n_t, templates = self._templates(templates)
         xp, _ = self._xptrs(x)
         if rho is None:
             rho = torch.empty((n_t, self.N_f), dtype=torch.float32, device=templates.device)
@@ -266,7 +278,7 @@ class CrossCorrPlan:
     def demod_search(self, templates, rho=None, stream=None):
         """Detector-frame (demodulation) rho [n_t, N_f] at the plan's output frequencies."""
         import torch
-        n_t = self._templates(templates)
+        n_t, templates = self._templates(templates)
         if rho is None:
             rho = torch.empty((n_t, self.N_f), dtype=torch.float32, device=templates.device)
         _check_tensor("rho", rho, torch.float32)

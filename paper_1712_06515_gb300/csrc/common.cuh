@@ -20,6 +20,7 @@ constexpr int MAX_D = 32;
 constexpr int MAX_TAPS = 2 * MAX_D + 1;
 constexpr int N_BIN_ITER = 4;   // fixed-point steps of the binary delay b = a_p sin(Omega (tau + b - T_asc))
 constexpr int N_SSB_ITER = 4;   // fixed-point steps of t = u - Delta(t)
+constexpr int N_KEPLER_ITER = 8; // joint fixed-point / Newton steps of the elliptical binary delay
 constexpr int MAX_L = 4096;     // largest coset FFT: 256 threads, one radix-16 butterfly each per pass
 
 // Learned interpolator: 8 taps from a 2 -> 64 -> 64 -> 8 tanh network, tabulated at
@@ -230,28 +231,72 @@ __device__ __forceinline__ double table_lerp(const double* tab, double t0, doubl
     return v0 + f * (v1 - v0);
 }
 
+// Orbit of one template in the form the timing code uses (times relative to t0).
+struct Orbit {
+    double a_p, tasc_rel, invP, e;
+    double tp_rel;          // periapsis time (elliptical)
+    double sinw, cosw, sq;  // sin w, cos w, sqrt(1 - e^2)
+};
+
+__device__ __forceinline__ Orbit make_orbit(const DevParams& p, const cc_template& T) {
+    Orbit o;
+    o.a_p = T.a_p;
+    o.tasc_rel = T.T_asc - p.t0;
+    o.invP = 1.0 / T.P;
+    o.e = T.e;
+    sincos(T.omega, &o.sinw, &o.cosw);
+    o.sq = sqrt(1.0 - T.e * T.e);
+    // the ascending node has true anomaly -w: its eccentric and mean anomalies give T_p
+    double sh, ch;
+    sincos(-0.5 * T.omega, &sh, &ch);
+    const double Ea = 2.0 * atan2(sqrt(1.0 - T.e) * sh, sqrt(1.0 + T.e) * ch);
+    o.tp_rel = o.tasc_rel - (Ea - T.e * sin(Ea)) * T.P * 0.15915494309189535;
+    return o;
+}
+
 // d(tau) = tau - t(tau) for detector X and one template (all times relative to t0).
-// tau(t) = t_SSB - a_p sin(Omega (t_SSB - T_asc)), t_SSB = t + Delta_X(t).
-// Binary part: b = a_p sin(theta0 + Omega b) with theta0 = Omega (tau - T_asc); one
+// tau(t) = t_SSB - R(t_SSB)/c, t_SSB = t + Delta_X(t).
+// Circular orbit: b = a_p sin(theta0 + Omega b) with theta0 = Omega (tau - T_asc); one
 // FP64 sincospi at theta0, then fixed-point steps through the angle-addition formula
 // with sin/cos of the small angle Omega b (|Omega b| <= 1.4e-4 rad) from their series
 // (remainders below 1e-26); the contraction a_p Omega ~ 1.3e-4 per step leaves
-// < 1e-15 s after N_BIN_ITER steps.  SSB part: t = u - Delta(t), u = tau + b, iterated
-// on Delta from Delta(u) (contraction |Delta'| <= 1e-4).  Both work on the small
-// quantities b and Delta so d = Delta - b keeps FP64 precision.
-__device__ __forceinline__ double knot_delay(const DevParams& p, int X, double a_p,
-                                             double tasc_rel, double invP, double tau) {
-    const double x0 = (tau - tasc_rel) * invP;            // orbital phase in cycles
-    double s0, c0;
-    sincospi(2.0 * x0, &s0, &c0);
-    const double om = 6.283185307179586 * invP;           // Omega
-    double b = a_p * s0;
+// < 1e-15 s after N_BIN_ITER steps.  Elliptical orbit: b = R(tau + b)/c with E from
+// Kepler's equation, one Newton step per fixed-point step from the previous E (the mean
+// anomaly moves by Omega db ~ 1e-4 rad per step), N_KEPLER_ITER steps (Newton from
+// E = M + e sin M converges quadratically to FP64 precision well within them for e < 0.95).
+// SSB part: t = u - Delta(t), u = tau + b, iterated on Delta from Delta(u) (contraction
+// |Delta'| <= 1e-4).  Both work on the small quantities b and Delta so d = Delta - b
+// keeps FP64 precision.
+__device__ __forceinline__ double knot_delay(const DevParams& p, int X, const Orbit& o, double tau) {
+    double b;
+    if (o.e == 0.0) {
+        const double x0 = (tau - o.tasc_rel) * o.invP;        // orbital phase in cycles
+        double s0, c0;
+        sincospi(2.0 * x0, &s0, &c0);
+        const double om = 6.283185307179586 * o.invP;         // Omega
+        b = o.a_p * s0;
 #pragma unroll
-    for (int it = 0; it < N_BIN_ITER; ++it) {
-        const double dl = om * b, d2 = dl * dl;
-        const double sd = dl * (1.0 - d2 * (1.0 / 6.0) * (1.0 - d2 * (1.0 / 20.0)));
-        const double cd = 1.0 - d2 * 0.5 * (1.0 - d2 * (1.0 / 12.0));
-        b = a_p * fma(s0, cd, c0 * sd);
+        for (int it = 0; it < N_BIN_ITER; ++it) {
+            const double dl = om * b, d2 = dl * dl;
+            const double sd = dl * (1.0 - d2 * (1.0 / 6.0) * (1.0 - d2 * (1.0 / 20.0)));
+            const double cd = 1.0 - d2 * 0.5 * (1.0 - d2 * (1.0 / 12.0));
+            b = o.a_p * fma(s0, cd, c0 * sd);
+        }
+    } else {
+        double xm = (tau - o.tp_rel) * o.invP;
+        xm -= floor(xm);
+        const double M0 = 6.283185307179586 * xm;             // mean anomaly at tau, [0, 2 pi)
+        const double om = 6.283185307179586 * o.invP;
+        double E = M0 + o.e * sin(M0), sE, cE;
+        sincos(E, &sE, &cE);
+        b = 0.0;
+#pragma unroll 1
+        for (int it = 0; it < N_KEPLER_ITER; ++it) {
+            const double M = M0 + om * b;                      // mean anomaly at u = tau + b
+            E -= (E - o.e * sE - M) / (1.0 - o.e * cE);
+            sincos(E, &sE, &cE);
+            b = o.a_p * (o.sinw * (cE - o.e) + o.cosw * o.sq * sE);
+        }
     }
     const double* tab = p.ssb[X];
     const double t0 = p.eph_t0[X], inv = p.inv_eph_dt[X];

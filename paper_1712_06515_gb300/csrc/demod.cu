@@ -107,12 +107,31 @@ __global__ void demod_timing_kernel(DevParams p, const cc_template* __restrict__
     const double d0 = __ldg(p.ssb[X] + i), d1 = __ldg(p.ssb[X] + i + 1);
     const double dl = d0 + (u - (double)i) * (d1 - d0);
     const double ddl = (d1 - d0) * p.inv_eph_dt[X];
-    // binary delay at t_SSB and dtau/dt (Eqs. t-ssb-equation, tau-equation)
-    const double invP = 1.0 / T.P;
-    double s, c;
-    sincospi(2.0 * ((tmid + dl - (T.T_asc - p.t0)) * invP), &s, &c);
-    const double d = dl - T.a_p * s;                                   // tau - t
-    const double dtau = (1.0 + ddl) * (1.0 - T.a_p * 6.283185307179586 * invP * c);
+    // binary delay R/c at t_SSB and its rate (Eqs. t-ssb-equation, tau-equation,
+    // Kepler-equation), dtau/dt = (1 + Delta') (1 - dR/du / c)
+    const Orbit o = make_orbit(p, T);
+    const double u_ssb = tmid + dl, om = 6.283185307179586 * o.invP;
+    double R, dR;
+    if (o.e == 0.0) {
+        double s, c;
+        sincospi(2.0 * ((u_ssb - o.tasc_rel) * o.invP), &s, &c);
+        R = o.a_p * s;
+        dR = o.a_p * om * c;
+    } else {
+        double xm = (u_ssb - o.tp_rel) * o.invP;
+        xm -= floor(xm);
+        const double M = 6.283185307179586 * xm;
+        double E = M + o.e * sin(M), sE, cE;
+        sincos(E, &sE, &cE);
+        for (int it = 0; it < N_KEPLER_ITER; ++it) {
+            E -= (E - o.e * sE - M) / (1.0 - o.e * cE);
+            sincos(E, &sE, &cE);
+        }
+        R = o.a_p * (o.sinw * (cE - o.e) + o.cosw * o.sq * sE);
+        dR = o.a_p * (-o.sinw * sE + o.cosw * o.sq * cE) * om / (1.0 - o.e * cE);
+    }
+    const double d = dl - R;                                           // tau - t
+    const double dtau = (1.0 + ddl) * (1.0 - dR);
     const double Tsft = nsft * p.dt;
     DemodTiming r;
     // x = (f (dtau - 1) + df) T_sft with f = f_h + df

@@ -102,10 +102,9 @@ knots_kernel(DevParams p, const cc_template* __restrict__ tm, int64_t t_base, in
     const int X = blockIdx.y;
     const int64_t tl = blockIdx.z, t = t_base + tl;
     const int64_t k0 = (int64_t)blockIdx.x * 256;
-    const cc_template T = tm[t];
-    const double tasc_rel = T.T_asc - p.t0, invP = 1.0 / T.P;
+    const Orbit orb = make_orbit(p, tm[t]);
     for (int i = threadIdx.x; i < 256 + 3; i += 256)
-        dk[i] = knot_delay(p, X, T.a_p, tasc_rel, invP, (double)((k0 - 1 + i) * KNOT) * p.dt);
+        dk[i] = knot_delay(p, X, orb, (double)((k0 - 1 + i) * KNOT) * p.dt);
     __syncthreads();
     const int64_t k = k0 + threadIdx.x;
     if (k < nkn)

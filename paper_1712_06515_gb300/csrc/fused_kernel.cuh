@@ -82,9 +82,7 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
     int* segact = (int*)(sm + lay.off_flags);
     int* cstart = (int*)(bins + nb);
 
-    const cc_template T = tm[t];
-    const double tasc_rel = T.T_asc - p.t0;
-    const double invP = 1.0 / T.P;
+    const Orbit orb = make_orbit(p, tm[t]);
 
     // this CTA's bins: cosets rank, rank+CL, ... concatenated
     if (tid == 0) {
@@ -145,7 +143,7 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
         for (int j = FUSED_THREADS - 1 - tid; j < nown * Q && j >= 0; j += FUSED_THREADS) {
             const int X = j / nown, i = rank + (j % nown) * CL;
             dkb[((size_t)buf * Q + X) * lay.nkseg + i] =
-                knot_delay(p, X, T.a_p, tasc_rel, invP, (double)((kA + i) * KNOT) * p.dt);
+                knot_delay(p, X, orb, (double)((kA + i) * KNOT) * p.dt);
         }
     };
     auto remote_dk = [&](int buf, int X, int i) -> double {

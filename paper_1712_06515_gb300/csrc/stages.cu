@@ -128,11 +128,9 @@ resample_kernel(DevParams p, const cc_template* __restrict__ tm, int64_t t_base,
         __syncthreads();
     } else {
         double* dk = (double*)(smem + sizeof(KnotRec) * nk);
-        const cc_template T = tm[t];
-        const double tasc_rel = T.T_asc - p.t0;
-        const double invP = 1.0 / T.P;
+        const Orbit orb = make_orbit(p, tm[t]);
         for (int i = tid; i < nk; i += blockDim.x)
-            dk[i] = knot_delay(p, X, T.a_p, tasc_rel, invP, (double)((kA + i) * KNOT) * p.dt);
+            dk[i] = knot_delay(p, X, orb, (double)((kA + i) * KNOT) * p.dt);
         __syncthreads();
         for (int i = 1 + tid; i < nk - 2; i += blockDim.x)
             rec[i] = make_knot(p, dk[i - 1], dk[i], dk[i + 1], dk[i + 2], (double)((kA + i) * KNOT) * p.dt);

@@ -16,7 +16,7 @@ from typing import List, Optional, Sequence
 
 import numpy as np
 
-from . import (INTERP_EXACT, PATH_FUSED, PATH_TWO_PASS, STORE_FP32, CrossCorrError, CrossCorrPlan)
+from . import (INTERP_EXACT, PATH_FUSED, PATH_TWO_PASS, STORE_FP32, CrossCorrError, CrossCorrPlan, templates5)
 
 CHUNK_WAVES = (5, 10, 20, 40)
 
@@ -64,7 +64,7 @@ class MultiBandSearch:
                  tune: bool = True, tune_templates: int = 64, learned_weights: Optional[str] = None):
         import torch
         self.x = [b[2] for b in bands]
-        self.templates = [b[3] for b in bands]
+        self.templates = [templates5(b[3]) for b in bands]
         self.plans: List[CrossCorrPlan] = [
             CrossCorrPlan(cfg, dets, store=store, interp=interp, learned_weights=learned_weights)
             for cfg, dets, _, _ in bands]

@@ -144,6 +144,8 @@ class Injection:
     cosi: float = 1.0
     psi: float = 0.0
     phi0: float = 0.0
+    e: float = 0.0            # eccentricity (0: circular orbit)
+    omega: float = 0.0        # argument of periapsis [rad]
 
 
 @dataclasses.dataclass
@@ -209,6 +211,28 @@ def _table_lerp(t0: float, dt: float, tab: np.ndarray, t: np.ndarray) -> np.ndar
     return tab[i] * (1.0 - f) + tab[i + 1] * f
 
 
+def orbital_roemer_delay(inj: Injection, tasc_rel: float, tssb: np.ndarray) -> np.ndarray:
+    """R/c of the injected orbit at SSB times tssb (relative to t0): circular,
+    a_p sin(2 pi (tssb - T_asc)/P), or Keplerian with eccentricity e and argument of
+    periapsis omega, the periapsis time placed so the ascending node (true anomaly
+    -omega) is at T_asc; Kepler's equation solved by bisection."""
+    if inj.e == 0.0:
+        return inj.a_p * np.sin(2.0 * np.pi * ((tssb - tasc_rel) / inj.P))
+    e, w = inj.e, inj.omega
+    nu = -w
+    E_asc = 2.0 * math.atan(math.sqrt((1.0 - e) / (1.0 + e)) * math.tan(0.5 * nu))
+    tp = tasc_rel - (E_asc - e * math.sin(E_asc)) * inj.P / (2.0 * math.pi)
+    M = 2.0 * np.pi * ((tssb - tp) / inj.P)
+    M = M - 2.0 * np.pi * np.floor(M / (2.0 * np.pi))              # [0, 2 pi)
+    lo, hi = np.zeros_like(M), np.full_like(M, 2.0 * np.pi)         # E - e sin E is increasing
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        below = mid - e * np.sin(mid) < M
+        lo, hi = np.where(below, mid, lo), np.where(below, hi, mid)
+    E = 0.5 * (lo + hi)
+    return inj.a_p * (math.sin(w) * (np.cos(E) - e) + math.cos(w) * math.sqrt(1.0 - e * e) * np.sin(E))
+
+
 def inject_signal(inj: Injection, cfg: SearchConfig, site: Site, det: DetectorTables,
                   exact_ephemeris: bool = True, exact_antenna: bool = True) -> np.ndarray:
     """Heterodyned complex CW signal at the detector sample times.
@@ -226,7 +250,7 @@ def inject_signal(inj: Injection, cfg: SearchConfig, site: Site, det: DetectorTa
         delay = _table_lerp(det.eph_t0, det.eph_dt, det.ssb_delay, t)
     tasc_rel = inj.T_asc - cfg.t0
     tssb = t + delay
-    binary = inj.a_p * np.sin(2.0 * np.pi * ((tssb - tasc_rel) / inj.P))
+    binary = orbital_roemer_delay(inj, tasc_rel, tssb)
     # f0 (tau - t0) - f_h (t - t0) = f0 (delay - binary) + (f0 - f_h) t
     cyc = inj.f0 * (delay - binary)
     cyc = cyc - np.floor(cyc)

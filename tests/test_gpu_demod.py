@@ -71,7 +71,7 @@ def test_demod_argument_errors():
     ds = synth.tiny(seed=33, n_templates=1)
     lib = _lib.load()
     with cc.CrossCorrPlan(ds.cfg, ds.dets) as plan:
-        tm = torch.from_numpy(ds.templates).to(DEV)
+        tm = cc.templates5(torch.from_numpy(ds.templates).to(DEV))
         rho = torch.empty((1, plan.N_f), dtype=torch.float32, device=DEV)
         st = lib.crosscorr_demod_search(plan._h, ctypes.c_void_p(int(tm.data_ptr())), 1,
                                         ctypes.c_void_p(int(rho.data_ptr())), None)

@@ -174,6 +174,7 @@ def test_learned_interp_argument_errors():
     try:
         rho = torch.empty((1, plan.N_f), dtype=torch.float32, device=DEV)
         xp = (ctypes.c_void_p * len(ds.dets))(*[int(x[i].data_ptr()) for i in range(len(ds.dets))])
+        tm = cc.templates5(tm)
         st = lib.crosscorr_search(h, xp, ctypes.c_void_p(int(tm.data_ptr())), 1,
                                   ctypes.c_void_p(int(rho.data_ptr())), None)
         assert st == 1 and b"crosscorr_plan_set_learned_interp" in lib.crosscorr_last_error()

@@ -25,6 +25,7 @@ TOL32 = 1e-4   # the FP32 parity tolerance of the other GPU tests, relative to m
 
 def _call_noalloc(lib, plan, x, tm, rho):
     xp = (ctypes.c_void_p * plan.Q)(*[int(x[i].data_ptr()) for i in range(plan.Q)])
+    tm = cc.templates5(tm)
     st = lib.crosscorr_search_noalloc(plan._h, xp, int(tm.data_ptr()), tm.shape[0], int(rho.data_ptr()),
                                       int(torch.cuda.current_stream().cuda_stream))
     return st
