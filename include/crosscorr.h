@@ -312,6 +312,22 @@ cc_status crosscorr_demod_search(cc_plan* plan, const cc_template* t_dev, int64_
 cc_status crosscorr_sfts_to_series(const void* band_dev, const int64_t* block_sft_dev, int64_t n_blocks,
                                    int64_t n_prime, double T_sft, double f_h, void* x_dev, void* stream);
 
+/* Template placement (Sec. III A; host functions, no GPU).  crosscorr_metric: the
+ * phase-mismatch metric g [3][3] (row-major, for lambda = (a_p, T_asc, P)) of Eq.
+ * phase-derivs-metric, g_ij = 1/2 < d(Phi_K - Phi_L)/d lambda^i d(Phi_K - Phi_L)/d lambda^j >
+ * over the pairs of the detector-frame statistic: SFT mid-times (k + 1/2) T_sft,
+ * k < floor(T_obs / T_sft), every unordered pair of distinct SFTs of the Q detectors within
+ * T_max (same-time pairs of two detectors have zero phase difference), for the circular
+ * orbit `orbit` (host; e must be 0) at frequency f; times relative to t0.
+ * crosscorr_lattice: the cubic lattice of Eq. metric-spacing-eq, spacing sqrt(mu / g_ii)
+ * from lo[i] covering [lo[i], hi[i]], written to out (host, capacity entries; circular
+ * templates, P varying fastest: out[(ia * nT + iT) * nP + iP]); *n_out receives the
+ * lattice size (out = NULL queries it). */
+cc_status crosscorr_metric(double T_obs, double T_sft, double T_max, int32_t Q, double f, const cc_template* orbit,
+                           double t0, double* g);
+cc_status crosscorr_lattice(const double* g, double mu, const double* lo, const double* hi, cc_template* out,
+                            int64_t capacity, int64_t* n_out);
+
 /* The k largest rho over (template, bin) of a device float[n_t][N_f] array,
  * descending, ties by (template, bin) ascending; hits_host receives
  * min(k, n_t*N_f) records.  Synchronises the stream.  1 <= k <= 4096. */

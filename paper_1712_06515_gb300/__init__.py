@@ -17,7 +17,7 @@ import numpy as np
 from . import _lib
 from ._lib import CcConfig, CcDetector, CcHit, CcLearnedInterp, CcPlanInfo, CcTuning, CrossCorrError, check
 
-__all__ = ["CrossCorrPlan", "CrossCorrError", "sfts_to_series", "PAIR_UNORDERED", "PAIR_CROSS_ONLY",
+__all__ = ["CrossCorrPlan", "CrossCorrError", "sfts_to_series", "metric", "lattice", "templates5", "PAIR_UNORDERED", "PAIR_CROSS_ONLY",
            "PAIR_ALL_ORDERED", "STORE_FP32", "STORE_BF16", "build", "load"]
 
 PAIR_UNORDERED, PAIR_CROSS_ONLY, PAIR_ALL_ORDERED = 0, 1, 2
@@ -60,6 +60,35 @@ def templates5(templates):
         return templates
     z = torch.zeros((templates.shape[0], 2), dtype=templates.dtype, device=templates.device)
     return torch.cat([templates, z], dim=1).contiguous()
+
+
+def metric(T_obs: float, T_sft: float, T_max: float, Q: int, f: float, a_p: float, T_asc: float, P: float,
+           t0: float = 0.0) -> np.ndarray:
+    """Phase-mismatch metric g [3, 3] for (a_p, T_asc, P) of a circular orbit (host, in the
+    library)."""
+    lib = _lib.load()
+    orb = np.array([a_p, T_asc, P, 0.0, 0.0], np.float64)
+    g = np.zeros(9, np.float64)
+    check("crosscorr_metric", lib.crosscorr_metric(float(T_obs), float(T_sft), float(T_max), int(Q), float(f),
+                                                   orb.ctypes.data_as(c_void_p), float(t0),
+                                                   g.ctypes.data_as(POINTER(c_double))))
+    return g.reshape(3, 3)
+
+
+def lattice(g, mu: float, lo, hi) -> np.ndarray:
+    """Cubic template lattice [n, 3] (a_p, T_asc, P) with spacing sqrt(mu / g_ii) over
+    [lo, hi] (host, in the library)."""
+    lib = _lib.load()
+    g = np.ascontiguousarray(g, np.float64).ravel()
+    lo = np.ascontiguousarray(lo, np.float64)
+    hi = np.ascontiguousarray(hi, np.float64)
+    n = c_int64()
+    P = POINTER(c_double)
+    args = (g.ctypes.data_as(P), float(mu), lo.ctypes.data_as(P), hi.ctypes.data_as(P))
+    check("crosscorr_lattice", lib.crosscorr_lattice(*args, None, 0, byref(n)))
+    out = np.zeros((n.value, 5), np.float64)
+    check("crosscorr_lattice", lib.crosscorr_lattice(*args, out.ctypes.data_as(c_void_p), n.value, byref(n)))
+    return out[:, :3].copy()
 
 
 def sfts_to_series(band, block_sft, T_sft: float, f_h: float, stream=None):

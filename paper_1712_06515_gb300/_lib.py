@@ -21,7 +21,7 @@ LIBDIR = os.path.join(PKG, "lib")
 LIBPATH = os.path.join(LIBDIR, "libcrosscorr.so")
 
 SOURCES = ["plan.cu", "stages.cu", "search.cu", "topk.cu", "fused.cu", "fused_l64_256.cu", "fused_l512_1024.cu",
-           "fused_l2048.cu", "fused_l4096.cu", "noalloc.cu", "learned.cu", "segpair.cu", "demod.cu", "sftseries.cu"]
+           "fused_l2048.cu", "fused_l4096.cu", "noalloc.cu", "learned.cu", "segpair.cu", "demod.cu", "sftseries.cu", "lattice.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 
@@ -133,6 +133,10 @@ SIGNATURES = {
     "crosscorr_plan_set_kernel_timing": (c_int, [c_void_p, c_int]),
     "crosscorr_plan_set_path": (c_int, [c_void_p, c_int]),
     "crosscorr_demod_prepare": (c_int, [c_void_p, POINTER(c_void_p), c_int32, c_double, c_void_p]),
+    "crosscorr_metric": (c_int, [c_double, c_double, c_double, c_int32, c_double, c_void_p, c_double,
+                                 POINTER(c_double)]),
+    "crosscorr_lattice": (c_int, [POINTER(c_double), c_double, POINTER(c_double), POINTER(c_double), c_void_p,
+                                  c_int64, POINTER(c_int64)]),
     "crosscorr_sfts_to_series": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_double, c_double, c_void_p,
                                          c_void_p]),
     "crosscorr_demod_search": (c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
