@@ -35,10 +35,9 @@ METRIC = "CrossCorr rho templates*freq-bins/sec on 1 GB300 (+% HBM roofline) vs 
 UNIT = "template*bins/s"
 GRID_TEMPLATES = 8000
 # DRAM bytes read + written per template by segpair_kernel<4096> on this workload, from
-# the ncu capture summarised in profiles/segpair_kernel_o1_band_64_templates.md (64
-# templates in one launch; traffic grows with the templates of a launch).  None once
-# the kernel changes.
-SEGPAIR_DRAM_BYTES_PER_TEMPLATE = (14.939288e9 + 25.929216e6) / 64
+# an ncu capture (traffic grows with the templates of a launch).  None until the current
+# kernel has been captured.
+SEGPAIR_DRAM_BYTES_PER_TEMPLATE = None
 SM_COUNT = 152
 FP32_LANES = 128
 

@@ -168,8 +168,12 @@ void timing_pair(cc_plan* plan, cudaEvent_t* start, cudaEvent_t* stop);
 // ---------------------------------------------------------------------------
 // Device helpers
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Complex sums and differences as paired FP32 operations (one f32x2 instruction for both
+// components, each rounded as the scalar operation): the transforms are bound by
+// instruction issue, and a pair takes one issue slot.  a - b is a + (-1) b by one fused
+// multiply-add, exact in the product, so it rounds as the subtraction does.
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
@@ -238,19 +242,32 @@ struct Orbit {
     double sinw, cosw, sq;  // sin w, cos w, sqrt(1 - e^2)
 };
 
+// sin and cos of an angle in radians through sincospi, whose argument reduction is exact
+// (no slow path for large arguments); the rounding of x / pi adds ~1e-16 relative.
+__device__ __forceinline__ void sincos_rad(double x, double* s, double* c) {
+    sincospi(x * 0.31830988618379067154, s, c);
+}
+
 __device__ __forceinline__ Orbit make_orbit(const DevParams& p, const cc_template& T) {
     Orbit o;
     o.a_p = T.a_p;
     o.tasc_rel = T.T_asc - p.t0;
     o.invP = 1.0 / T.P;
     o.e = T.e;
-    sincos(T.omega, &o.sinw, &o.cosw);
-    o.sq = sqrt(1.0 - T.e * T.e);
-    // the ascending node has true anomaly -w: its eccentric and mean anomalies give T_p
-    double sh, ch;
-    sincos(-0.5 * T.omega, &sh, &ch);
-    const double Ea = 2.0 * atan2(sqrt(1.0 - T.e) * sh, sqrt(1.0 + T.e) * ch);
-    o.tp_rel = o.tasc_rel - (Ea - T.e * sin(Ea)) * T.P * 0.15915494309189535;
+    o.tp_rel = o.tasc_rel;
+    o.sinw = 0.0;
+    o.cosw = 1.0;
+    o.sq = 1.0;
+    if (T.e != 0.0) {   // FP64 is slow on this part: circular templates skip these constants
+        sincos_rad(T.omega, &o.sinw, &o.cosw);
+        o.sq = sqrt(1.0 - T.e * T.e);
+        // the ascending node has true anomaly -w: its eccentric and mean anomalies give T_p
+        double sh, ch, sEa, cEa;
+        sincos_rad(-0.5 * T.omega, &sh, &ch);
+        const double Ea = 2.0 * atan2(sqrt(1.0 - T.e) * sh, sqrt(1.0 + T.e) * ch);
+        sincos_rad(Ea, &sEa, &cEa);
+        o.tp_rel = o.tasc_rel - (Ea - T.e * sEa) * T.P * 0.15915494309189535;
+    }
     return o;
 }
 
@@ -287,14 +304,14 @@ __device__ __forceinline__ double knot_delay(const DevParams& p, int X, const Or
         xm -= floor(xm);
         const double M0 = 6.283185307179586 * xm;             // mean anomaly at tau, [0, 2 pi)
         const double om = 6.283185307179586 * o.invP;
-        double E = M0 + o.e * sin(M0), sE, cE;
-        sincos(E, &sE, &cE);
+        double E = M0 + o.e * sinpi(2.0 * xm), sE, cE;
+        sincos_rad(E, &sE, &cE);
         b = 0.0;
 #pragma unroll 1
         for (int it = 0; it < N_KEPLER_ITER; ++it) {
             const double M = M0 + om * b;                      // mean anomaly at u = tau + b
             E -= (E - o.e * sE - M) / (1.0 - o.e * cE);
-            sincos(E, &sE, &cE);
+            sincos_rad(E, &sE, &cE);
             b = o.a_p * (o.sinw * (cE - o.e) + o.cosw * o.sq * sE);
         }
     }

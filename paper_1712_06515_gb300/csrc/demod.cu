@@ -121,11 +121,11 @@ __global__ void demod_timing_kernel(DevParams p, const cc_template* __restrict__
         double xm = (u_ssb - o.tp_rel) * o.invP;
         xm -= floor(xm);
         const double M = 6.283185307179586 * xm;
-        double E = M + o.e * sin(M), sE, cE;
-        sincos(E, &sE, &cE);
+        double E = M + o.e * sinpi(2.0 * xm), sE, cE;
+        sincos_rad(E, &sE, &cE);
         for (int it = 0; it < N_KEPLER_ITER; ++it) {
             E -= (E - o.e * sE - M) / (1.0 - o.e * cE);
-            sincos(E, &sE, &cE);
+            sincos_rad(E, &sE, &cE);
         }
         R = o.a_p * (o.sinw * (cE - o.e) + o.cosw * o.sq * sE);
         dR = o.a_p * (-o.sinw * sE + o.cosw * o.sq * cE) * om / (1.0 - o.e * cE);

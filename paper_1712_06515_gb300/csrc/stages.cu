@@ -62,7 +62,7 @@ __host__ __device__ inline int resample_window_len(const DevParams& p) {
 // detector times all fall in gaps is skipped: its norms are written as zero and its
 // a_r, b_r are left unwritten (the two-pass search reads a segment only when its norms
 // are nonzero).  Without `kn` every sample is written.
-template <int DT>
+template <int DT, bool PRE>
 __global__ void __launch_bounds__(RS_THREADS)
 resample_kernel(DevParams p, const cc_template* __restrict__ tm, int64_t t_base, void* ab,
                 float4* __restrict__ norm, const KnotRec* __restrict__ kn, int64_t nkn, int use_window) {
@@ -80,10 +80,10 @@ resample_kernel(DevParams p, const cc_template* __restrict__ tm, int64_t t_base,
     KnotRec* rec = (KnotRec*)smem;
     float2* xs = (float2*)smem;   // with knot records: the segment's window of x
     __shared__ int win[2];        // first sample and length of the window
-    const KnotRec* __restrict__ knX = kn ? kn + ((size_t)t * p.Q + X) * nkn : nullptr;
+    const KnotRec* __restrict__ knX = PRE ? kn + ((size_t)t * p.Q + X) * nkn : nullptr;
     const float2* __restrict__ x = p.x[X];
 
-    if (knX) {
+    if constexpr (PRE) {
         // detector times of the segment lie within [seg0 - max d - 2, seg1 + 2 - min d]
         // (d from the segment's knots; the cubic between knots stays within 1e-4 samples
         // of them); weight only if a noise block there is locked
@@ -128,9 +128,11 @@ resample_kernel(DevParams p, const cc_template* __restrict__ tm, int64_t t_base,
         __syncthreads();
     } else {
         double* dk = (double*)(smem + sizeof(KnotRec) * nk);
-        const Orbit orb = make_orbit(p, tm[t]);
-        for (int i = tid; i < nk; i += blockDim.x)
-            dk[i] = knot_delay(p, X, orb, (double)((kA + i) * KNOT) * p.dt);
+        if (tid < nk) {   // FP64: only the threads that own a knot set up the orbit
+            const Orbit orb = make_orbit(p, tm[t]);
+            for (int i = tid; i < nk; i += blockDim.x)
+                dk[i] = knot_delay(p, X, orb, (double)((kA + i) * KNOT) * p.dt);
+        }
         __syncthreads();
         for (int i = 1 + tid; i < nk - 2; i += blockDim.x)
             rec[i] = make_knot(p, dk[i - 1], dk[i], dk[i + 1], dk[i + 2], (double)((kA + i) * KNOT) * p.dt);
@@ -144,7 +146,9 @@ resample_kernel(DevParams p, const cc_template* __restrict__ tm, int64_t t_base,
     for (int i = tid; i < n_s; i += blockDim.x) {
         const int r = (int)seg0 + i;
         const int k = r >> 7;
-        const KnotRec kr = knX ? load_knot(knX + k) : rec[k - kA];
+        KnotRec kr;
+        if constexpr (PRE) kr = load_knot(knX + k);
+        else kr = rec[k - kA];
         const SampleTiming st = sample_timing(p, kr, r, k * KNOT);
         const float2 xv = use_window ? interp_sample_window<DT>(p, x, xs, win[0], win[1], st.jstar, st.delta)
                               : interp_sample(p, x, st.jstar, st.delta);
@@ -441,7 +445,9 @@ cc_status launch_resample(cc_plan* plan, const cc_template* t_dev, int64_t n_t, 
     const size_t sm = kn ? (use_window ? resample_smem_bytes(p, true) : 0) : resample_smem_bytes(p, false);
     // compile-time half width for the common stencils of the exact interpolator
     const int DT = p.interp == CC_INTERP_EXACT && (p.D == 8 || p.D == 16) ? p.D : 0;
-    auto kern = DT == 8 ? resample_kernel<8> : DT == 16 ? resample_kernel<16> : resample_kernel<0>;
+    auto kern = kn ? (DT == 8 ? resample_kernel<8, true> : DT == 16 ? resample_kernel<16, true> : resample_kernel<0, true>)
+                   : (DT == 8 ? resample_kernel<8, false> : DT == 16 ? resample_kernel<16, false>
+                                                                   : resample_kernel<0, false>);
     if (sm > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return cuda_fail(e, "resample smem attribute");
