@@ -78,6 +78,7 @@ constexpr int FUSED_THREADS = 512;
 constexpr int FUSED_WARPS = FUSED_THREADS / 32;
 constexpr int MAX_CLUSTER = 8;
 constexpr int ACC_SLOTS = 4;   // register pair-sum accumulators per thread (bins per coset <= 2048)
+constexpr size_t KNOT_WS_BUDGET = (size_t)8 << 30;   // knot records of one template batch
 constexpr int SEGACT_DEPTH = 4;   // ring of per-segment detector-activity flags in the fused kernel
 
 // Shared-memory layout and work split of the fused kernel (byte offsets).
@@ -382,6 +383,16 @@ __device__ __forceinline__ SampleTiming sample_timing(const DevParams& p, const 
     float psi = kr.psi - p.f_h_dt * pp - p.f_r_dt * (float)(r - rk);
     s.psi = psi - rintf(psi);
     return s;
+}
+
+// exp(2 pi i psi) for a phase psi in [-1/2, 1/2] cycles (sample_timing reduces it): the
+// hardware sine and cosine, whose absolute error on [-pi, pi] is below 4e-7, far inside the
+// FP32 parity bar; the full-range sincospif costs several times the instructions in a
+// kernel bound by instruction issue.
+__device__ __forceinline__ float2 phase_rot(float psi) {
+    float s, c;
+    __sincosf(6.283185307179586f * psi, &s, &c);
+    return make_float2(c, s);
 }
 
 // Windowed-sinc taps on xp[0 .. 2D] (sample j* - D first) at offset delta != 0: the sum

@@ -255,9 +255,7 @@ fused_kernel(DevParams p, FusedLayout lay, const cc_template* __restrict__ tm, i
                     }
                     const SampleTiming st = sample_timing(p, kr, r, k * KNOT);
                     const float2 xv = interp_sample(p, x, st.jstar, st.delta);
-                    float sn, cs;
-                    sincospif(2.0f * st.psi, &sn, &cs);
-                    const float2 xr = cmul(xv, make_float2(cs, sn));
+                    const float2 xr = cmul(xv, phase_rot(st.psi));
                     const SampleWeights wt = sample_weights(p, X, st.jstar, st.delta);
                     sa[li] = cscale(xr, wt.alpha);
                     sb[li] = cscale(xr, wt.beta);

@@ -6,7 +6,7 @@
 namespace cc {
 cc_status set_inputs(cc_plan* plan, const void* const* x_dev);
 cc_status launch_resample(cc_plan* plan, const cc_template* t_dev, int64_t n_t, void* ab, float* norm,
-                          cudaStream_t st, const KnotRec* kn = nullptr, int64_t nkn = 0);
+                          cudaStream_t st, const KnotRec* kn = nullptr, int64_t nkn = 0, int write_inactive = 0);
 cc_status launch_segfft(cc_plan* plan, const void* ab, int64_t n_t, void* F, cudaStream_t st);
 cc_status launch_norm_pairs(cc_plan* plan, const void* F, const float* norm, int64_t n_t, double* Dws,
                             float* rawws, float* rho, cudaStream_t st);
@@ -16,7 +16,9 @@ size_t two_pass_workspace_bytes(const cc_plan* plan, int64_t n_t);
 cc_status search_two_pass(cc_plan* plan, const cc_template* t_dev, int64_t n_t, float* rho, cudaStream_t st);
 
 constexpr size_t STAGED_WS_BUDGET = (size_t)6 << 30;
-constexpr size_t KNOT_WS_BUDGET = (size_t)8 << 30;
+size_t knot_bytes_per_template(const cc_plan* plan);
+cc_status resample_with_knots(cc_plan* plan, const cc_template* t_dev, int64_t n_t, void* ab, float* norm,
+                              cudaStream_t st, KnotRec* kn, int64_t kbatch);
 
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -26,11 +28,13 @@ static void staged_batch(const cc_plan* p, int64_t n_t, int64_t* batch, size_t* 
     const size_t ab = (size_t)p->Q * 2 * p->N_tau * elem;
     const size_t F = (size_t)p->Q * p->M * 2 * p->N_f * sizeof(float2);
     const size_t nm = (size_t)p->Q * p->M * sizeof(float4);
-    const size_t per = align256(ab) + align256(F) + align256(nm) + 256;
+    const size_t kn = knot_bytes_per_template(p);
+    const size_t per = align256(ab) + align256(F) + align256(nm) + align256(kn) + 256;
     int64_t b = (int64_t)std::max<size_t>(1, STAGED_WS_BUDGET / per);
     b = std::min<int64_t>(b, n_t);
     *batch = b;
-    *bytes = (align256(ab * b) + align256(F * b) + align256(nm * b) + align256(pair_workspace_bytes(p, b)));
+    *bytes = (align256(ab * b) + align256(F * b) + align256(nm * b) + align256(pair_workspace_bytes(p, b)) +
+              align256(kn * b));
 }
 
 // Fused path: layout for a batch of templates, knot-record batch and workspace bytes
@@ -134,9 +138,10 @@ extern "C" cc_status crosscorr_search(cc_plan* plan, const void* const* x_dev, c
     w += align256((size_t)plan->Q * plan->M * sizeof(float4) * batch);
     double* Dws = (double*)w;
     float* rawws = (float*)((char*)w + (((size_t)batch * sizeof(double) + 255) & ~(size_t)255));
+    KnotRec* kn = (KnotRec*)((char*)w + align256(pair_workspace_bytes(plan, batch)));
     for (int64_t t0 = 0; t0 < n_t; t0 += batch) {
         const int64_t nb = std::min(batch, n_t - t0);
-        if ((s = launch_resample(plan, t_dev + t0, nb, ab, nm, st)) != CC_OK) return s;
+        if ((s = resample_with_knots(plan, t_dev + t0, nb, ab, nm, st, kn, nb)) != CC_OK) return s;
         if ((s = launch_segfft(plan, ab, nb, F, st)) != CC_OK) return s;
         if ((s = launch_norm_pairs(plan, F, nm, nb, Dws, rawws, rho_dev + t0 * plan->N_f, st)) != CC_OK) return s;
     }

@@ -20,7 +20,7 @@
 namespace cc {
 
 cc_status launch_resample(cc_plan* plan, const cc_template* t_dev, int64_t n_t, void* ab, float* norm,
-                          cudaStream_t st, const KnotRec* kn = nullptr, int64_t nkn = 0);
+                          cudaStream_t st, const KnotRec* kn = nullptr, int64_t nkn = 0, int write_inactive = 0);
 cc_status launch_norm(cc_plan* plan, const float* norm, int64_t n_t, double* Dws, cudaStream_t st);
 cc_status launch_knots(cc_plan* plan, const cc_template* t_dev, int64_t n_t, KnotRec* kn, cudaStream_t st);
 cc_status launch_pair_finalize(cc_plan* plan, const float* raw, const double* Dws, int n_rows, int64_t n_t,
@@ -30,14 +30,11 @@ constexpr int SP_THREADS = 256;
 constexpr size_t TWO_PASS_WS_BUDGET = (size_t)24 << 30;   // a_r, b_r of one template batch
 
 struct SegPairLayout {
-    int nb;             // largest coset bin list
     int mmax;           // largest transform position of any bin
     int n_chunks;       // segment chunks per (template, weight, coset)
-    int pad_;
     int64_t chunk_len;  // segments per chunk
     size_t off_fft;     // [2][padded L] float2: out-of-place transform buffers
-    size_t off_h;       // [L/2] float2: detector 0's kept outputs (thread-private slots)
-    size_t off_bins;    // [nb] int2 (m, k)
+    size_t off_h;       // [mmax + 1] float2: detector 0's kept outputs (thread-private slots)
     size_t bytes;
 };
 
@@ -70,10 +67,7 @@ segpair_kernel(DevParams p, SegPairLayout lay, const void* __restrict__ ab, cons
     float2* A = (float2*)(sm + lay.off_fft);
     float2* Bf = A + PL;
     float2* H = (float2*)(sm + lay.off_h);
-    int2* bins = (int2*)(sm + lay.off_bins);
     const int o = __ldg(p.coset_off + c), nbc = __ldg(p.coset_off + c + 1) - o;
-    for (int i = tid; i < nbc; i += SP_THREADS)
-        bins[i] = make_int2(__ldg(p.coset_m + o + i), __ldg(p.coset_k + o + i));
 
     float accP[SLP], cmpP[SLP];
     float2 prevP[SLP];
@@ -186,7 +180,7 @@ segpair_kernel(DevParams p, SegPairLayout lay, const void* __restrict__ ab, cons
     }
     __syncthreads();
     float* outp = raw + ((size_t)t * 2 * lay.n_chunks + (size_t)w * lay.n_chunks + chunk) * p.N_f;
-    for (int i = tid; i < nbc; i += SP_THREADS) outp[bins[i].y] = accm[bins[i].x];
+    for (int i = tid; i < nbc; i += SP_THREADS) outp[__ldg(p.coset_k + o + i)] = accm[__ldg(p.coset_m + o + i)];
 }
 
 static size_t al16(size_t b) { return (b + 15) & ~(size_t)15; }
@@ -200,16 +194,11 @@ bool segpair_layout(const cc_plan* plan, int64_t n_t, SegPairLayout* lay) {
     if (p.L < 64 || p.L > 4096 || plan->N_f < 1) return false;
     lay->mmax = (int)((plan->kbar.back() - plan->k0) / p.C);
     if (2 * lay->mmax >= p.L) return false;
-    int nb = 1;
-    for (int c = 0; c < p.C; ++c) nb = std::max(nb, plan->coset_off[c + 1] - plan->coset_off[c]);
-    lay->nb = nb;
     size_t o = 0;
     lay->off_fft = o;
     o = al16(o + (size_t)2 * padded_len(p.L) * sizeof(float2));
     lay->off_h = o;
-    o = al16(o + (size_t)(p.L / 2) * sizeof(float2));
-    lay->off_bins = o;
-    o = al16(o + (size_t)nb * sizeof(int2));
+    o = al16(o + (size_t)(lay->mmax + 1) * sizeof(float2));
     lay->bytes = o;
     if (lay->bytes > 113 * 1024) return false;   // two CTAs per SM
     // chunks: about ten waves of two CTAs per SM, each chunk at least 4R + 1 segments

@@ -60,12 +60,14 @@ __host__ __device__ inline int resample_window_len(const DevParams& p) {
 // Stage 1: one block per (segment K, detector X, template t).  With `kn` (knot records
 // of the pre-pass, [n_t][Q][nkn]) the FP64 knots are not recomputed, and a segment whose
 // detector times all fall in gaps is skipped: its norms are written as zero and its
-// a_r, b_r are left unwritten (the two-pass search reads a segment only when its norms
-// are nonzero).  Without `kn` every sample is written.
+// a_r, b_r are written as zero (`write_inactive`, the staged stage: every weight there is
+// zero) or left unwritten (the two-pass search reads a segment only when its norms are
+// nonzero).  Without `kn` every sample is computed.
 template <int DT, bool PRE>
 __global__ void __launch_bounds__(RS_THREADS)
 resample_kernel(DevParams p, const cc_template* __restrict__ tm, int64_t t_base, void* ab,
-                float4* __restrict__ norm, const KnotRec* __restrict__ kn, int64_t nkn, int use_window) {
+                float4* __restrict__ norm, const KnotRec* __restrict__ kn, int64_t nkn, int use_window,
+                int write_inactive) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float red[32];
     __shared__ int active;
@@ -117,6 +119,13 @@ resample_kernel(DevParams p, const cc_template* __restrict__ tm, int64_t t_base,
         __syncthreads();
         if (!active) {
             if (tid == 0) norm[(t * p.Q + X) * p.M + K] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (write_inactive) {
+                const int64_t za = ((t * p.Q + X) * 2 + 0) * p.N_tau + seg0, zb = za + p.N_tau;
+                for (int i = tid; i < (int)p.N_s; i += blockDim.x) {
+                    store_series(ab, p.store, za + i, make_float2(0.f, 0.f));
+                    store_series(ab, p.store, zb + i, make_float2(0.f, 0.f));
+                }
+            }
             return;
         }
         // the segment's window of the series, zero outside [0, N_t)
@@ -152,9 +161,7 @@ resample_kernel(DevParams p, const cc_template* __restrict__ tm, int64_t t_base,
         const SampleTiming st = sample_timing(p, kr, r, k * KNOT);
         const float2 xv = use_window ? interp_sample_window<DT>(p, x, xs, win[0], win[1], st.jstar, st.delta)
                               : interp_sample(p, x, st.jstar, st.delta);
-        float sn, cs;
-        sincospif(2.0f * st.psi, &sn, &cs);
-        const float2 xr = cmul(xv, make_float2(cs, sn));
+        const float2 xr = cmul(xv, phase_rot(st.psi));
         const SampleWeights w = sample_weights(p, X, st.jstar, st.delta);
         store_series(ab, p.store, sa + r, cscale(xr, w.alpha));
         store_series(ab, p.store, sb + r, cscale(xr, w.beta));
@@ -437,7 +444,7 @@ size_t resample_smem_bytes(const DevParams& p, bool window) {
 }
 
 cc_status launch_resample(cc_plan* plan, const cc_template* t_dev, int64_t n_t, void* ab,
-                          float* norm, cudaStream_t st, const KnotRec* kn, int64_t nkn) {
+                          float* norm, cudaStream_t st, const KnotRec* kn, int64_t nkn, int write_inactive) {
     const DevParams& p = plan->dp;
     // with knot records, the segment's window of x is staged in shared memory when it
     // leaves room for several blocks per SM
@@ -455,11 +462,37 @@ cc_status launch_resample(cc_plan* plan, const cc_template* t_dev, int64_t n_t, 
     for (int64_t t0 = 0; t0 < n_t; t0 += MAX_GRID_YZ) {
         const int64_t nt = std::min<int64_t>(MAX_GRID_YZ, n_t - t0);
         dim3 grid((unsigned)p.M, (unsigned)p.Q, (unsigned)nt);
-        kern<<<grid, RS_THREADS, sm, st>>>(p, t_dev, t0, ab, (float4*)norm, kn, nkn, use_window);
+        kern<<<grid, RS_THREADS, sm, st>>>(p, t_dev, t0, ab, (float4*)norm, kn, nkn, use_window, write_inactive);
         count_launch();
     }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? CC_OK : cuda_fail(e, "resample launch");
+}
+
+cc_status launch_knots(cc_plan* plan, const cc_template* t_dev, int64_t n_t, KnotRec* kn, cudaStream_t st);
+
+// Knot records of one template's detectors, bytes.
+size_t knot_bytes_per_template(const cc_plan* plan) {
+    return (size_t)plan->Q * knot_rows(plan) * sizeof(KnotRec);
+}
+
+// The complete a_r, b_r and segment norms of n_t templates (the staged stage): FP64 knots
+// by the pre-pass for kbatch templates at a time into kn, then the resampling kernel
+// with those records, writing zeros where a detector's weights vanish over a segment.
+cc_status resample_with_knots(cc_plan* plan, const cc_template* t_dev, int64_t n_t, void* ab, float* norm,
+                              cudaStream_t st, KnotRec* kn, int64_t kbatch) {
+    const size_t elem = plan->cfg.store == CC_STORE_BF16 ? 4 : 8;
+    const size_t ab_t = (size_t)plan->Q * 2 * plan->N_tau * elem;
+    const size_t nm_t = (size_t)plan->Q * plan->M * 4;
+    const int64_t nkn = knot_rows(plan);
+    for (int64_t c0 = 0; c0 < n_t; c0 += kbatch) {
+        const int64_t nc = std::min(kbatch, n_t - c0);
+        cc_status s = launch_knots(plan, t_dev + c0, nc, kn, st);
+        if (s != CC_OK) return s;
+        s = launch_resample(plan, t_dev + c0, nc, (char*)ab + ab_t * c0, norm + nm_t * c0, st, kn, nkn, 1);
+        if (s != CC_OK) return s;
+    }
+    return CC_OK;
 }
 
 template <int LT>
@@ -588,7 +621,18 @@ cc_status crosscorr_resample(cc_plan* plan, const void* const* x_dev, const cc_t
     if (!t_dev || !ab_dev || !norm_dev) return fail(CC_ERR_INVALID, "null device pointer");
     cc_status s = set_inputs(plan, x_dev);
     if (s != CC_OK) return s;
-    return launch_resample(plan, t_dev, n_t, ab_dev, norm_dev, (cudaStream_t)stream, nullptr, 0);
+    // knot records in the plan's workspace, as many templates at a time as it holds (a
+    // caller-owned workspace too small for one template's records: knots in each block)
+    const size_t krow = knot_bytes_per_template(plan);
+    int64_t kbatch;
+    if (plan->ws_external) {
+        kbatch = std::min<int64_t>(n_t, (int64_t)(plan->ws_bytes / krow));
+    } else {
+        kbatch = std::max<int64_t>(1, std::min<int64_t>(n_t, (int64_t)(KNOT_WS_BUDGET / krow)));
+        if ((s = ensure_workspace(plan, krow * kbatch)) != CC_OK) return s;
+    }
+    if (kbatch < 1) return launch_resample(plan, t_dev, n_t, ab_dev, norm_dev, (cudaStream_t)stream, nullptr, 0, 0);
+    return resample_with_knots(plan, t_dev, n_t, ab_dev, norm_dev, (cudaStream_t)stream, (KnotRec*)plan->ws, kbatch);
 }
 
 cc_status crosscorr_segment_fft(cc_plan* plan, const void* ab_dev, int64_t n_t, void* F_dev,
