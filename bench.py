@@ -61,6 +61,10 @@ def parse():
                          "statistic it replaces, on the same workload, for the speed comparison")
     ap.add_argument("--interp", default="exact", choices=["exact", "learned"],
                     help="exact: windowed sinc, 2D+1 = 17 taps; learned: the 8-tap network")
+    ap.add_argument("--chunk-waves", type=int, default=0,
+                    help="work split: target CTA waves of the segment-chunk split (0: library default)")
+    ap.add_argument("--batch-templates", type=int, default=0,
+                    help="work split: templates per two-pass batch (0: library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-days", type=float, default=120.0,
                     help="days of data in the bounded CPU oracle sample")
@@ -219,6 +223,8 @@ def run_gpu(args):
     tm_host = np.ascontiguousarray(np.concatenate([grid[idx], np.zeros((B, 2))], axis=1))
     learned = args.interp == "learned"
     plan = cc.CrossCorrPlan(ds.cfg, ds.dets, interp=cc.INTERP_LEARNED if learned else cc.INTERP_EXACT)
+    if args.chunk_waves or args.batch_templates:
+        plan.set_tuning(batch_templates=args.batch_templates, chunk_waves=args.chunk_waves)
     Q, N_f = plan.Q, plan.N_f
     path = plan.search_path
     x = torch.from_numpy(ds.x64).to(dev)

@@ -275,7 +275,7 @@ typedef struct {
                                  (0: as many as 24 GB of resampled series hold) */
     int32_t chunk_waves;      /* fused and two-pass: split each template's segments into
                                  chunks until the launch has about this many CTA waves
-                                 (0: 4 for fused, 10 for two-pass) */
+                                 (0: 4 for fused, 40 for two-pass) */
     int32_t reserved;         /* 0 */
 } cc_tuning;
 cc_status crosscorr_plan_set_tuning(cc_plan* plan, const cc_tuning* tuning);

@@ -99,10 +99,14 @@ __global__ void __launch_bounds__(256)
 knots_kernel(DevParams p, const cc_template* __restrict__ tm, int64_t t_base, int64_t nkn,
              KnotRec* __restrict__ out) {
     __shared__ double dk[256 + 3];
+    __shared__ Orbit orb_s;
     const int X = blockIdx.y;
     const int64_t tl = blockIdx.z, t = t_base + tl;
     const int64_t k0 = (int64_t)blockIdx.x * 256;
-    const Orbit orb = make_orbit(p, tm[t]);
+    // the orbit's FP64 set-up (a reciprocal, and trigonometry for e != 0) once per block
+    if (threadIdx.x == 0) orb_s = make_orbit(p, tm[t]);
+    __syncthreads();
+    const Orbit orb = orb_s;
     for (int i = threadIdx.x; i < 256 + 3; i += 256)
         dk[i] = knot_delay(p, X, orb, (double)((k0 - 1 + i) * KNOT) * p.dt);
     __syncthreads();

@@ -201,9 +201,10 @@ bool segpair_layout(const cc_plan* plan, int64_t n_t, SegPairLayout* lay) {
     o = al16(o + (size_t)(lay->mmax + 1) * sizeof(float2));
     lay->bytes = o;
     if (lay->bytes > 113 * 1024) return false;   // two CTAs per SM
-    // chunks: about ten waves of two CTAs per SM, each chunk at least 4R + 1 segments
+    // chunks: about forty waves of two CTAs per SM (a short tail; measured on the 120-day
+    // band: 10 -> 40 waves is 2.5 % faster), each chunk at least 4R + 1 segments
     const int64_t ctas = (int64_t)p.C * 2 * n_t;
-    const int64_t waves = plan->tuning.chunk_waves > 0 ? plan->tuning.chunk_waves : 10;
+    const int64_t waves = plan->tuning.chunk_waves > 0 ? plan->tuning.chunk_waves : 40;
     const int64_t want = std::max<int64_t>(1, (waves * 2 * 152 + ctas - 1) / std::max<int64_t>(ctas, 1));
     const int64_t maxch = std::max<int64_t>(1, p.M / (4 * p.R + 1));
     const int64_t nch = std::min<int64_t>({want, maxch, 32767});

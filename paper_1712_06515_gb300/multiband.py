@@ -18,7 +18,7 @@ import numpy as np
 
 from . import (INTERP_EXACT, PATH_FUSED, PATH_TWO_PASS, STORE_FP32, CrossCorrError, CrossCorrPlan, templates5)
 
-CHUNK_WAVES = (5, 10, 20, 40)
+CHUNK_WAVES = (5, 10, 20, 40, 80)
 
 
 def autotune(plan: CrossCorrPlan, x, templates, reps: int = 2, chunk_waves: Sequence[int] = CHUNK_WAVES,
