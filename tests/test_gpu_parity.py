@@ -162,6 +162,36 @@ def test_resample_stage_parity(name):
                                            atol=2e-5 * max(1e-30, np.abs(norms[i]).max()))
 
 
+@pytest.mark.parametrize("ws_bytes", [256, None])
+def test_resample_stage_knot_paths(ws_bytes):
+    """The resampling stage takes its FP64 knots from the pre-pass when the workspace holds
+    one template's knot records (zeros written where a detector's weights vanish over a
+    segment) and computes them in each block when a caller-owned workspace is too small;
+    both against the oracle, and against each other on the zeroed (detector, segment)s."""
+    ds = case_ds("default", n_templates=2)
+    p = oracle.make_plan(ds.cfg)
+    with cc.CrossCorrPlan(ds.cfg, ds.dets) as plan:
+        x, tm = dev_inputs(ds)
+        if ws_bytes is not None:
+            plan.set_workspace(torch.empty(ws_bytes, dtype=torch.uint8, device=DEV))
+        ab = torch.full((2, plan.Q, 2, plan.N_tau), float("nan"), dtype=torch.complex64, device=DEV)
+        ab, nrm = plan.resample(x, tm, ab=ab)
+        ab = ab.cpu().numpy()
+        nrm = nrm.cpu().numpy()
+    n_used = p.M * p.N_s
+    for t, tmpl in enumerate(ds.templates):
+        for q in range(ds.cfg.n_det):
+            a, b, norms, ok = oracle_ab(ds, p, tmpl, q)
+            assert np.isfinite(ab[t, q, :, :n_used]).all()      # every sample of every segment written
+            scale = max(np.abs(a).max(), np.abs(b).max())
+            assert np.abs(ab[t, q, 0, :n_used] - a)[ok].max() <= 2e-5 * scale
+            assert np.abs(ab[t, q, 1, :n_used] - b)[ok].max() <= 2e-5 * scale
+            dead = (nrm[t, q, :, 0] == 0) & (nrm[t, q, :, 1] == 0)
+            for K in np.nonzero(dead)[0]:
+                seg = slice(K * p.N_s, (K + 1) * p.N_s)
+                assert np.all(ab[t, q, :, seg] == 0) and np.all(a[seg] == 0) and np.all(b[seg] == 0)
+
+
 @pytest.mark.parametrize("name", ["default", "fband_005", "T_max0"])
 def test_segment_fft_stage_parity(name):
     """Oracle a_r, b_r in, GPU spectra out, against the oracle's FFT route (which
