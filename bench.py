@@ -442,6 +442,12 @@ def run_multiband(args):
                    "templates_per_step": int(sum(t.shape[0] for (_, _, _, t) in bands)),
                    "template_scale": args.template_scale,
                    "paths": [{1: "fused", 2: "two-pass"}[t["path"]] + f"/w{t['chunk_waves']}" for t in mb.tuning],
+                   # per band, from the autotuner's timing of its first 64 templates: coset
+                   # length, ms per template, fraction of the FP32 peak (algorithmic flops)
+                   "bands": [{"L": int(pl.info["L"]), "ms_per_template": round(t["ms"] / min(64, tt.shape[0]), 4),
+                              "frac": round(algorithmic_costs(pl.info, pl.Q, 1, cf.D, learned)["total_flops"]
+                                            / (t["ms"] / min(64, tt.shape[0]) * 1e-3) / (peak * 1e12), 3)}
+                             for pl, t, tt, (cf, _, _, _) in zip(mb.plans, mb.tuning, mb.templates, bands)],
                    "interp": "learned 8-tap" if learned else "windowed sinc, 17 taps",
                    "l2": "inputs: 32 bands x 2 x 6.9 MB series (442 MB, larger than L2)"},
         "roofline": {"bound": "alu", "kernel": "graph (all kernels of all bands)", "achieved": achieved,

@@ -32,9 +32,11 @@ constexpr size_t TWO_PASS_WS_BUDGET = (size_t)24 << 30;   // a_r, b_r of one tem
 struct SegPairLayout {
     int mmax;           // largest transform position of any bin
     int n_chunks;       // segment chunks per (template, weight, coset)
+    int grouped;        // L <= 2048: transforms per CTA, min(4096 / L, 2 C) (segpair_grouped_kernel)
+    int pad_;
     int64_t chunk_len;  // segments per chunk
-    size_t off_fft;     // [2][padded L] float2: out-of-place transform buffers
-    size_t off_h;       // [mmax + 1] float2: detector 0's kept outputs (thread-private slots)
+    size_t off_fft;     // [G][2][padded L] float2: out-of-place transform buffers (G = 1 for L = 4096)
+    size_t off_h;       // [G][mmax + 1] float2: detector 0's kept outputs (thread-private slots)
     size_t bytes;
 };
 
@@ -183,6 +185,198 @@ segpair_kernel(DevParams p, SegPairLayout lay, const void* __restrict__ ab, cons
     for (int i = tid; i < nbc; i += SP_THREADS) outp[__ldg(p.coset_k + o + i)] = accm[__ldg(p.coset_m + o + i)];
 }
 
+// ---------------------------------------------------------------------------
+// Coset lengths L <= 2048: one transform per group of L/16 threads, G = 4096 / L groups
+// per 256-thread CTA, each group one (weight, coset) unit of the same template and chunk
+// (units u = w C + c, CTA x-index covering units x G .. x G + G - 1), so that every thread
+// holds 16 values in every pass: the radix-16 passes have L/16 butterflies, and the last
+// pass of radix R < 16 has 16 / R butterflies per thread.  (With one transform per CTA a
+// 256-point transform would keep 16 of 256 threads busy.)  The template, chunk and
+// segment are common to the CTA, so the detector-activity branches and the barriers are
+// uniform.
+template <int LT>
+struct GroupedShape {
+    static constexpr int L = LT;
+    static constexpr int G = 4096 / L;               // transforms per CTA
+    static constexpr int GT = L / 16;                // threads per transform
+    static constexpr int RLAST = last_radix(L);
+    static constexpr int NSL = L / RLAST;            // butterflies of the last pass
+    static constexpr int BPT = NSL / GT;             // of them per thread: 16 / RLAST
+    static constexpr int SLP = RLAST / 2 > 0 ? RLAST / 2 : 1;   // kept outputs per butterfly (m < L/2)
+    static constexpr int NINT = pp_intermediate_passes(L);      // radix-16 passes with NS = 16
+    static_assert(G * GT == SP_THREADS && BPT * RLAST == 16, "16 values per thread in every pass");
+};
+
+template <int LT, bool BF16>
+__global__ void __launch_bounds__(SP_THREADS, 2)
+segpair_grouped_kernel(DevParams p, SegPairLayout lay, const void* __restrict__ ab,
+                       const float4* __restrict__ norm, float* __restrict__ raw) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    using S = GroupedShape<LT>;
+    constexpr int L = S::L, PL = padded_len(L), GT = S::GT, RLAST = S::RLAST, NSL = S::NSL;
+    constexpr int BPT = S::BPT, SLP = S::SLP;
+    constexpr bool KEEP_READS_A = S::NINT == 0;   // the last pass reads the first pass's buffer
+
+    const int tid = threadIdx.x, g = tid / GT, j = tid % GT;
+    const int C = p.C;
+    const int u = blockIdx.x * lay.grouped + g;   // (weight, coset) unit of this group
+    const bool unit_ok = u < 2 * C;
+    const int c = unit_ok ? u % C : 0, w = unit_ok ? u / C : 0;
+    const int chunk = blockIdx.y;
+    const int64_t t = blockIdx.z;
+    const int Q = p.Q;
+    const int64_t N_s = p.N_s, R = p.R, M = p.M, N_tau = p.N_tau;
+    const int64_t Ka = (int64_t)chunk * lay.chunk_len;
+    const int64_t Kb = imin64(M, Ka + lay.chunk_len);
+    const int64_t Kl = imax64(0, Ka - R);
+    const int Hs = lay.mmax + 1;
+
+    float2* A = (float2*)(sm + lay.off_fft) + (size_t)g * 2 * PL;
+    float2* Bf = A + PL;
+    float2* H = (float2*)(sm + lay.off_h) + (size_t)g * Hs;
+
+    float accP[BPT * SLP], cmpP[BPT * SLP];
+    float2 prevP[BPT * SLP];
+#pragma unroll
+    for (int e = 0; e < BPT * SLP; ++e) {
+        accP[e] = cmpP[e] = 0.f;
+        prevP[e] = make_float2(0.f, 0.f);
+    }
+    const uint64_t N = (uint64_t)p.N_FFT, mask = N - 1;
+    const uint64_t bc = ((uint64_t)p.b0 + (uint64_t)c) & mask;
+    const float2* __restrict__ twr = p.twc + (size_t)c * N_s;
+    const float4* __restrict__ nt = norm + (size_t)t * Q * M;
+    const size_t abt = (size_t)t * Q * 2 * N_tau;
+    auto load_ab = [&](size_t i) -> float2 {
+        if constexpr (BF16) return __bfloat1622float2(((const __nv_bfloat162*)ab)[i]);
+        else return __ldg((const float2*)ab + i);
+    };
+
+    // first radix-16 pass of detector X's segment (sample r - seg0 at position r mod L,
+    // times the coset twiddle), stored to A
+    auto first_pass = [&](int X, int64_t seg0) {
+        const size_t row = abt + ((size_t)X * 2 + w) * N_tau + seg0;
+        const int offn = (int)((-seg0) & (int64_t)(L - 1));
+        float2 v[16];
+        if (N_s <= L) {
+            float2 vv[16], tw[16];
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                const int rr = (j + r * GT + offn) & (L - 1);
+                const bool in = unit_ok && rr < (int)N_s;
+                vv[r] = in ? load_ab(row + rr) : make_float2(0.f, 0.f);
+                tw[r] = in ? __ldg(twr + rr) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int r = 0; r < 16; ++r) v[r] = cmul(vv[r], tw[r]);
+        } else {
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                float2 acc = make_float2(0.f, 0.f);
+                if (unit_ok)
+                    for (int rr = (j + r * GT + offn) & (L - 1); rr < (int)N_s; rr += L)
+                        acc = cadd(acc, cmul(load_ab(row + rr), __ldg(twr + rr)));
+                v[r] = acc;
+            }
+        }
+        dft16(v);
+        float2* d = A + 17 * j;   // padi(16 j + r) = 17 j + r
+#pragma unroll
+        for (int r = 0; r < 16; ++r) d[r] = v[r];
+    };
+    // the passes after the first: an optional radix-16 pass (NS = 16) A -> B, then the
+    // last pass of radix RLAST into registers, BPT butterflies per thread: butterfly
+    // b = j + GT q leaves output r of its transform (bin m = b + NSL r) in o[q SLP + r]
+    auto rest = [&](float2 (&o)[BPT * SLP]) {
+        const float2* src = A;
+        if constexpr (S::NINT == 1) {
+            stockham_pass_oop_t<16, L, 16>(A, Bf, j, p.twL);
+            __syncthreads();
+            src = Bf;
+        }
+#pragma unroll
+        for (int q = 0; q < BPT; ++q) {
+            const int b = j + GT * q;
+            float2 v[16];
+            const float2* s = src + padi(b);
+#pragma unroll
+            for (int r = 0; r < RLAST; ++r) v[r] = s[r * pstride<NSL>()];
+            apply_twiddles<RLAST>(v, p.twL, b, L - 1);
+            dft_r<RLAST>(v);
+#pragma unroll
+            for (int r = 0; r < SLP; ++r) o[q * SLP + r] = v[r];
+        }
+    };
+
+    for (int64_t K = Kl; K < Kb; ++K) {
+        const int64_t seg0 = K * N_s;
+        const float2 wseg = twiddle_N((bc * ((uint64_t)seg0 & mask)) & mask, N);
+        const float4 n0 = nt[K], nl = nt[(size_t)(Q - 1) * M + K];
+        const bool a0 = n0.x + n0.y > 0.f, al = nl.x + nl.y > 0.f;
+        float2 o[BPT * SLP];
+        if (Q > 1 && a0) {
+            first_pass(0, seg0);
+            __syncthreads();
+            rest(o);
+#pragma unroll
+            for (int q = 0; q < BPT; ++q)
+#pragma unroll
+                for (int r = 0; r < SLP; ++r) {
+                    const int m = j + GT * q + NSL * r;
+                    if (m <= lay.mmax) H[m] = o[q * SLP + r];   // read back by this thread only
+                }
+            if constexpr (KEEP_READS_A) __syncthreads();   // detector 1's first pass rewrites A
+        }
+        if (al) {
+            first_pass(Q - 1, seg0);
+            __syncthreads();
+            rest(o);
+        }
+        const float2 wc = make_float2(wseg.x, -wseg.y);
+        const bool acc_on = K >= Ka;
+#pragma unroll
+        for (int q = 0; q < BPT; ++q)
+#pragma unroll
+            for (int r = 0; r < SLP; ++r) {
+                const int e = q * SLP + r;
+                const int m = j + GT * q + NSL * r;
+                if (m <= lay.mmax) {
+                    const float2 Fl = al ? o[e] : make_float2(0.f, 0.f);
+                    float2 F0 = Fl, F1 = make_float2(0.f, 0.f);
+                    if (Q > 1) {
+                        F0 = a0 ? H[m] : make_float2(0.f, 0.f);
+                        F1 = Fl;
+                    }
+                    const float2 Sv = cadd(F0, F1);
+                    const float2 P = R > 0 ? cmul(prevP[e], wc) : make_float2(0.f, 0.f);
+                    const float term = p.pair_mode == CC_PAIRS_ALL_ORDERED ? fmaf(2.f, redot(Sv, P), redot(Sv, Sv))
+                                                                           : redot(Sv, P) + redot(F1, F0);
+                    if (acc_on) kahan_add(accP[e], cmpP[e], term);
+                    if (R > 0) prevP[e] = cmul(Sv, wseg);
+                }
+            }
+        // with no intermediate pass the last pass read A, which the next segment's first
+        // pass rewrites
+        if constexpr (KEEP_READS_A) __syncthreads();
+    }
+    // partial sums of this group's (template, weight, chunk) row for its coset's bins
+    __syncthreads();
+    float* accm = (float*)A;
+#pragma unroll
+    for (int q = 0; q < BPT; ++q)
+#pragma unroll
+        for (int r = 0; r < SLP; ++r) {
+            const int m = j + GT * q + NSL * r;
+            if (m <= lay.mmax) accm[m] = accP[q * SLP + r];
+        }
+    __syncthreads();
+    if (unit_ok) {
+        const int o0 = __ldg(p.coset_off + c), nbc = __ldg(p.coset_off + c + 1) - o0;
+        float* outp = raw + ((size_t)t * 2 * lay.n_chunks + (size_t)w * lay.n_chunks + chunk) * p.N_f;
+        for (int i = j; i < nbc; i += GT) outp[__ldg(p.coset_k + o0 + i)] = accm[__ldg(p.coset_m + o0 + i)];
+    }
+}
+
 static size_t al16(size_t b) { return (b + 15) & ~(size_t)15; }
 static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -194,18 +388,24 @@ bool segpair_layout(const cc_plan* plan, int64_t n_t, SegPairLayout* lay) {
     if (p.L < 64 || p.L > 4096 || plan->N_f < 1) return false;
     lay->mmax = (int)((plan->kbar.back() - plan->k0) / p.C);
     if (2 * lay->mmax >= p.L) return false;
+    // L <= 2048: G transforms per CTA (segpair_grouped_kernel), each with its own buffers;
+    // no more groups than the template has (weight, coset) units
+    const int G = p.L <= 2048 ? std::min(4096 / (int)p.L, 2 * (int)p.C) : 1;
+    lay->grouped = p.L <= 2048 ? G : 0;
     size_t o = 0;
     lay->off_fft = o;
-    o = al16(o + (size_t)2 * padded_len(p.L) * sizeof(float2));
+    o = al16(o + (size_t)G * 2 * padded_len(p.L) * sizeof(float2));
     lay->off_h = o;
-    o = al16(o + (size_t)(lay->mmax + 1) * sizeof(float2));
+    o = al16(o + (size_t)G * (lay->mmax + 1) * sizeof(float2));
     lay->bytes = o;
     if (lay->bytes > 113 * 1024) return false;   // two CTAs per SM
     // chunks: about forty waves of two CTAs per SM (a short tail; measured on the 120-day
     // band: 10 -> 40 waves is 2.5 % faster), each chunk at least 4R + 1 segments
-    const int64_t ctas = (int64_t)p.C * 2 * n_t;
+    const int64_t ctas = (int64_t)((2 * p.C + G - 1) / G) * n_t;
+    // CTAs per SM: two of 256 threads, more when the grouped kernel's CTAs are smaller
+    const int64_t per_sm = p.L <= 2048 ? std::max<int64_t>(2, 2 * (4096 / p.L) / G) : 2;
     const int64_t waves = plan->tuning.chunk_waves > 0 ? plan->tuning.chunk_waves : 40;
-    const int64_t want = std::max<int64_t>(1, (waves * 2 * 152 + ctas - 1) / std::max<int64_t>(ctas, 1));
+    const int64_t want = std::max<int64_t>(1, (waves * per_sm * 152 + ctas - 1) / std::max<int64_t>(ctas, 1));
     const int64_t maxch = std::max<int64_t>(1, p.M / (4 * p.R + 1));
     const int64_t nch = std::min<int64_t>({want, maxch, 32767});
     lay->chunk_len = (p.M + nch - 1) / nch;
@@ -230,16 +430,41 @@ static cudaError_t launch_segpair_lt(dim3 grid, size_t smem, cudaStream_t st, co
     return launch_segpair_t<LT, false>(grid, smem, st, p, lay, ab, norm, raw);
 }
 
+template <int LT>
+static cudaError_t launch_grouped_lt(const DevParams& p, const SegPairLayout& lay, int64_t n_t, const void* ab,
+                                     const float4* norm, float* raw, cudaStream_t st) {
+    const int G = lay.grouped;
+    const dim3 grid((unsigned)((2 * p.C + G - 1) / G), (unsigned)lay.n_chunks, (unsigned)n_t);
+    const unsigned threads = (unsigned)(G * GroupedShape<LT>::GT);
+    if (p.store == CC_STORE_BF16) {
+        cudaError_t e = cudaFuncSetAttribute(segpair_grouped_kernel<LT, true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.bytes);
+        if (e != cudaSuccess) return e;
+        segpair_grouped_kernel<LT, true><<<grid, threads, lay.bytes, st>>>(p, lay, ab, norm, raw);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(segpair_grouped_kernel<LT, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.bytes);
+        if (e != cudaSuccess) return e;
+        segpair_grouped_kernel<LT, false><<<grid, threads, lay.bytes, st>>>(p, lay, ab, norm, raw);
+    }
+    return cudaGetLastError();
+}
+
 static cudaError_t launch_segpair(const DevParams& p, const SegPairLayout& lay, int64_t n_t, const void* ab,
                                   const float4* norm, float* raw, cudaStream_t st) {
+    if (lay.grouped) {
+        switch (p.L) {
+            case 64: return launch_grouped_lt<64>(p, lay, n_t, ab, norm, raw, st);
+            case 128: return launch_grouped_lt<128>(p, lay, n_t, ab, norm, raw, st);
+            case 256: return launch_grouped_lt<256>(p, lay, n_t, ab, norm, raw, st);
+            case 512: return launch_grouped_lt<512>(p, lay, n_t, ab, norm, raw, st);
+            case 1024: return launch_grouped_lt<1024>(p, lay, n_t, ab, norm, raw, st);
+            case 2048: return launch_grouped_lt<2048>(p, lay, n_t, ab, norm, raw, st);
+        }
+        return cudaErrorInvalidValue;
+    }
     const dim3 grid((unsigned)p.C, (unsigned)(2 * lay.n_chunks), (unsigned)n_t);
     switch (p.L) {
-        case 64: return launch_segpair_lt<64>(grid, lay.bytes, st, p, lay, ab, norm, raw);
-        case 128: return launch_segpair_lt<128>(grid, lay.bytes, st, p, lay, ab, norm, raw);
-        case 256: return launch_segpair_lt<256>(grid, lay.bytes, st, p, lay, ab, norm, raw);
-        case 512: return launch_segpair_lt<512>(grid, lay.bytes, st, p, lay, ab, norm, raw);
-        case 1024: return launch_segpair_lt<1024>(grid, lay.bytes, st, p, lay, ab, norm, raw);
-        case 2048: return launch_segpair_lt<2048>(grid, lay.bytes, st, p, lay, ab, norm, raw);
         case 4096: return launch_segpair_lt<4096>(grid, lay.bytes, st, p, lay, ab, norm, raw);
     }
     return cudaErrorInvalidValue;
