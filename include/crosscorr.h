@@ -191,7 +191,11 @@ cc_status crosscorr_plan_info(const cc_plan* plan, cc_plan_info* info, double* f
  *   alpha^2 sigma^2, beta^2 sigma^2, alpha beta sigma^2   (hat-A, hat-B, hat-C).
  * x_dev: host array of Q device pointers to complex64[N_t].  t_dev: device
  * cc_template[n_t].  ab_dev: device complex64 (store = FP32) or bf16 pairs
- * (store = BF16) [n_t][Q][2][N_tau].  norm_dev: device float[n_t][Q][M][4]. */
+ * (store = BF16) [n_t][Q][2][N_tau].  norm_dev: device float[n_t][Q][M][4].
+ * The FP64 timing knots of up to 8 GB of templates at a time are kept in the plan's
+ * workspace (grown as needed; a caller-owned workspace too small for one template's
+ * knots makes every block compute its own).  Samples of a segment over which a
+ * detector's noise blocks are all gaps are written as exact zeros. */
 cc_status crosscorr_resample(cc_plan* plan, const void* const* x_dev, const cc_template* t_dev,
                              int64_t n_t, void* ab_dev, float* norm_dev, void* stream);
 
