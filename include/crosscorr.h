@@ -350,14 +350,15 @@ const char* crosscorr_last_error(void);
  * diagnostic counter, incremented on the host at every launch). */
 uint64_t crosscorr_kernel_launches(void);
 
-/* Diagnostic timing of the fused kernel (off by default).  While on, each launch of the
- * fused kernel by crosscorr_search / crosscorr_search_noalloc is bracketed by a pair of
- * CUDA events recorded on the launching stream (the knot pre-pass and the final
+/* Diagnostic timing of the search's dominant kernel (off by default).  While on, each
+ * launch of the spectrum + pair-sum kernel (two-pass path) or of the one-pass kernel
+ * (fused path, crosscorr_search_noalloc) is bracketed by a pair of CUDA events recorded
+ * on the launching stream (the knot pre-pass, the resampling kernel and the final
  * normalisation pass are outside the pair).  Turning it off keeps the pending records. */
 cc_status crosscorr_plan_set_kernel_timing(cc_plan* plan, int on);
 
-/* Total device time of the fused-kernel launches recorded since the last call, in ms,
- * and their number; waits for those launches to finish, then clears the record. */
+/* Total device time of the timed launches recorded since the last call, in ms, and
+ * their number; waits for those launches to finish, then clears the record. */
 cc_status crosscorr_plan_kernel_time(cc_plan* plan, double* ms, int64_t* launches);
 
 #ifdef __cplusplus

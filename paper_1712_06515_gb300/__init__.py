@@ -316,11 +316,12 @@ class CrossCorrPlan:
         return rho
 
     def set_kernel_timing(self, on: bool = True):
-        """Diagnostic: bracket each fused-kernel launch with CUDA events on its stream."""
+        """Diagnostic: bracket each launch of the search's dominant kernel (spectrum + pair
+        sum on the two-pass path, the one-pass kernel on the fused path) with CUDA events."""
         check("crosscorr_plan_set_kernel_timing", self._lib.crosscorr_plan_set_kernel_timing(self._h, int(on)))
 
     def kernel_time(self):
-        """(total ms, launches) of the fused-kernel launches timed since the last call."""
+        """(total ms, launches) of the dominant-kernel launches timed since the last call."""
         ms, n = c_double(), c_int64()
         check("crosscorr_plan_kernel_time", self._lib.crosscorr_plan_kernel_time(self._h, byref(ms), byref(n)))
         return ms.value, n.value

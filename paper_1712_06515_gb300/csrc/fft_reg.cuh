@@ -142,49 +142,6 @@ __device__ __forceinline__ void apply_twiddles(float2 (&v)[16], const float2* __
     }
 }
 
-// One Stockham pass of radix R over an L-point buffer in padded shared memory, done
-// in place: loads, twiddles and the DFT in registers, barrier, stores.  `j` is this
-// thread's butterfly (active if j < L/R); `sync` is the barrier of the threads that
-// share the buffer.  Ns is the product of the radices of the earlier passes.
-template <int R, typename Sync>
-__device__ __forceinline__ void stockham_pass(float2* buf, int L, int Ns, int j,
-                                              const float2* __restrict__ twL, Sync sync) {
-    const int B = L / R;
-    float2 v[16];
-    const bool act = j < B;
-    const int k = j & (Ns - 1);
-    if (act) {
-#pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = buf[padi(j + r * B)];
-        if (Ns > 1) apply_twiddles<R>(v, twL, k * (L / (Ns * R)), L - 1);
-        dft_r<R>(v);
-    }
-    sync();
-    if (act) {
-        const int idxD = (j - k) * R + k;
-#pragma unroll
-        for (int r = 0; r < R; ++r) buf[padi(idxD + r * Ns)] = v[r];
-    }
-    sync();
-}
-
-// Stockham passes after the first one (which the caller runs on gathered registers):
-// radix-16 passes while at least 16 remain, then one pass of the leftover radix.
-template <typename Sync>
-__device__ __forceinline__ void stockham_rest(float2* buf, int L, int log2L, int Ns, int j,
-                                              const float2* __restrict__ twL, Sync sync) {
-    int rem = log2L;
-    for (int n = Ns; n > 1; n >>= 1) --rem;   // bits already transformed
-    while (rem >= 4) {
-        stockham_pass<16>(buf, L, Ns, j, twL, sync);
-        Ns <<= 4;
-        rem -= 4;
-    }
-    if (rem == 3) stockham_pass<8>(buf, L, Ns, j, twL, sync);
-    else if (rem == 2) stockham_pass<4>(buf, L, Ns, j, twL, sync);
-    else if (rem == 1) stockham_pass<2>(buf, L, Ns, j, twL, sync);
-}
-
 }  // namespace cc
 
 namespace cc {
