@@ -245,7 +245,7 @@ def run_gpu(args):
     clocks = ClockSampler(local)
     clocks.start()
     plan.kernel_time()            # clear
-    plan.set_kernel_timing(True)  # event pair around every fused-kernel launch, same stream
+    plan.set_kernel_timing(True)  # event pair around every dominant-kernel launch, same stream
     n0 = lib.crosscorr_kernel_launches()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
