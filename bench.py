@@ -35,9 +35,9 @@ METRIC = "CrossCorr rho templates*freq-bins/sec on 1 GB300 (+% HBM roofline) vs 
 UNIT = "template*bins/s"
 GRID_TEMPLATES = 8000
 # DRAM bytes read + written per template by segpair_kernel<4096> on this workload, from
-# the ncu capture summarised in profiles/segpair_kernel_o1_band_8_templates.md (8
-# templates in one launch; the reads of a_r, b_r grow with the templates of a launch).
-# None once the kernel changes.
+# an ncu capture of one launch on 8 templates (its summary is kept with the profiles;
+# the reads of a_r, b_r grow with the templates of a launch).  None once the kernel
+# changes.
 SEGPAIR_DRAM_BYTES_PER_TEMPLATE = (1.770469e9 + 74.267904e6) / 8
 SM_COUNT = 152
 FP32_LANES = 128
