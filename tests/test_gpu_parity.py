@@ -371,6 +371,22 @@ def test_o1_band_full_size_injected_template():
             assert_rho_close(got, ref)
 
 
+def test_o1_band_bench_launch_configuration_sampled_templates():
+    """The launch configuration bench.py times, at full size: the first 80 templates of the
+    8000-template grid (the bench's seed) in one search, i.e. two-pass batches of 72 and 8
+    templates with the default 40-wave chunk split; the first and last template of each
+    batch against the oracle at the FP32 bar."""
+    ds = synth.o1_band()
+    tm = np.ascontiguousarray(np.concatenate([ds.templates[:80], np.zeros((80, 2))], axis=1))
+    with cc.CrossCorrPlan(ds.cfg, ds.dets) as plan:
+        assert plan.search_path == cc.PATH_TWO_PASS
+        x = torch.from_numpy(ds.x64).to(DEV)
+        got = plan.search(x, torch.from_numpy(tm).to(DEV)).cpu().numpy().astype(np.float64)
+    pick = [0, 71, 72, 79]
+    ref = oracle.rho(ds, templates=ds.templates[pick])
+    assert_rho_close(got[pick], ref)
+
+
 def test_fused_search_is_deterministic_on_full_size_chunked_batch():
     """Race check: the fused kernel's halves and cluster peers meet only at barriers, so a
     chunked full-size batch (long gaps, segments with inactive detectors) gives the same
