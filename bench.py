@@ -491,23 +491,54 @@ def run_demod(args):
     n0 = lib.crosscorr_kernel_launches()
     clocks = ClockSampler(0)
     clocks.start()
+    plan.kernel_time()            # clear
+    plan.set_kernel_timing(True)  # event pair around every pair-loop launch, same stream
     e0.record(stream)
     for _ in range(args.steps):
         plan.demod_search(tm, rho)
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
+    plan.set_kernel_timing(False)
+    pair_ms, pair_launches = plan.kernel_time()
     elapsed = e0.elapsed_time(e1) / 1000.0
     units = B * plan.N_f * args.steps
     nsft = int(round(ds.cfg.T_sft / ds.cfg.dt))
-    locked = sum(int(np.sum(d.sigma[: ds.cfg.n_samples // nsft] > 0)) for d in ds.dets)
+    n_blk = ds.cfg.n_samples // nsft
+    lk = [np.asarray(d.sigma[:n_blk]) > 0 for d in ds.dets]
+    locked = sum(int(np.sum(v)) for v in lk)
+    # unordered pairs of distinct SFTs within T_max (every detector pair, lags 0..Rs blocks)
+    Rs = int(math.floor(ds.cfg.T_max / ds.cfg.T_sft + 1e-9))
+    pairs = 0
+    for X in range(len(lk)):
+        for Y in range(X, len(lk)):
+            for lag in range(0, Rs + 1):
+                if X == Y and lag == 0:
+                    continue
+                a, b = lk[X][: n_blk - lag], lk[Y][lag:]
+                pairs += int(np.sum(a & b))
+                if X != Y and lag > 0:
+                    pairs += int(np.sum(lk[Y][: n_blk - lag] & lk[X][lag:]))
+    # algorithmic flops per (template, bin): 12 per pair (the filter weight, Re of the
+    # product, the normalisation term, two accumulations) and 30 per locked SFT (two
+    # sinc-weighted bins, the phase and its rotation, Xi^2)
+    flops_tb = 12.0 * pairs + 30.0 * locked
+    clk_max = float((clk or {}).get("sm_max_mhz") or 2070.0)
+    peak = SM_COUNT * FP32_LANES * 2 * clk_max * 1e6 / 1e12
+    achieved = flops_tb * units / (pair_ms / 1e3) / 1e12 if pair_ms > 0 else None
     out = {
         "metric": METRIC, "value": units / elapsed, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000.0 * elapsed / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "o1_band: 2 det, 120 d at 60% duty, 0.5 Hz at 150 Hz, T_sft=360 s SFTs, "
                                "T_max=3600 s", "method": "detector-frame (demodulation) CrossCorr, n_bin=2",
-                   "templates_per_step": B, "locked_sfts": locked, "sft_ms_once": sft_ms},
+                   "templates_per_step": B, "locked_sfts": locked, "sft_pairs": pairs, "sft_ms_once": sft_ms},
+        "roofline": {"bound": "alu", "kernel": "demod_pair_kernel", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak if achieved else None, "traffic": None,
+                     "peak_kind": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 flop x {clk_max:g} MHz",
+                     "flops_per_template_bin": flops_tb, "kernel_ms_per_launch": pair_ms / max(1, pair_launches),
+                     "kernel_launches": pair_launches,
+                     "kernel_share_of_step": pair_ms / (1e3 * elapsed) if elapsed > 0 else None},
         "clocks": clk, "gpu_launches": int(lib.crosscorr_kernel_launches() - n0),
     }
     print(json.dumps(out), flush=True)

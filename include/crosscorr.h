@@ -351,9 +351,10 @@ const char* crosscorr_last_error(void);
 uint64_t crosscorr_kernel_launches(void);
 
 /* Diagnostic timing of the search's dominant kernel (off by default).  While on, each
- * launch of the spectrum + pair-sum kernel (two-pass path) or of the one-pass kernel
- * (fused path, crosscorr_search_noalloc) is bracketed by a pair of CUDA events recorded
- * on the launching stream (the knot pre-pass, the resampling kernel and the final
+ * launch of the spectrum + pair-sum kernel (two-pass path), of the one-pass kernel
+ * (fused path, crosscorr_search_noalloc) or of the pair-loop kernel of
+ * crosscorr_demod_search is bracketed by a pair of CUDA events recorded on the launching
+ * stream (the knot pre-pass, the resampling kernel and the final
  * normalisation pass are outside the pair).  Turning it off keeps the pending records. */
 cc_status crosscorr_plan_set_kernel_timing(cc_plan* plan, int on);
 

@@ -357,11 +357,15 @@ extern "C" cc_status crosscorr_demod_search(cc_plan* plan, const cc_template* t_
         demod_timing_kernel<<<dim3((unsigned)((n_blk + 127) / 128), (unsigned)p.Q, (unsigned)nb), 128, 0, st>>>(
             p, t_dev + t0, nsft, n_blk, df0, dK, (DemodTiming*)plan->ws);
         count_launch();
+        cudaEvent_t ev0, ev1;   // diagnostic timing of the pair loop (crosscorr_plan_set_kernel_timing)
+        timing_pair(plan, &ev0, &ev1);
+        if (ev0) cudaEventRecord(ev0, st);
         demod_pair_kernel<<<dim3((unsigned)((plan->N_f + nthr - 1) / nthr), (unsigned)nb), nthr, smem, st>>>(
             p, nsft, plan->demod_m_lo, plan->demod_nbins, n_blk, Rs, (const float2*)plan->demod_z,
             (const float4*)plan->demod_w, (const DemodTiming*)plan->ws, (const double*)plan->demod_df,
             (const int64_t*)plan->demod_kbar, t0, rho_dev);
         count_launch();
+        if (ev1) cudaEventRecord(ev1, st);
     }
     e = cudaGetLastError();
     return e == cudaSuccess ? CC_OK : cuda_fail(e, "demodulation launch");
