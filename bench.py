@@ -52,9 +52,10 @@ def parse():
     ap.add_argument("--templates", type=int, default=GRID_TEMPLATES,
                     help="templates per step per rank (default: the whole 40x200 grid)")
     ap.add_argument("--path", default="search", choices=["search", "staged"])
-    ap.add_argument("--workload", default="o1_band", choices=["o1_band", "multiband"],
-                    help="o1_band: the 120-day single band (default); multiband: 32 bands over "
-                         "20-250 Hz from one CUDA graph launch")
+    ap.add_argument("--workload", default="o1_band", choices=["o1_band", "o1_long", "multiband"],
+                    help="o1_band: the 120-day single band (default); o1_long: the same band at "
+                         "T_max = 36000 s with BF16 storage of the resampled series; multiband: 32 "
+                         "bands over 20-250 Hz from one CUDA graph launch")
     ap.add_argument("--template-scale", type=float, default=0.25,
                     help="multiband: fraction of the 4.1e5-template grid per step")
     ap.add_argument("--method", default="resampled", choices=["resampled", "demod"],
@@ -216,14 +217,16 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    ds = synth.o1_band(seed=1002)
+    long_lag = args.workload == "o1_long"
+    ds = synth.o1_band(seed=1002, T_max=36000.0 if long_lag else 3600.0)
     B = args.templates
     grid = ds.templates
     idx = (np.arange(B) + rank * B) % grid.shape[0]
     # template rows (a_p, T_asc, P, e, omega): the circular grid with e = omega = 0
     tm_host = np.ascontiguousarray(np.concatenate([grid[idx], np.zeros((B, 2))], axis=1))
     learned = args.interp == "learned"
-    plan = cc.CrossCorrPlan(ds.cfg, ds.dets, interp=cc.INTERP_LEARNED if learned else cc.INTERP_EXACT)
+    plan = cc.CrossCorrPlan(ds.cfg, ds.dets, interp=cc.INTERP_LEARNED if learned else cc.INTERP_EXACT,
+                            store=cc.STORE_BF16 if long_lag else cc.STORE_FP32)
     if args.chunk_waves or args.batch_templates:
         plan.set_tuning(batch_templates=args.batch_templates, chunk_waves=args.chunk_waves)
     Q, N_f = plan.Q, plan.N_f
@@ -322,7 +325,8 @@ def run_gpu(args):
         peak = SM_COUNT * FP32_LANES * 2 * clk_max * 1e6 / 1e12
         other_ms = max(0.0, 1e3 * elapsed - fused_ms) / (B * args.steps)
         traffic = None
-        if path == cc.PATH_TWO_PASS and SEGPAIR_DRAM_BYTES_PER_TEMPLATE is not None and fused_launches:
+        if path == cc.PATH_TWO_PASS and SEGPAIR_DRAM_BYTES_PER_TEMPLATE is not None and fused_launches \
+                and not long_lag:
             traffic = SEGPAIR_DRAM_BYTES_PER_TEMPLATE * B * args.steps / fused_launches
         # the staged stage kernels are HBM-bound: algorithmic bytes (input read once,
         # output written once) over their event-timed duration, against the measured copy peak
@@ -348,12 +352,16 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": 1000.0 * elapsed / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "o1_band: 2 det, 120 d at 60% duty, 0.5 Hz at 150 Hz, "
-                                   "T_sft=360 s, T_max=T_short=3600 s, 40x200 orbital grid",
+            "config": {"workload": ("o1_long: 2 det, 120 d at 60% duty, 0.5 Hz at 150 Hz, T_sft=360 s, "
+                                    "T_max=T_short=36000 s, BF16 storage of the resampled series, "
+                                    "40x200 orbital grid") if long_lag else
+                                   ("o1_band: 2 det, 120 d at 60% duty, 0.5 Hz at 150 Hz, "
+                                    "T_sft=360 s, T_max=T_short=3600 s, 40x200 orbital grid"),
                        "templates_per_step_per_rank": B, "grid_templates": GRID_TEMPLATES,
                        "N_f": N_f, "N_FFT": info["N_FFT"], "M": info["M"], "L": info["L"], "C": info["C"],
                        "l2": "inputs larger than L2 (2 x 83 MB complex64 series)",
-                       "timing_precision": "f64 knots, f32 interpolation/FFT/pairs",
+                       "timing_precision": "f64 knots, f32 interpolation/FFT/pairs"
+                                           + (", bf16 storage of a_r, b_r" if long_lag else ""),
                        "search_path": {cc.PATH_FUSED: "fused (one cluster kernel)",
                                        cc.PATH_TWO_PASS: "two-pass (resample to HBM, then spectra + pairs)",
                                        cc.PATH_STAGED: "staged"}[path],
@@ -471,7 +479,8 @@ def run_demod(args):
     import synth
     import paper_1712_06515_gb300 as cc
     dev = torch.device("cuda", 0)
-    ds = synth.o1_band(seed=1002)
+    long_lag = args.workload == "o1_long"
+    ds = synth.o1_band(seed=1002, T_max=36000.0 if long_lag else 3600.0)
     B = args.templates
     tm = cc.templates5(torch.from_numpy(np.ascontiguousarray(ds.templates[:B])).to(dev))
     plan = cc.CrossCorrPlan(ds.cfg, ds.dets)
