@@ -26,3 +26,22 @@ def test_reference_arm_json_line():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert "workload" in d["config"]
+
+
+def test_roofline_flop_count_at_the_120_day_band():
+    """The numerator of the bench's roofline: the spectrum kernel's algorithmic flops per
+    template on the 120-day band (N_FFT = 32768, M = 2880 segments of 3600 samples, 12356
+    bins, R = 1, two detectors), written out here term by term: 2 weights x 2 detectors x
+    2880 segments of 5 N log2 N, and 8 flops per (weight, detector, segment, bin) and
+    partner with 2R + 2 = 4 partners."""
+    sys.path.insert(0, ROOT)
+    import bench
+    info = {"N_FFT": 32768, "M": 2880, "N_f": 12356, "N_tau": 2880 * 3600, "R": 1}
+    c = bench.algorithmic_costs(info, 2, 1)
+    fft = 2 * 2 * 2880 * (5 * 32768 * 15)
+    pairs = 2 * 2 * 2880 * 12356 * 8 * 4
+    assert c["fft_flops"] == fft == 28_311_552_000
+    assert c["pair_flops"] == pairs == 4_554_915_840
+    assert abs(c["fft_flops"] + c["pair_flops"] - 3.2866e10) < 1e6
+    # resampling: 17 taps x 8 flops + 30 per sample and detector
+    assert c["interp_flops"] == 2 * 2880 * 3600 * (8 * 17 + 30)
