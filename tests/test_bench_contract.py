@@ -45,3 +45,13 @@ def test_roofline_flop_count_at_the_120_day_band():
     assert abs(c["fft_flops"] + c["pair_flops"] - 3.2866e10) < 1e6
     # resampling: 17 taps x 8 flops + 30 per sample and detector
     assert c["interp_flops"] == 2 * 2880 * 3600 * (8 * 17 + 30)
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    """Under torchrun only rank 0 runs the reference arm and prints; the others exit 0."""
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                          "--steps", "1", "--warmup", "0", "--cpu-days", "2"], capture_output=True, text=True,
+                         timeout=600, cwd=ROOT, env=env)
+    assert out.returncode == 0, out.stderr[-2000:]
+    assert not [l for l in out.stdout.splitlines() if l.startswith("{")]
