@@ -87,3 +87,42 @@ def test_library_metric_and_lattice_match_oracle():
     ref = olat.lattice(g, 0.1, lo, hi)
     got = cc.lattice(g, 0.1, lo, hi)
     np.testing.assert_array_equal(got, ref)
+
+
+def test_library_metric_and_lattice_reject_bad_arguments():
+    """Error behaviour of the host functions as the header states it: invalid sizes and
+    ranges are CC_ERR_INVALID, an eccentric orbit is CC_ERR_UNSUPPORTED for the metric,
+    and an output smaller than the lattice is refused after *n_out reports its size."""
+    import ctypes
+    import paper_1712_06515_gb300 as cc
+    from paper_1712_06515_gb300 import _lib
+    _lib.build()
+    lib = _lib.load()
+    dp = ctypes.POINTER(ctypes.c_double)
+    orb = np.array([A_P, 5000.0, P, 0.0, 0.0])
+    g = np.zeros(9)
+    call = lambda T_obs, T_sft, T_max, Q, f, o: lib.crosscorr_metric(
+        T_obs, T_sft, T_max, Q, f, o.ctypes.data_as(ctypes.c_void_p), 0.0, g.ctypes.data_as(dp))
+    assert call(86400.0, 360.0, 3600.0, 2, F, orb) == 0
+    assert call(86400.0, 0.0, 3600.0, 2, F, orb) == 1           # T_sft > 0
+    assert call(86400.0, 360.0, -1.0, 2, F, orb) == 1           # T_max >= 0
+    assert call(86400.0, 360.0, 3600.0, 0, F, orb) == 1         # 1 <= Q
+    assert call(200.0, 360.0, 3600.0, 2, F, orb) == 1           # fewer than two SFTs
+    ecc = orb.copy()
+    ecc[3] = 0.2
+    assert call(86400.0, 360.0, 3600.0, 2, F, ecc) == 5         # circular orbits only
+    assert lib.crosscorr_metric(86400.0, 360.0, 3600.0, 2, F, None, 0.0, g.ctypes.data_as(dp)) == 1
+
+    gm = olat.metric(86400.0 * 10, 360.0, 3600.0, 2, F, A_P, 5000.0, P).ravel().copy()
+    lo = np.array([1.36, 4000.0, P - 0.2])
+    hi = np.array([1.52, 4600.0, P + 0.2])
+    n = ctypes.c_int64()
+    args = lambda mu, l, h: (gm.ctypes.data_as(dp), mu, l.ctypes.data_as(dp), h.ctypes.data_as(dp))
+    assert lib.crosscorr_lattice(*args(0.1, lo, hi), None, 0, ctypes.byref(n)) == 0 and n.value > 1
+    small = np.zeros((n.value - 1, 5))
+    assert lib.crosscorr_lattice(*args(0.1, lo, hi), small.ctypes.data_as(ctypes.c_void_p), n.value - 1,
+                                 ctypes.byref(n)) == 1
+    assert lib.crosscorr_lattice(*args(0.0, lo, hi), None, 0, ctypes.byref(n)) == 1      # mu > 0
+    assert lib.crosscorr_lattice(*args(0.1, hi, lo), None, 0, ctypes.byref(n)) == 1      # lo <= hi
+    with pytest.raises(cc.CrossCorrError):
+        cc.lattice(gm.reshape(3, 3), -1.0, lo, hi)
