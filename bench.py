@@ -63,6 +63,8 @@ def parse():
                          "statistic it replaces, on the same workload, for the speed comparison")
     ap.add_argument("--interp", default="exact", choices=["exact", "learned"],
                     help="exact: windowed sinc, 2D+1 = 17 taps; learned: the 8-tap network")
+    ap.add_argument("--search-path", default="auto", choices=["auto", "fused", "two_pass", "staged"],
+                    help="force the path of crosscorr_search (auto: the library's choice)")
     ap.add_argument("--chunk-waves", type=int, default=0,
                     help="work split: target CTA waves of the segment-chunk split (0: library default)")
     ap.add_argument("--batch-templates", type=int, default=0,
@@ -229,6 +231,8 @@ def run_gpu(args):
                             store=cc.STORE_BF16 if long_lag else cc.STORE_FP32)
     if args.chunk_waves or args.batch_templates:
         plan.set_tuning(batch_templates=args.batch_templates, chunk_waves=args.chunk_waves)
+    if args.search_path != "auto":
+        plan.set_path({"fused": cc.PATH_FUSED, "two_pass": cc.PATH_TWO_PASS, "staged": cc.PATH_STAGED}[args.search_path])
     Q, N_f = plan.Q, plan.N_f
     path = plan.search_path
     x = torch.from_numpy(ds.x64).to(dev)
