@@ -15,7 +15,8 @@ import paper_1712_06515_gb300 as cc  # noqa: E402
 DEV = torch.device("cuda:0")
 
 
-@pytest.mark.parametrize("n_prime,T_sft,f_h", [(360, 360.0, 150.0), (64, 64.0, 120.0), (1440, 1440.0, 99.5)])
+@pytest.mark.parametrize("n_prime,T_sft,f_h", [(360, 360.0, 150.0), (64, 64.0, 120.0), (1440, 1440.0, 99.5),
+                                               (64, 64.0, 120.015625)])   # odd heterodyne bin 7681
 def test_sfts_to_series_matches_oracle(n_prime, T_sft, f_h):
     rng = np.random.default_rng(n_prime)
     n_blocks = 40

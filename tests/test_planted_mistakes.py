@@ -6,6 +6,10 @@ the oracle module's source held in memory, executes that source in place of the 
 a fresh interpreter, re-binds the package's names to the mutated functions, and runs the
 module's pin tests there: they must fail.  Nothing is written to disk.  An entry whose
 text no longer occurs in the source fails the test, so the list follows the oracle.
+
+Only mistakes that change some result are listed: with f_h on an SFT bin (the reading
+the SFT-to-series conversion rests on) the per-SFT heterodyne factor exp(-2 pi i f_h K
+T_sft) is exactly 1, so flipping its sign changes nothing and is not a mistake to catch.
 """
 import os
 import subprocess
@@ -84,13 +88,39 @@ LEARNED = [
     ("output bias dropped", "return h @ model.W3 + model.b3", "return h @ model.W3"),
 ]
 
+ORBITS = [
+    ("Kepler's equation sign", "dE = (E - e * np.sin(E) - M) / (1.0 - e * np.cos(E))",
+     "dE = (E + e * np.sin(E) - M) / (1.0 - e * np.cos(E))"),
+    ("periapsis from +w", "    nu = -omega", "    nu = omega"),
+    ("cos E - e", "(np.cos(E) - e)", "(np.cos(E) + e)"),
+    ("sqrt(1 - e^2) dropped", "math.sqrt(1.0 - e * e) * np.sin(E)", "(1.0 - e * e) * np.sin(E)"),
+]
+
+SFT_SERIES = [
+    ("half-band sign dropped", "np.where(j % 2 == 0, 1.0, -1.0) * np.fft.ifft", "1.0 * np.fft.ifft"),
+    ("heterodyne phase at the SFT mid-time", "cyc = f_h * (K * T_sft)", "cyc = f_h * ((K + 0.5) * T_sft)"),
+    ("1/T_sft dropped", "* Np / T_sft", "* Np"),
+]
+
+LATTICE = [
+    ("factor 1/2 dropped", "return 0.5 * (dd @ dd.T) / dd.shape[1]", "return (dd @ dd.T) / dd.shape[1]"),
+    ("dPhi/dP without 1/P", "* (t - T_asc_rel) * c / P])", "* (t - T_asc_rel) * c])"),
+    ("spacing mu / g", "d = math.sqrt(mu / g[i, i])", "d = mu / g[i, i]"),
+    ("same-time pairs of one detector", "mult = Q * (Q - 1) // 2 if lag == 0 else Q * Q", "mult = Q * Q"),
+    ("dPhi/da_p sign", "return np.stack([-2.0 * math.pi * f * np.sin(psi),",
+     "return np.stack([2.0 * math.pi * f * np.sin(psi),"),
+]
+
 CASES = ([("oracle.crosscorr", "oracle/crosscorr.py", "tests/test_oracle_pins.py") + m for m in CROSSCORR]
+         + [("oracle.crosscorr", "oracle/crosscorr.py", "tests/test_orbit_pins.py") + m for m in ORBITS]
+         + [("oracle.sft_series", "oracle/sft_series.py", "tests/test_sft_series_pins.py") + m for m in SFT_SERIES]
+         + [("oracle.lattice", "oracle/lattice.py", "tests/test_lattice.py") + m for m in LATTICE]
          + [("oracle.demod", "oracle/demod.py", "tests/test_demod_pins.py") + m for m in DEMOD]
          + [("oracle.learned", "oracle/learned.py", "tests/test_learned_pins.py") + m for m in LEARNED])
 
 
 @pytest.mark.parametrize("mod_name,path,pins,what,old,new", CASES,
-                         ids=[f"{c[0].split('.')[1]}: {c[3]}" for c in CASES])
+                         ids=[f"{os.path.basename(c[2])[:-3]}: {c[3]}" for c in CASES])
 def test_planted_mistake_is_caught(mod_name, path, pins, what, old, new):
     r = subprocess.run([sys.executable, "-c", RUNNER, ROOT, mod_name, os.path.join(ROOT, path), old, new,
                         os.path.join(ROOT, pins)], cwd=ROOT, capture_output=True, text=True, timeout=600)

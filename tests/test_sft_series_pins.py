@@ -47,9 +47,9 @@ def test_round_trip_of_a_band_limited_series():
     assert abs(dtp - 2.0) < 1e-15
 
 
+@pytest.mark.parametrize("k_h", [96, 97])       # odd k_h: f_h (K + 1/2) T_sft is not an integer
 @pytest.mark.parametrize("dl", [5, -11, 0])
-def test_tone_on_a_bin_is_phase_continuous_across_sfts(dl):
-    k_h = 96
+def test_tone_on_a_bin_is_phase_continuous_across_sfts(dl, k_h):
     f_h = k_h / T_SFT
     f = (k_h + dl) / T_SFT
     phi = 0.4
