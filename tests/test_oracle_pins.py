@@ -263,6 +263,8 @@ def test_recovered_power_matches_paper():
     Ns, M = 64, 64
     cfg = SearchConfig(t0=0.0, dt=1.0, n_samples=Ns * M, f_h=100.0, f_band=0.2,
                        T_sft=Ns, T_max=Ns, T_short=Ns, pair_mode=oracle.PAIR_CROSS_ONLY)
+    # the paper's set-up: pairs up to T_max = T_short span T_coh = 3 T_short
+    assert oracle.make_plan(cfg).T_coh == g["T_coh_over_T_short"] * Ns
     kappas = (np.arange(48) + 0.5) / 48 - 0.5
     for mult, expect in zip((1, 2, 3), g["values"]):
         p = oracle.make_plan(cfg, n_fft=3 * Ns * mult)
@@ -285,6 +287,19 @@ def _zero_roemer_tiny(seed, noise, inj=None, n=4096, sigma_jitter=0.2, duty=0.85
                     const_ab=(0.7, -0.4), sigma_jitter=sigma_jitter, duty=duty,
                     templates=np.array([[0.0, synth.T_ASC_O1, synth.SCO_X1_P]]))
     return ds
+
+
+def test_noise_block_against_exact_floor():
+    """The T_sft block of detector time t = (j* + delta) dt' is floor((j* + delta) / nsft),
+    here in exact rational arithmetic, for offsets of both signs at and near block
+    boundaries (the oracle decides it from the integer j* and the sign of delta)."""
+    from fractions import Fraction
+    nsft = 360
+    js = np.arange(-2 * nsft - 3, 2 * nsft + 4)
+    for d in (-0.5, -0.3, -1e-9, 0.0, 1e-9, 0.25, 0.4999):
+        got = oracle.noise_block(js, np.full(js.shape, d), nsft)
+        ref = [math.floor((Fraction(int(j)) + Fraction(d)) / nsft) for j in js]
+        assert list(got) == ref, d
 
 
 def test_unit_variance_in_noise():

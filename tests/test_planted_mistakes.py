@@ -58,6 +58,21 @@ CROSSCORR = [
     ("bins rounded up", "kbar = k0 + np.floor(nu_R * k).astype(np.int64)",
      "kbar = k0 + np.ceil(nu_R * k).astype(np.int64)"),
     ("sigma for sigma^2", "    alpha = np.where(m, a / s2, 0.0)", "    alpha = np.where(m, a / np.sqrt(s2), 0.0)"),
+    ("T_coh without 2 T_max", "T_coh = 2.0 * cfg.T_max + T_short", "T_coh = cfg.T_max + T_short"),
+    ("metric spacing constant", "dlf = math.sqrt(6.0 * cfg.mu_f / math.pi) / T_coh",
+     "dlf = math.sqrt(3.0 * cfg.mu_f / math.pi) / T_coh"),
+    ("k0 one bin low", "f_FFT) * T_FFT + 1e-9))", "f_FFT) * T_FFT - 1e-9))"),
+    ("f_FFT without the half band", "f_FFT = cfg.f_h + f_r - 0.5 / dt", "f_FFT = cfg.f_h + f_r"),
+    ("taps mirrored", "acc += xj * (w[n] * np.sinc(delta - (n - D)))", "acc += xj * (w[n] * np.sinc(delta + (n - D)))"),
+    ("table fraction reversed", "    f = u - i\n", "    f = i - u + 1.0\n"),
+    ("noise-block tie", "return np.where((rem == 0) & (delta < 0), q - 1, q)",
+     "return np.where((rem == 0) & (delta > 0), q - 1, q)"),
+    ("b from the a table", "    b = _lerp(det.ab_t0, det.ab_dt, det.b_tab, t)", "    b = _lerp(det.ab_t0, det.ab_dt, det.a_tab, t)"),
+    ("f_r* rotation sign", "pre = np.exp(-2j * np.pi * (plan.f_r * s * plan.dt))",
+     "pre = np.exp(2j * np.pi * (plan.f_r * s * plan.dt))"),
+    ("sqrt(2) dropped", "rho_k = math.sqrt(2.0) * raw / math.sqrt(Dn)", "rho_k = raw / math.sqrt(Dn)"),
+    ("R rounded up", "R = int(math.floor(cfg.T_max / T_short + 1e-9))", "R = int(math.ceil(cfg.T_max / T_short + 1e-9))"),
+    ("ragged tail kept", "M = int(cfg.n_samples) // N_s", "M = -(-int(cfg.n_samples) // N_s)"),
 ]
 
 DEMOD = [
