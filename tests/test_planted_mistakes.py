@@ -90,6 +90,14 @@ DEMOD = [
     ("Xi weight dropped", "Y.append(xi * zK * np.exp(-2j * np.pi * cyc))", "Y.append(zK * np.exp(-2j * np.pi * cyc))"),
     ("b from the a table", "BH.append(scale * _lerp(det.ab_t0, det.ab_dt, det.b_tab, tmid))",
      "BH.append(scale * _lerp(det.ab_t0, det.ab_dt, det.a_tab, tmid))"),
+    ("pairs at exactly T_max dropped", "if T[L] - T[K] > T_max + 1e-9:", "if T[L] - T[K] > T_max - 1e-9:"),
+    ("2 dropped from the normalisation", "raw / np.sqrt(2.0 * den), 0.0)", "raw / np.sqrt(den), 0.0)"),
+    ("Earth's Doppler dropped from dtau/dt", "return dl - R, (1.0 + ddl) * (1.0 - dR)", "return dl - R, (1.0 - dR)"),
+    ("orbital Doppler sign", "return dl - R, (1.0 + ddl) * (1.0 - dR)", "return dl - R, (1.0 + ddl) * (1.0 + dR)"),
+    ("(f - f_h) t dropped from the phase", "cyc = np.outer(d, f) + np.outer(tmid, dfreq)", "cyc = np.outer(d, f)"),
+    ("z_K not divided by Xi", "return zK / xi, xi", "return zK, xi"),
+    ("SSB slope per table step", "ddl = (det.ssb_delay[i + 1] - det.ssb_delay[i]) / det.eph_dt",
+     "ddl = (det.ssb_delay[i + 1] - det.ssb_delay[i])"),
 ]
 
 LEARNED = [
@@ -101,6 +109,12 @@ LEARNED = [
     ("floor for negative offsets", "j0 = np.where(neg, jstar - 1, jstar)", "j0 = jstar"),
     ("u for negative offsets", "u = np.where(neg, delta + 1.0, delta)", "u = np.abs(delta)"),
     ("output bias dropped", "return h @ model.W3 + model.b3", "return h @ model.W3"),
+    ("first bias dropped", "h = np.tanh(s @ model.W1 + model.b1)", "h = np.tanh(s @ model.W1)"),
+    ("inputs swapped", "    h = np.tanh(s @ model.W1 + model.b1)", "    h = np.tanh(s[..., ::-1] @ model.W1 + model.b1)"),
+    ("taps reversed", "acc += np.where(ok, x[np.clip(j, 0, N_t - 1)], 0.0) * c[..., n]",
+     "acc += np.where(ok, x[np.clip(j, 0, N_t - 1)], 0.0) * c[..., model.n_taps - 1 - n]"),
+    ("samples outside the series kept", "        ok = (j >= 0) & (j < N_t)\n        acc += np.where(ok,",
+     "        ok = (j >= -N_t) & (j < N_t)\n        acc += np.where(ok,"),
 ]
 
 ORBITS = [
