@@ -190,9 +190,10 @@ def test_delay_special_cases():
 # ---------------------------------------------------------------------------
 # Spectra, pairs, normalisation
 # ---------------------------------------------------------------------------
+@pytest.mark.parametrize("f_h", [120.0, 120.3])      # f_h dt' not an integer: the heterodyne matters
 @pytest.mark.parametrize("f_band", [0.5, 0.05, 0.37])
-def test_direct_dft_equals_fft_route(f_band):
-    cfg = SearchConfig(t0=0.0, dt=1.0, n_samples=2048, f_h=120.0, f_band=f_band,
+def test_direct_dft_equals_fft_route(f_band, f_h):
+    cfg = SearchConfig(t0=0.0, dt=1.0, n_samples=2048, f_h=f_h, f_band=f_band,
                        T_sft=64.0, T_max=128.0, T_short=128.0)
     p = oracle.make_plan(cfg)
     rng = np.random.default_rng(7)

@@ -73,6 +73,11 @@ CROSSCORR = [
     ("sqrt(2) dropped", "rho_k = math.sqrt(2.0) * raw / math.sqrt(Dn)", "rho_k = raw / math.sqrt(Dn)"),
     ("R rounded up", "R = int(math.floor(cfg.T_max / T_short + 1e-9))", "R = int(math.ceil(cfg.T_max / T_short + 1e-9))"),
     ("ragged tail kept", "M = int(cfg.n_samples) // N_s", "M = -(-int(cfg.n_samples) // N_s)"),
+    ("remainder as printed (no final |b|)", "math.floor(abs(a) / abs(b)) * abs(b)", "math.floor(abs(a) / abs(b))"),
+    ("direct DFT at absolute frequencies", "cyc = np.outer(plan.dfreq, r * plan.dt)", "cyc = np.outer(plan.freq, r * plan.dt)"),
+    ("hat-A with sigma", "A = (alpha[:n] ** 2 * s2[:n])", "A = (alpha[:n] ** 2 * np.sqrt(s2[:n]))"),
+    ("top-k ties by descending index", "order = np.lexsort((np.arange(flat.size), -flat))[:k]",
+     "order = np.lexsort((-np.arange(flat.size), -flat))[:k]"),
 ]
 
 DEMOD = [
