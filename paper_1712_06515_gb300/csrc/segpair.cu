@@ -186,10 +186,11 @@ segpair_kernel(DevParams p, SegPairLayout lay, const void* __restrict__ ab, cons
 }
 
 // ---------------------------------------------------------------------------
-// Coset lengths L <= 2048: one transform per group of L/16 threads, G = 4096 / L groups
-// per 256-thread CTA, each group one (weight, coset) unit of the same template and chunk
-// (units u = w C + c, CTA x-index covering units x G .. x G + G - 1), so that every thread
-// holds 16 values in every pass: the radix-16 passes have L/16 butterflies, and the last
+// Coset lengths L <= 2048: one transform per group of L/16 threads, G = min(4096 / L, 2 C)
+// groups per CTA (256 threads when the template has at least 4096 / L (weight, coset)
+// units, fewer otherwise), each group one unit of the same template and chunk (units
+// u = w C + c, CTA x-index covering units x G .. x G + G - 1), so that every thread holds
+// 16 values in every pass: the radix-16 passes have L/16 butterflies, and the last
 // pass of radix R < 16 has 16 / R butterflies per thread.  (With one transform per CTA a
 // 256-point transform would keep 16 of 256 threads busy.)  The template, chunk and
 // segment are common to the CTA, so the detector-activity branches and the barriers are
@@ -197,7 +198,7 @@ segpair_kernel(DevParams p, SegPairLayout lay, const void* __restrict__ ab, cons
 template <int LT>
 struct GroupedShape {
     static constexpr int L = LT;
-    static constexpr int G = 4096 / L;               // transforms per CTA
+    static constexpr int G = 4096 / L;               // transforms per 256-thread CTA (at most)
     static constexpr int GT = L / 16;                // threads per transform
     static constexpr int RLAST = last_radix(L);
     static constexpr int NSL = L / RLAST;            // butterflies of the last pass
