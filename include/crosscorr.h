@@ -232,7 +232,10 @@ cc_status crosscorr_search(cc_plan* plan, const void* const* x_dev, const cc_tem
  *   - plans that need the staged path (BF16 storage, very long segments) return
  *     CC_ERR_UNSUPPORTED;
  *   - the first call on a device looks up the array's device address with that device
- *     current, so make that first call before any stream capture;
+ *     current, so make that first call before any stream capture; after a device reset
+ *     (cudaDeviceReset or another teardown of the primary context) the array is reloaded,
+ *     possibly at another address, and the next call looks it up again, so that call too
+ *     must come before any capture;
  *   - every call shares the array and it keeps the last call's contents; each call
  *     overwrites the entries it uses before reading them, so nothing needs clearing,
  *     but calls that overlap on the GPU (other streams, other host threads) race on it
@@ -334,7 +337,11 @@ cc_status crosscorr_lattice(const double* g, double mu, const double* lo, const 
 
 /* The k largest rho over (template, bin) of a device float[n_t][N_f] array,
  * descending, ties by (template, bin) ascending; hits_host receives
- * min(k, n_t*N_f) records.  Synchronises the stream.  1 <= k <= 4096. */
+ * min(k, n_t*N_f) records.  Synchronises the stream.  1 <= k <= 4096.
+ * Its candidate lists live in a plan-owned buffer of about 15 MB, allocated by the
+ * first call on the plan (later calls allocate nothing) and separate from the search
+ * workspace, so a search queued on another stream for the same plan is not disturbed;
+ * two top-k calls on one plan must not run at the same time (one plan per thread). */
 cc_status crosscorr_rho_topk(cc_plan* plan, const float* rho_dev, int64_t n_t, int k,
                              cc_hit* hits_host, void* stream);
 

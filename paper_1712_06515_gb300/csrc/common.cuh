@@ -146,6 +146,8 @@ struct cc_plan {
     // workspace (grown on demand by staged/fused paths)
     void* ws = nullptr;
     size_t ws_bytes = 0;
+    // top-k candidate lists (crosscorr_rho_topk), allocated by its first call
+    void* topk_ws = nullptr;
 };
 
 namespace cc {

@@ -6,9 +6,11 @@
 
 namespace cc {
 
-// rho = sqrt(2) sum_chunks raw / sqrt(sum_chunks D), in place on the first chunk's row
-__global__ void finalize_kernel(const float* __restrict__ raw, const double* __restrict__ dpart,
-                                int64_t N_f, int n_chunks, int64_t t_base, float* __restrict__ rho) {
+// rho = sqrt(2) sum_chunks raw / sqrt(sum_chunks D).  With one chunk the caller passes
+// raw == rho (the kernel scales rho in place: each thread reads its element before it
+// writes it), so neither pointer is declared __restrict__.
+__global__ void finalize_kernel(const float* raw, const double* __restrict__ dpart,
+                                int64_t N_f, int n_chunks, int64_t t_base, float* rho) {
     const int64_t t = t_base + blockIdx.y;
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= N_f) return;

@@ -24,11 +24,45 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocMaxTemplates];
 
-// Device address of g_noalloc_scratch on each device, resolved on the first call made
-// with that device current.  In host code the array's name is only a stand-in for
-// the symbol, not an address a kernel can use.
+// Device address of g_noalloc_scratch in each device's current context, resolved on
+// the first call made with that device current.  In host code the array's name is only
+// a stand-in for the symbol, not an address a kernel can use.  The address belongs to
+// the context the module was loaded into: after cudaDeviceReset (or any teardown of the
+// primary context) the module is loaded again, possibly elsewhere, so the cache is keyed
+// by the context's process-unique id and the next call resolves the address anew.
+typedef int (*CtxGetCurrentFn)(void**);                        // cuCtxGetCurrent
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);         // cuCtxGetId
+
 std::mutex g_mu;
-double* g_scratch_ptr[kMaxDevices] = {};
+struct ScratchEntry {
+    unsigned long long ctx_id;   // 0: not resolved
+    double* ptr;
+};
+ScratchEntry g_scratch[kMaxDevices] = {};
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+
+// Id of the context current on this thread, 0 when none is current yet.
+cc_status current_context_id(unsigned long long* id) {
+    *id = 0;
+    if (!g_ctx_current || !g_ctx_id) {
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+        if (e == cudaSuccess)
+            e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+        if (e != cudaSuccess) return cc::cuda_fail(e, "cudaGetDriverEntryPointByVersion");
+        if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return cc::fail(CC_ERR_CUDA, "driver entry points cuCtxGetCurrent/cuCtxGetId not found");
+        g_ctx_current = (CtxGetCurrentFn)f1;
+        g_ctx_id = (CtxGetIdFn)f2;
+    }
+    void* ctx = nullptr;
+    if (g_ctx_current(&ctx) != 0) return cc::fail(CC_ERR_CUDA, "cuCtxGetCurrent failed");
+    if (ctx && g_ctx_id(ctx, id) != 0) return cc::fail(CC_ERR_CUDA, "cuCtxGetId failed");
+    return CC_OK;
+}
 
 cc_status scratch_for_current_device(double** out) {
     int dev = 0;
@@ -36,13 +70,18 @@ cc_status scratch_for_current_device(double** out) {
     if (e != cudaSuccess) return cc::cuda_fail(e, "cudaGetDevice");
     if (dev < 0 || dev >= kMaxDevices) return cc::fail(CC_ERR_UNSUPPORTED, "device ordinal above 63");
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[dev]) {
+    unsigned long long id = 0;
+    cc_status s = current_context_id(&id);
+    if (s != CC_OK) return s;
+    if (id == 0 || g_scratch[dev].ctx_id != id) {
         void* ptr = nullptr;
-        e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);   // makes the primary context current if needed
         if (e != cudaSuccess) return cc::cuda_fail(e, "cudaGetSymbolAddress (static scratch)");
-        g_scratch_ptr[dev] = (double*)ptr;
+        if ((s = current_context_id(&id)) != CC_OK) return s;
+        g_scratch[dev].ctx_id = id;
+        g_scratch[dev].ptr = (double*)ptr;
     }
-    *out = g_scratch_ptr[dev];
+    *out = g_scratch[dev].ptr;
     return CC_OK;
 }
 

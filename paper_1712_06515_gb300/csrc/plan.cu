@@ -174,6 +174,7 @@ void crosscorr_plan_destroy(cc_plan* p) {
         if (d) cudaFree(d);
     if (p->learned_w) cudaFree(p->learned_w);
     if (p->learned_taps) cudaFree(p->learned_taps);
+    if (p->topk_ws) cudaFree(p->topk_ws);
     delete p;
 }
 

@@ -16,6 +16,12 @@ namespace cc {
 
 constexpr int TOPK_THREADS = 512;
 constexpr int TOPK_MAX = 4096;
+constexpr int TOPK_BLOCKS = 304;   // pass-1 blocks (two per SM)
+
+// per-block lists of TOPK_MAX candidates plus the merged list, values and indices
+static size_t topk_buffer_bytes() {
+    return ((size_t)TOPK_BLOCKS + 1) * TOPK_MAX * (sizeof(float) + sizeof(long long)) + 64;
+}
 
 struct __align__(16) Cand {
     float v;
@@ -82,7 +88,11 @@ __device__ void scan_slice(const float* __restrict__ src, const long long* __res
             }
         }
         __syncthreads();
-        int n = *ncand;
+        const int n = *ncand;
+        // every thread has read the count before any thread admits the next tile's
+        // candidates: otherwise a fast warp's atomicAdd reaches a slow warp's read and the
+        // warps disagree on whether to merge (divergent barriers, overfull buffer)
+        __syncthreads();
         if (n > KP - (int)blockDim.x || base + blockDim.x >= end) {
             if (n > 0) merge_best(s, KP, n);
             if (threadIdx.x == 0) *ncand = 0;
@@ -133,14 +143,20 @@ extern "C" cc_status crosscorr_rho_topk(cc_plan* plan, const float* rho_dev, int
     int KP = 1;
     while (KP < k) KP <<= 1;
     KP = std::max(KP, 2 * TOPK_THREADS);   // candidate buffer must exceed one tile
-    int nb = (int)std::min<long long>(304, (n + 65535) / 65536);
+    int nb = (int)std::min<long long>(TOPK_BLOCKS, (n + 65535) / 65536);
     nb = std::max(nb, 1);
     size_t cand = (size_t)nb * KP;
-    size_t need = cand * (sizeof(float) + sizeof(long long)) + (size_t)KP * (sizeof(float) + sizeof(long long)) + 64;
-    // The workspace is shared with other calls on this plan; grow it if needed.
-    cc_status s = ensure_workspace(plan, std::max(need, plan->ws_bytes));
-    if (s != CC_OK) return s;
-    char* w = (char*)plan->ws;
+    // Candidate lists live in a buffer of their own, sized once for the largest k and
+    // block count, so top-k never touches (or grows) the search workspace: a search
+    // queued on another stream for this plan keeps its workspace intact.
+    if (!plan->topk_ws) {
+        cudaError_t ea = cudaMalloc(&plan->topk_ws, topk_buffer_bytes());
+        if (ea != cudaSuccess) {
+            plan->topk_ws = nullptr;
+            return cuda_fail(ea, "top-k candidate buffer");
+        }
+    }
+    char* w = (char*)plan->topk_ws;
     long long* ci = (long long*)w;
     long long* fi = ci + cand;
     float* cv = (float*)(fi + KP);

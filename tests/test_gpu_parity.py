@@ -327,6 +327,29 @@ def test_topk_ordering_and_ties():
     assert np.allclose(hits["freq"], plan.freqs[hits["bin"]])
 
 
+@pytest.mark.parametrize("kind,k", [("ramp", 4096), ("ramp", 700), ("normal", 4096), ("ties", 1000)])
+def test_topk_many_tiles_per_block(kind, k):
+    """Top-k over 2.5e7 values: each of the 304 pass-1 blocks scans ~160 tiles of 512.  A
+    rising ramp admits every element of every tile, so candidate buffers fill and merge
+    every few tiles with k near the buffer size; the result must equal the oracle's."""
+    ds = case_ds("default")
+    with cc.CrossCorrPlan(ds.cfg, ds.dets) as plan:
+        n_t = -(-25_000_000 // plan.N_f)
+        n = n_t * plan.N_f
+        rng = np.random.default_rng(17)
+        if kind == "ramp":
+            vals = (np.arange(n, dtype=np.float64) * 1e-3 + rng.uniform(0, 5e-4, n)).astype(np.float32)
+        elif kind == "normal":
+            vals = rng.standard_normal(n).astype(np.float32)
+        else:   # many equal values: ties decided by the flat index
+            vals = rng.integers(0, 50, n).astype(np.float32)
+        vals = vals.reshape(n_t, plan.N_f)
+        hits = plan.topk(torch.from_numpy(vals).to(DEV), k)
+        ti, bi, vi = oracle.topk(vals.astype(np.float64), k)
+    assert list(zip(hits["tmpl"], hits["bin"])) == list(zip(ti, bi))
+    np.testing.assert_array_equal(hits["rho"], vi.astype(np.float32))
+
+
 def test_plain_day_all_templates():
     """One day, 1 Hz band at 100 Hz, 20% gaps, T_max = 0, the 4x4x4 grid (64 templates)."""
     ds = synth.plain_day()
