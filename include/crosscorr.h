@@ -253,7 +253,9 @@ cc_status crosscorr_search_noalloc(cc_plan* plan, const void* const* x_dev, cons
  *                     storage type (up to 24 GB of workspace), then one CTA per
  *                     (coset, weight) transforms each segment and folds it into the
  *                     pair sum on chip (Q <= 2, R <= 1, not CC_PAIRS_CROSS_ONLY, coset
- *                     length >= 64, output bins in the lower half of each coset);
+ *                     length >= 64, output bins in the lower half of each coset); for
+ *                     coset length 4096 with whole segments this is a persistent kernel
+ *                     fed by TMA bulk copies (see crosscorr_plan_check);
  *   CC_PATH_STAGED    the three stage kernels with spectra in HBM (any plan). */
 enum { CC_PATH_AUTO = 0, CC_PATH_FUSED = 1, CC_PATH_TWO_PASS = 2, CC_PATH_STAGED = 3 };
 
@@ -334,6 +336,15 @@ cc_status crosscorr_metric(double T_obs, double T_sft, double T_max, int32_t Q, 
                            double t0, double* g);
 cc_status crosscorr_lattice(const double* g, double mu, const double* lo, const double* hi, cc_template* out,
                             int64_t capacity, int64_t* n_out);
+
+/* Device-side status of the plan's kernels.  Kernels that wait on asynchronous copies
+ * (the persistent spectrum kernel of the two-pass path waits on its TMA bulk copies)
+ * bound every wait to about one second; a wait that runs out sets a device error word of
+ * the plan and the kernel returns early.  This call synchronises `stream`, reads the
+ * word, clears it and returns CC_ERR_TIMEOUT if it was set (the rho of every search since
+ * the previous check is then invalid), else CC_OK.  crosscorr_rho_topk makes the same
+ * check.  No counterpart in the paper: error reporting of this implementation. */
+cc_status crosscorr_plan_check(cc_plan* plan, void* stream);
 
 /* The k largest rho over (template, bin) of a device float[n_t][N_f] array,
  * descending, ties by (template, bin) ascending; hits_host receives

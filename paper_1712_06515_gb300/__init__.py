@@ -326,6 +326,11 @@ class CrossCorrPlan:
         check("crosscorr_plan_kernel_time", self._lib.crosscorr_plan_kernel_time(self._h, byref(ms), byref(n)))
         return ms.value, n.value
 
+    def check(self, stream=None):
+        """Synchronise the stream and raise if a kernel's bounded device wait ran out since
+        the last check (the rho of those searches is then invalid)."""
+        check("crosscorr_plan_check", self._lib.crosscorr_plan_check(self._h, _stream_handle(stream)))
+
     def topk(self, rho, k, stream=None):
         """k best (template, bin, freq, rho), descending, ties by (template, bin)."""
         import torch

@@ -81,6 +81,33 @@ __device__ __forceinline__ void dft16(float2 (&v)[16]) {
     for (int i = 0; i < 16; ++i) v[i] = t[i];
 }
 
+// The 16-point DFT of dft16 restricted to its outputs X[0..7], left in v[0..7] (v[8..15]
+// hold intermediate values): the outer 4-point DFTs need only their outputs k2 = 0, 1,
+// X[k1] = (Y0 + Y2) + (Y1 + Y3) and X[k1 + 4] = (Y0 - Y2) - i (Y1 - Y3).
+__device__ __forceinline__ void dft16_lo8(float2 (&v)[16]) {
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft4(v[n2], v[n2 + 4], v[n2 + 8], v[n2 + 12]);
+    v[5] = w16<1>(v[5]);
+    v[9] = w16<2>(v[9]);
+    v[13] = w16<3>(v[13]);
+    v[6] = w16<2>(v[6]);
+    v[10] = w16<4>(v[10]);
+    v[14] = w16<6>(v[14]);
+    v[7] = w16<3>(v[7]);
+    v[11] = w16<6>(v[11]);
+    v[15] = w16<9>(v[15]);
+    float2 t[8];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        const float2 a0 = v[4 * k1], a1 = v[4 * k1 + 1], a2 = v[4 * k1 + 2], a3 = v[4 * k1 + 3];
+        const float2 s0 = cadd(a0, a2), d0 = csub(a0, a2), s1 = cadd(a1, a3), d1 = mul_negi(csub(a1, a3));
+        t[k1] = cadd(s0, s1);
+        t[k1 + 4] = cadd(d0, d1);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = t[i];
+}
+
 // 8-point DFT: n = 4 n1 + n2 (n1 < 2), k = k1 + 2 k2.
 __device__ __forceinline__ void dft8(float2 (&v)[16]) {
 #pragma unroll

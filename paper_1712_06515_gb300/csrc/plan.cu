@@ -165,6 +165,21 @@ cc_status crosscorr_plan_kernel_time(cc_plan* plan, double* ms, int64_t* launche
     return CC_OK;
 }
 
+cc_status crosscorr_plan_check(cc_plan* plan, void* stream) {
+    if (!plan) return cc::fail(CC_ERR_INVALID, "plan is null");
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, plan->dp.err, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cc::cuda_fail(e, "reading the device error word");
+    if (h == 0) return CC_OK;
+    e = cudaMemsetAsync(plan->dp.err, 0, sizeof(unsigned), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cc::cuda_fail(e, "clearing the device error word");
+    return cc::fail(CC_ERR_TIMEOUT, "a kernel's bounded wait for its staged samples ran out; "
+                                    "the results of the searches since the last check are invalid");
+}
+
 void crosscorr_plan_destroy(cc_plan* p) {
     if (!p) return;
     for (void* d : p->dev_allocs) cudaFree(d);
@@ -360,6 +375,16 @@ cc_status crosscorr_plan(const cc_config* cfg, const cc_detector* dets, cc_plan*
         double ang = -2.0 * M_PI * (double)j / (double)L;
         tw[j] = make_float2((float)cos(ang), (float)sin(ang));
     }
+    // second radix-16 pass of an L-point transform (Stockham, 16 butterfly classes k):
+    // tw2[r][k] = exp(-2 pi i (L / 256) k r / L), r, k < 16
+    std::vector<float2> tw2(256);
+    for (int64_t r = 0; r < 16; ++r)
+        for (int64_t k = 0; k < 16; ++k) {
+            const int64_t j = ((L / 256) * k * r) % L;
+            const double ang = -2.0 * M_PI * (double)j / (double)L;
+            tw2[r * 16 + k] = make_float2((float)cos(ang), (float)sin(ang));
+        }
+    const unsigned zero_word = 0;
     p->coset_off = off;
     // per-coset twiddles of the segment-local sample index (FP64 phase, exact integer index)
     const int64_t b0 = ((p->k0 - N / 2) % N + N) % N;
@@ -377,7 +402,9 @@ cc_status crosscorr_plan(const cc_config* cfg, const cc_detector* dets, cc_plan*
         (st = upload(p, off.data(), off.size(), &dp.coset_off)) != CC_OK ||
         (st = upload(p, ck.data(), ck.size(), &dp.coset_k)) != CC_OK ||
         (st = upload(p, cm.data(), cm.size(), &dp.coset_m)) != CC_OK ||
-        (st = upload(p, tw.data(), tw.size(), &dp.twL)) != CC_OK) {
+        (st = upload(p, tw.data(), tw.size(), &dp.twL)) != CC_OK ||
+        (st = upload(p, tw2.data(), tw2.size(), &dp.tw2)) != CC_OK ||
+        (st = upload(p, &zero_word, 1, (const unsigned**)&dp.err)) != CC_OK) {
         crosscorr_plan_destroy(p);
         return st;
     }

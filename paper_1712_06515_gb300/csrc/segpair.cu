@@ -14,8 +14,7 @@
 // unordered pair set, 2 Re(conj(S) P) + |S|^2 with auto-correlation included.
 #include <algorithm>
 
-#include "common.cuh"
-#include "fft_reg.cuh"
+#include "segpair.cuh"
 
 namespace cc {
 
@@ -29,16 +28,7 @@ cc_status launch_pair_finalize(cc_plan* plan, const float* raw, const double* Dw
 constexpr int SP_THREADS = 256;
 constexpr size_t TWO_PASS_WS_BUDGET = (size_t)24 << 30;   // a_r, b_r of one template batch
 
-struct SegPairLayout {
-    int mmax;           // largest transform position of any bin
-    int n_chunks;       // segment chunks per (template, weight, coset)
-    int grouped;        // L <= 2048: transforms per CTA, min(4096 / L, 2 C) (segpair_grouped_kernel)
-    int pad_;
-    int64_t chunk_len;  // segments per chunk
-    size_t off_fft;     // [G][2][padded L] float2: out-of-place transform buffers (G = 1 for L = 4096)
-    size_t off_h;       // [G][mmax + 1] float2: detector 0's kept outputs (thread-private slots)
-    size_t bytes;
-};
+
 
 // grid: x = coset c, y = weight w * n_chunks + chunk, z = template within the batch.
 // ab: [n_t][Q][2][N_tau] complex64 (bf16 pairs with BF16 storage), norm: [n_t][Q][M] (hat-A, hat-B, hat-C, 0),
@@ -408,7 +398,8 @@ bool segpair_layout(const cc_plan* plan, int64_t n_t, SegPairLayout* lay) {
     const int64_t waves = plan->tuning.chunk_waves > 0 ? plan->tuning.chunk_waves : 40;
     const int64_t want = std::max<int64_t>(1, (waves * per_sm * 152 + ctas - 1) / std::max<int64_t>(ctas, 1));
     const int64_t maxch = std::max<int64_t>(1, p.M / (4 * p.R + 1));
-    const int64_t nch = std::min<int64_t>({want, maxch, 32767});
+    const int64_t nch = segpair_tma_supported(plan) ? segpair_tma_chunks(plan, n_t)
+                                                    : std::min<int64_t>({want, maxch, 32767});
     lay->chunk_len = (p.M + nch - 1) / nch;
     lay->n_chunks = (int)((p.M + lay->chunk_len - 1) / lay->chunk_len);
     return true;
@@ -486,7 +477,7 @@ static void two_pass_batch(const cc_plan* plan, int64_t n_t, const SegPairLayout
     *batch = b;
     *bytes = al256(per_ab * b) + al256((size_t)plan->Q * plan->M * sizeof(float4) * b) +
              al256((size_t)b * sizeof(double)) + al256((size_t)b * 2 * lay.n_chunks * plan->N_f * sizeof(float)) +
-             al256((size_t)b * plan->Q * knot_rows(plan) * sizeof(KnotRec));
+             al256((size_t)b * plan->Q * knot_rows(plan) * sizeof(KnotRec)) + al256((size_t)plan->C * sizeof(int));
 }
 
 bool two_pass_supported(const cc_plan* plan) {
@@ -523,7 +514,10 @@ cc_status search_two_pass(cc_plan* plan, const cc_template* t_dev, int64_t n_t, 
     float* raw = (float*)w;
     w += al256((size_t)batch * 2 * lay.n_chunks * plan->N_f * sizeof(float));
     KnotRec* kn = (KnotRec*)w;
+    w += al256((size_t)batch * plan->Q * knot_rows(plan) * sizeof(KnotRec));
+    int* counters = (int*)w;   // unit counters of the persistent kernel
     const int64_t nkn = knot_rows(plan);
+    const bool tma = segpair_tma_supported(plan);
     const DevParams& p = plan->dp;
     for (int64_t t0 = 0; t0 < n_t; t0 += batch) {
         const int64_t nb = std::min(batch, n_t - t0);
@@ -536,10 +530,16 @@ cc_status search_two_pass(cc_plan* plan, const cc_template* t_dev, int64_t n_t, 
         cudaEvent_t ev0, ev1;
         timing_pair(plan, &ev0, &ev1);
         if (ev0) cudaEventRecord(ev0, st);
-        cudaError_t e = launch_segpair(p, lb, nb, ab, (const float4*)nrm, raw, st);
-        count_launch();
-        if (ev1) cudaEventRecord(ev1, st);
-        if (e != cudaSuccess) return cuda_fail(e, "segpair launch");
+        if (tma) {
+            s = launch_segpair_tma(plan, lb, nb, ab, (const float4*)nrm, raw, counters, st);
+            if (ev1) cudaEventRecord(ev1, st);
+            if (s != CC_OK) return s;
+        } else {
+            cudaError_t e = launch_segpair(p, lb, nb, ab, (const float4*)nrm, raw, st);
+            count_launch();
+            if (ev1) cudaEventRecord(ev1, st);
+            if (e != cudaSuccess) return cuda_fail(e, "segpair launch");
+        }
         if ((s = launch_pair_finalize(plan, raw, D, 2 * lb.n_chunks, nb, rho + t0 * plan->N_f, st)) != CC_OK)
             return s;
     }

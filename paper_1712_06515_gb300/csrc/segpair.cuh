@@ -1,0 +1,28 @@
+// Shared declarations of the two-pass search's spectrum + pair-sum kernels (segpair.cu,
+// segpair_tma.cu).
+#pragma once
+
+#include "common.cuh"
+#include "fft_reg.cuh"
+
+namespace cc {
+
+struct SegPairLayout {
+    int mmax;           // largest transform position of any bin
+    int n_chunks;       // segment chunks per (template, weight, coset)
+    int grouped;        // L <= 2048: transforms per CTA, min(4096 / L, 2 C) (segpair_grouped_kernel)
+    int pad_;
+    int64_t chunk_len;  // segments per chunk
+    size_t off_fft;     // [G][2][padded L] float2: out-of-place transform buffers (G = 1 for L = 4096)
+    size_t off_h;       // [G][mmax + 1] float2: detector 0's kept outputs (thread-private slots)
+    size_t bytes;
+};
+
+// The persistent, TMA-staged kernel for coset length 4096 (segpair_tma.cu): whether the
+// plan fits it, and one launch over a template batch of the two-pass path.
+bool segpair_tma_supported(const cc_plan* plan);
+int segpair_tma_chunks(const cc_plan* plan, int64_t n_t);
+cc_status launch_segpair_tma(cc_plan* plan, const SegPairLayout& lay, int64_t n_t, const void* ab,
+                             const float4* norm, float* raw, int* counters, cudaStream_t st);
+
+}  // namespace cc

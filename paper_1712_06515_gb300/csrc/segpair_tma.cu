@@ -1,0 +1,408 @@
+// Spectrum + pair-sum kernel of the two-pass search for coset length L = 4096 (the
+// 120-day single band: N_FFT = 32768 = 8 cosets of 4096, N_s = 3600 samples per
+// segment): a persistent kernel whose segment samples arrive by TMA bulk copies.
+//
+// Per (template, weight, chunk of segments, coset) unit a CTA walks the chunk's
+// segments; per segment it transforms detector 0's and detector 1's samples (each the
+// zero-padded N_FFT-point DFT restricted to coset c, Sec. III B 4: an L-point transform
+// of the samples times exp(-2 pi i (b0 + c) s / N_FFT)) and folds the two spectra into
+// the pair sum of Eq. final-formatted-rho, as segpair_kernel does.  What differs:
+//
+//   * staging: the N_s samples of the next (detector, segment) transform are copied
+//     from HBM/L2 into shared memory by one cp.async.bulk (TMA, completion on an
+//     mbarrier) issued as soon as the current transform's first pass has read the stage,
+//     so the copy runs under the current transform's second and third passes instead of
+//     stalling the first pass on global loads;
+//   * scheduling: one CTA per SM slot (persistent), units handed out by a per-coset
+//     atomic counter; a CTA starts on the coset smid mod C, so the CTAs sharing an SM
+//     work on one coset and its 28.8 KB twiddle row stays in L1, and takes units of
+//     other cosets once its own queue is empty (results never depend on placement);
+//   * the second pass takes its 15 twiddles from a 16 x 16 table instead of forming 11
+//     of them by products, and the last pass computes only the 8 outputs m < L/2 that
+//     hold output bins.
+//
+// Waits on the mbarrier are bounded (about one second of clock): a wait that runs out
+// sets bit 0 of the plan's device error word, every thread of the CTA agrees on it at
+// the next barrier, the CTA waits (bounded again) for the copy still in flight and
+// returns; crosscorr_plan_check reports CC_ERR_TIMEOUT.
+#include <algorithm>
+
+#include "segpair.cuh"
+
+namespace cc {
+
+namespace {
+
+constexpr int TT_THREADS = 256;
+constexpr int TT_L = 4096;
+constexpr long long WAIT_LIMIT_CYCLES = 2000000000LL;   // ~1 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity; false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > WAIT_LIMIT_CYCLES) return false;
+    return true;
+}
+
+// 1-D bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16),
+// completing `bytes` transactions on the mbarrier.
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ unsigned sm_id() {
+    unsigned id;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(id));
+    return id;
+}
+
+struct TmaWork {
+    int mmax;
+    int n_chunks;
+    int64_t chunk_len;
+    int64_t units;        // (template, weight, chunk) units per coset
+    uint32_t off_y, off_z, off_h, off_stage, off_bar;
+    uint32_t stage_bytes;   // N_s samples of one (detector, weight, segment) row
+};
+
+// ab: [n_t][Q][2][N_tau] complex64 (bf16 pairs with BF16 storage), norm: [n_t][Q][M]
+// (hat-A, hat-B, hat-C, 0), raw: [n_t][2 * n_chunks][N_f] partial pair sums, counters:
+// [C] unit counters (zero at launch).
+template <bool BF16>
+__global__ void __launch_bounds__(TT_THREADS, 2)
+segpair_tma_kernel(DevParams p, TmaWork q, const void* __restrict__ ab, const float4* __restrict__ norm,
+                   float* __restrict__ raw, int* __restrict__ counters) {
+    extern __shared__ __align__(128) unsigned char sm[];
+    constexpr int L = TT_L;
+    constexpr int NSL = 256;    // butterflies of each pass = threads
+    constexpr int SLP = 8;      // kept outputs per thread: m = tid + 256 r, r < 8 (m < L/2)
+    float2* Y = (float2*)(sm + q.off_y);
+    float2* Z = (float2*)(sm + q.off_z);
+    float2* H = (float2*)(sm + q.off_h);
+    unsigned char* stage = sm + q.off_stage;
+    uint64_t* bar = (uint64_t*)(sm + q.off_bar);
+    __shared__ int s_unit, s_coset;
+
+    const int tid = threadIdx.x, Q = p.Q, C = p.C;
+    const int64_t N_s = p.N_s, R = p.R, M = p.M, N_tau = p.N_tau;
+    const uint64_t N = (uint64_t)p.N_FFT, mask = N - 1;
+    constexpr uint32_t ESZ = BF16 ? 4 : 8;
+
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    int my_c = (int)(sm_id() % (unsigned)C), tries = 0;   // thread 0's queue position
+
+    for (;;) {
+        if (tid == 0) {
+            int u = -1;
+            while (tries < C) {
+                const int v = atomicAdd(counters + my_c, 1);
+                if (v < q.units) {
+                    u = v;
+                    break;
+                }
+                my_c = my_c + 1 == C ? 0 : my_c + 1;   // this coset's queue is empty: help the next
+                ++tries;
+            }
+            s_unit = u;
+            s_coset = my_c;
+        }
+        __syncthreads();
+        const int u = s_unit, c = s_coset;
+        if (u < 0) break;
+        const int64_t t = u / (2 * q.n_chunks);
+        const int rem = u % (2 * q.n_chunks), w = rem / q.n_chunks, chunk = rem % q.n_chunks;
+        const int64_t Ka = (int64_t)chunk * q.chunk_len;
+        const int64_t Kb = imin64(M, Ka + q.chunk_len);
+        const int64_t Kl = imax64(0, Ka - R);
+        const uint64_t bc = ((uint64_t)p.b0 + (uint64_t)c) & mask;
+        const float2* __restrict__ twr = p.twc + (size_t)c * N_s;
+        const float4* __restrict__ nt = norm + (size_t)t * Q * M;
+        // element offset of (template t, detector X, weight w) row
+        const size_t abt = (size_t)t * Q * 2 * N_tau + (size_t)w * N_tau;
+        auto active = [&](int64_t K, int X) {
+            const float4 n = nt[(size_t)X * M + K];
+            return n.x + n.y > 0.f;
+        };
+        // the transform after (K, X) in unit order (detector 0, then detector Q-1, of each
+        // segment; inactive ones skipped); X = -1 starts at segment K
+        auto next_after = [&](int64_t K, int X, int64_t& nK, int& nX) -> bool {
+            if (X == 0 && Q > 1 && active(K, Q - 1)) {
+                nK = K;
+                nX = Q - 1;
+                return true;
+            }
+            for (int64_t k = X < 0 ? K : K + 1; k < Kb; ++k) {
+                if (Q > 1 && active(k, 0)) {
+                    nK = k;
+                    nX = 0;
+                    return true;
+                }
+                if (active(k, Q - 1)) {
+                    nK = k;
+                    nX = Q - 1;
+                    return true;
+                }
+            }
+            return false;
+        };
+        auto issue = [&](int64_t K, int X) {   // thread 0, after a barrier that ends every read of the stage
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            const char* src = (const char*)ab + (abt + (size_t)X * 2 * N_tau + (size_t)(K * N_s)) * ESZ;
+            mbar_arrive_expect_tx(bar, q.stage_bytes);
+            tma_load_1d(stage, src, q.stage_bytes, bar);
+        };
+
+        float accP[SLP], cmpP[SLP];
+        float2 prevP[SLP];
+#pragma unroll
+        for (int r = 0; r < SLP; ++r) {
+            accP[r] = cmpP[r] = 0.f;
+            prevP[r] = make_float2(0.f, 0.f);
+        }
+        int64_t sK = 0;   // staged transform (sK, sX)
+        int sX = 0;
+        bool staged = next_after(Kl, -1, sK, sX);
+        if (staged && tid == 0) issue(sK, sX);
+
+        for (int64_t K = Kl; K < Kb; ++K) {
+            const int64_t seg0 = K * N_s;
+            const float2 wseg = twiddle_N((bc * ((uint64_t)seg0 & mask)) & mask, N);
+            const bool a0 = active(K, 0), al = active(K, Q - 1);
+            float2 v[16];
+#pragma unroll 1
+            for (int pass = 0; pass < 2; ++pass) {
+                const int X = pass == 0 ? 0 : Q - 1;
+                if (pass == 0 ? !(Q > 1 && a0) : !al) continue;
+                // (K, X) is the staged transform
+                const bool ok = mbar_wait(bar, phase);
+                phase ^= 1;
+                // first radix-16 pass: sample s = (tid + 256 r + offn) mod L of the segment
+                // (absolute index: the segment-start phase is part of the transform) times
+                // the coset twiddle
+                {
+                    const int offn = (int)((-seg0) & (int64_t)(L - 1));
+                    float2 x[16], tw[16];
+#pragma unroll
+                    for (int r = 0; r < 16; ++r) {
+                        const int s = (tid + r * 256 + offn) & (L - 1);
+                        const bool in = s < (int)N_s;
+                        if constexpr (BF16)
+                            x[r] = in ? __bfloat1622float2(((const __nv_bfloat162*)stage)[s]) : make_float2(0.f, 0.f);
+                        else
+                            x[r] = in ? ((const float2*)stage)[s] : make_float2(0.f, 0.f);
+                        tw[r] = in ? __ldg(twr + s) : make_float2(0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int r = 0; r < 16; ++r) v[r] = cmul(x[r], tw[r]);
+                    dft16(v);
+                    float2* d = Y + 17 * tid;   // padi(16 tid + r)
+#pragma unroll
+                    for (int r = 0; r < 16; ++r) d[r] = v[r];
+                }
+                int64_t nK = 0;
+                int nX = 0;
+                const bool more = next_after(K, X, nK, nX);
+                // every thread has read the stage and written Y; all agree on a failed wait
+                if (__syncthreads_or(!ok)) {
+                    if (tid == 0) {
+                        atomicOr(p.err, 1u);
+                        mbar_wait(bar, phase ^ 1);   // the copy still in flight, bounded
+                    }
+                    __syncthreads();
+                    return;
+                }
+                if (more && tid == 0) issue(nK, nX);
+                // second pass (NS = 16): Y -> Z, twiddles W_L^(16 k r) from the table
+                {
+                    const int k = tid & 15;
+                    const float2* s = Y + padi(tid);
+#pragma unroll
+                    for (int r = 0; r < 16; ++r) v[r] = s[r * pstride<256>()];
+#pragma unroll
+                    for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], __ldg(p.tw2 + r * 16 + k));
+                    dft16(v);
+                    float2* d = Z + padi((tid - k) * 16 + k);
+#pragma unroll
+                    for (int r = 0; r < 16; ++r) d[r * pstride<16>()] = v[r];
+                }
+                __syncthreads();
+                // last pass (NS = 256) into registers: v[r] = X[tid + 256 r], r < 8
+                {
+                    const float2* s = Z + padi(tid);
+#pragma unroll
+                    for (int r = 0; r < 16; ++r) v[r] = s[r * pstride<256>()];
+                    apply_twiddles<16>(v, p.twL, tid, L - 1);
+                    dft16_lo8(v);
+                }
+                if (pass == 0) {
+#pragma unroll
+                    for (int r = 0; r < SLP; ++r)
+                        if (tid + NSL * r <= q.mmax) H[r * NSL + tid] = v[r];   // read back by this thread only
+                }
+            }
+            // pair terms of segment K (F = 0 for a detector with no weight in it)
+            const float2 wc = make_float2(wseg.x, -wseg.y);
+            const bool acc_on = K >= Ka;
+#pragma unroll
+            for (int r = 0; r < SLP; ++r) {
+                const int m = tid + NSL * r;
+                if (m <= q.mmax) {
+                    const float2 Fl = al ? v[r] : make_float2(0.f, 0.f);
+                    float2 F0 = Fl, F1 = make_float2(0.f, 0.f);
+                    if (Q > 1) {
+                        F0 = a0 ? H[r * NSL + tid] : make_float2(0.f, 0.f);
+                        F1 = Fl;
+                    }
+                    const float2 S = cadd(F0, F1);
+                    const float2 P = R > 0 ? cmul(prevP[r], wc) : make_float2(0.f, 0.f);
+                    const float term = p.pair_mode == CC_PAIRS_ALL_ORDERED ? fmaf(2.f, redot(S, P), redot(S, S))
+                                                                           : redot(S, P) + redot(F1, F0);
+                    if (acc_on) kahan_add(accP[r], cmpP[r], term);
+                    if (R > 0) prevP[r] = cmul(S, wseg);
+                }
+            }
+        }
+        // partial sums of this (template, weight, chunk) row for the coset's bins, staged
+        // through Y (the last transform's reads of Y ended before its second barrier)
+        __syncthreads();
+        float* accm = (float*)Y;
+#pragma unroll
+        for (int r = 0; r < SLP; ++r)
+            if (tid + NSL * r <= q.mmax) accm[tid + NSL * r] = accP[r];
+        __syncthreads();
+        const int o = __ldg(p.coset_off + c), nbc = __ldg(p.coset_off + c + 1) - o;
+        float* outp = raw + ((size_t)t * 2 * q.n_chunks + (size_t)w * q.n_chunks + chunk) * p.N_f;
+        for (int i = tid; i < nbc; i += TT_THREADS) outp[__ldg(p.coset_k + o + i)] = accm[__ldg(p.coset_m + o + i)];
+        // the next unit's first pass rewrites Y: the unit fetch's barrier orders it
+    }
+}
+
+size_t al128(size_t b) { return (b + 127) & ~(size_t)127; }
+
+bool tma_layout(const cc_plan* plan, TmaWork* q, size_t* bytes) {
+    const DevParams& p = plan->dp;
+    const int esz = p.store == CC_STORE_BF16 ? 4 : 8;
+    q->mmax = (int)((plan->kbar.back() - plan->k0) / p.C);
+    q->stage_bytes = (uint32_t)(p.N_s * esz);
+    size_t o = 0;
+    q->off_stage = (uint32_t)o;
+    o = al128(o + q->stage_bytes);
+    q->off_y = (uint32_t)o;
+    o = al128(o + (size_t)padded_len(TT_L) * sizeof(float2));
+    q->off_z = (uint32_t)o;
+    o = al128(o + (size_t)padded_len(TT_L) * sizeof(float2));
+    q->off_h = (uint32_t)o;
+    o = al128(o + (size_t)(q->mmax + 1) * sizeof(float2));
+    q->off_bar = (uint32_t)o;
+    o += 16;
+    *bytes = o;
+    return o <= 113 * 1024;   // two CTAs per SM
+}
+
+template <bool BF16>
+int occupancy(size_t smem) {
+    int n = 0;
+    if (cudaFuncSetAttribute(segpair_tma_kernel<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, segpair_tma_kernel<BF16>, TT_THREADS, smem) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+}  // namespace
+
+// Coset length 4096 with whole segments (N_s <= 4096), Q <= 2, R <= 1, the output bins
+// in the lower half of each coset transform, and rows that start on 16-byte boundaries
+// (the bulk copies): N_s and N_tau even (FP32) or multiples of 4 (BF16).
+bool segpair_tma_supported(const cc_plan* plan) {
+    const DevParams& p = plan->dp;
+    if (p.L != TT_L || p.N_s > TT_L || p.Q > 2 || p.R > 1 || p.pair_mode == CC_PAIRS_CROSS_ONLY || plan->N_f < 1)
+        return false;
+    const int64_t al = p.store == CC_STORE_BF16 ? 4 : 2;
+    if (p.N_s % al || p.N_tau % al) return false;
+    TmaWork q;
+    size_t bytes;
+    if (!tma_layout(plan, &q, &bytes)) return false;
+    return 2 * q.mmax < TT_L;
+}
+
+// Segment chunks per (template, weight) for a batch of n_t templates: about
+// `units per CTA` (the tuning's chunk_waves, default 24) units per persistent CTA, each
+// chunk at least 4R + 1 segments.
+int segpair_tma_chunks(const cc_plan* plan, int64_t n_t) {
+    const DevParams& p = plan->dp;
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t per_cta = plan->tuning.chunk_waves > 0 ? plan->tuning.chunk_waves : 24;
+    const int64_t ctas_per_coset = std::max<int64_t>(1, 2 * (int64_t)sms / p.C);
+    const int64_t want = (per_cta * ctas_per_coset + 2 * n_t - 1) / (2 * n_t);
+    const int64_t maxch = std::max<int64_t>(1, p.M / (4 * p.R + 1));
+    return (int)std::max<int64_t>(1, std::min<int64_t>({want, maxch, 32767}));
+}
+
+cc_status launch_segpair_tma(cc_plan* plan, const SegPairLayout& lay, int64_t n_t, const void* ab,
+                             const float4* norm, float* raw, int* counters, cudaStream_t st) {
+    const DevParams& p = plan->dp;
+    TmaWork q;
+    size_t bytes;
+    if (!tma_layout(plan, &q, &bytes)) return fail(CC_ERR_UNSUPPORTED, "segpair_tma layout");
+    q.n_chunks = lay.n_chunks;
+    q.chunk_len = lay.chunk_len;
+    q.units = n_t * 2 * lay.n_chunks;
+    if (q.units > 0x7fffffff) return fail(CC_ERR_UNSUPPORTED, "too many work units in one launch");
+    const bool bf16 = p.store == CC_STORE_BF16;
+    const int occ = bf16 ? occupancy<true>(bytes) : occupancy<false>(bytes);
+    if (occ < 1) return fail(CC_ERR_UNSUPPORTED, "segpair_tma kernel does not fit an SM");
+    int dev = 0, sms = 152;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "device attributes");
+    const int64_t grid = std::min<int64_t>((int64_t)occ * sms, q.units * p.C);
+    if ((e = cudaMemsetAsync(counters, 0, sizeof(int) * p.C, st)) != cudaSuccess)
+        return cuda_fail(e, "unit counters");
+    if (bf16)
+        segpair_tma_kernel<true><<<(unsigned)grid, TT_THREADS, bytes, st>>>(p, q, ab, norm, raw, counters);
+    else
+        segpair_tma_kernel<false><<<(unsigned)grid, TT_THREADS, bytes, st>>>(p, q, ab, norm, raw, counters);
+    count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "segpair_tma launch");
+    return CC_OK;
+}
+
+}  // namespace cc

@@ -178,6 +178,11 @@ extern "C" cc_status crosscorr_rho_topk(cc_plan* plan, const float* rho_dev, int
     if (e == cudaSuccess) e = cudaMemcpyAsync(hi.data(), fi, sizeof(long long) * KP, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "topk copy");
+    // the stream is synchronised: report a failed bounded wait of the searches before it
+    unsigned err_word = 0;
+    e = cudaMemcpy(&err_word, plan->dp.err, sizeof(err_word), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the device error word");
+    if (err_word) return crosscorr_plan_check(plan, stream);
     const int nk = (int)std::min<long long>(k, n);
     for (int i = 0; i < nk; ++i) {
         cc_hit h;
