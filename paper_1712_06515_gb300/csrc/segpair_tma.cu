@@ -17,9 +17,16 @@
 //     atomic counter; a CTA starts on the coset smid mod C, so the CTAs sharing an SM
 //     work on one coset and its 28.8 KB twiddle row stays in L1, and takes units of
 //     other cosets once its own queue is empty (results never depend on placement);
-//   * the second pass takes its 15 twiddles from a 16 x 16 table instead of forming 11
-//     of them by products, and the last pass computes only the 8 outputs m < L/2 that
-//     hold output bins.
+//   * segment-relative positions: sample s of a segment sits at transform position s
+//     (no wrap), so its transform T_K(m) = sum_s x_s W_N^((b0+c) s) W_L^(m s) lacks the
+//     segment-start phase W_N^(k seg0_K) of bin k = b0 + c + C m.  In a pair of
+//     consecutive segments that phase leaves theta(m) = W_N^(-k N_s), one constant per
+//     bin: Re(conj(F_K) F_(K-1)) = Re(conj(T_K) T_(K-1) theta(m)), and the same-segment
+//     terms carry no phase.  With N_s a multiple of 16, theta(m + 256) = theta(m), so each
+//     thread needs one theta for its eight bins m = tid + 256 r;
+//   * the second pass takes its 15 twiddles from a 16 x 16 table, the last pass's four
+//     base twiddles (which depend only on the thread) are loaded once, and the last pass
+//     computes only the 8 outputs m < L/2 that hold output bins.
 //
 // Waits on the mbarrier are bounded (about one second of clock): a wait that runs out
 // sets bit 0 of the plan's device error word, every thread of the CTA agrees on it at
@@ -124,6 +131,9 @@ segpair_tma_kernel(DevParams p, TmaWork q, const void* __restrict__ ab, const fl
     __syncthreads();
     uint32_t phase = 0;
     int my_c = (int)(sm_id() % (unsigned)C), tries = 0;   // thread 0's queue position
+    // last pass (NS = 256): thread tid's twiddles are W_L^(tid r), formed from these four
+    const float2 b1 = __ldg(p.twL + tid), b2 = __ldg(p.twL + ((2 * tid) & (L - 1)));
+    const float2 b4 = __ldg(p.twL + ((4 * tid) & (L - 1))), b8 = __ldg(p.twL + ((8 * tid) & (L - 1)));
 
     for (;;) {
         if (tid == 0) {
@@ -150,6 +160,8 @@ segpair_tma_kernel(DevParams p, TmaWork q, const void* __restrict__ ab, const fl
         const int64_t Kl = imax64(0, Ka - R);
         const uint64_t bc = ((uint64_t)p.b0 + (uint64_t)c) & mask;
         const float2* __restrict__ twr = p.twc + (size_t)c * N_s;
+        // pair phase of this thread's bins: theta = W_N^(-(bc + C tid) N_s)
+        const float2 theta = twiddle_N((N - ((bc + (uint64_t)C * tid) * (uint64_t)N_s & mask)) & mask, N);
         const float4* __restrict__ nt = norm + (size_t)t * Q * M;
         // element offset of (template t, detector X, weight w) row
         const size_t abt = (size_t)t * Q * 2 * N_tau + (size_t)w * N_tau;
@@ -199,8 +211,6 @@ segpair_tma_kernel(DevParams p, TmaWork q, const void* __restrict__ ab, const fl
         if (staged && tid == 0) issue(sK, sX);
 
         for (int64_t K = Kl; K < Kb; ++K) {
-            const int64_t seg0 = K * N_s;
-            const float2 wseg = twiddle_N((bc * ((uint64_t)seg0 & mask)) & mask, N);
             const bool a0 = active(K, 0), al = active(K, Q - 1);
             float2 v[16];
 #pragma unroll 1
@@ -210,15 +220,13 @@ segpair_tma_kernel(DevParams p, TmaWork q, const void* __restrict__ ab, const fl
                 // (K, X) is the staged transform
                 const bool ok = mbar_wait(bar, phase);
                 phase ^= 1;
-                // first radix-16 pass: sample s = (tid + 256 r + offn) mod L of the segment
-                // (absolute index: the segment-start phase is part of the transform) times
-                // the coset twiddle
+                // first radix-16 pass: sample s = tid + 256 r of the segment (zero beyond
+                // N_s) times the coset twiddle
                 {
-                    const int offn = (int)((-seg0) & (int64_t)(L - 1));
                     float2 x[16], tw[16];
 #pragma unroll
                     for (int r = 0; r < 16; ++r) {
-                        const int s = (tid + r * 256 + offn) & (L - 1);
+                        const int s = tid + r * 256;
                         const bool in = s < (int)N_s;
                         if constexpr (BF16)
                             x[r] = in ? __bfloat1622float2(((const __nv_bfloat162*)stage)[s]) : make_float2(0.f, 0.f);
@@ -265,7 +273,23 @@ segpair_tma_kernel(DevParams p, TmaWork q, const void* __restrict__ ab, const fl
                     const float2* s = Z + padi(tid);
 #pragma unroll
                     for (int r = 0; r < 16; ++r) v[r] = s[r * pstride<256>()];
-                    apply_twiddles<16>(v, p.twL, tid, L - 1);
+                    const float2 b3 = cmul(b2, b1);
+                    v[1] = cmul(v[1], b1);
+                    v[2] = cmul(v[2], b2);
+                    v[3] = cmul(v[3], b3);
+                    v[4] = cmul(v[4], b4);
+                    v[5] = cmul(v[5], cmul(b4, b1));
+                    v[6] = cmul(v[6], cmul(b4, b2));
+                    v[7] = cmul(v[7], cmul(b4, b3));
+                    v[8] = cmul(v[8], b8);
+                    v[9] = cmul(v[9], cmul(b8, b1));
+                    v[10] = cmul(v[10], cmul(b8, b2));
+                    v[11] = cmul(v[11], cmul(b8, b3));
+                    const float2 b12 = cmul(b8, b4);
+                    v[12] = cmul(v[12], b12);
+                    v[13] = cmul(v[13], cmul(b12, b1));
+                    v[14] = cmul(v[14], cmul(b12, b2));
+                    v[15] = cmul(v[15], cmul(b12, b3));
                     dft16_lo8(v);
                 }
                 if (pass == 0) {
@@ -274,8 +298,8 @@ segpair_tma_kernel(DevParams p, TmaWork q, const void* __restrict__ ab, const fl
                         if (tid + NSL * r <= q.mmax) H[r * NSL + tid] = v[r];   // read back by this thread only
                 }
             }
-            // pair terms of segment K (F = 0 for a detector with no weight in it)
-            const float2 wc = make_float2(wseg.x, -wseg.y);
+            // pair terms of segment K (F = 0 for a detector with no weight in it); prevP
+            // holds the previous segment's detector sum times theta
             const bool acc_on = K >= Ka;
 #pragma unroll
             for (int r = 0; r < SLP; ++r) {
@@ -288,11 +312,11 @@ segpair_tma_kernel(DevParams p, TmaWork q, const void* __restrict__ ab, const fl
                         F1 = Fl;
                     }
                     const float2 S = cadd(F0, F1);
-                    const float2 P = R > 0 ? cmul(prevP[r], wc) : make_float2(0.f, 0.f);
+                    const float2 P = R > 0 ? prevP[r] : make_float2(0.f, 0.f);
                     const float term = p.pair_mode == CC_PAIRS_ALL_ORDERED ? fmaf(2.f, redot(S, P), redot(S, S))
                                                                            : redot(S, P) + redot(F1, F0);
                     if (acc_on) kahan_add(accP[r], cmpP[r], term);
-                    if (R > 0) prevP[r] = cmul(S, wseg);
+                    if (R > 0) prevP[r] = cmul(S, theta);
                 }
             }
         }
@@ -346,15 +370,15 @@ int occupancy(size_t smem) {
 
 }  // namespace
 
-// Coset length 4096 with whole segments (N_s <= 4096), Q <= 2, R <= 1, the output bins
-// in the lower half of each coset transform, and rows that start on 16-byte boundaries
-// (the bulk copies): N_s and N_tau even (FP32) or multiples of 4 (BF16).
+// Coset length 4096 with whole segments (N_s <= 4096) of a multiple of 16 samples (rows
+// then start on 16-byte boundaries for the bulk copies, and the pair phase repeats every
+// 256 bins), Q <= 2, R <= 1, the output bins in the lower half of each coset transform.
 bool segpair_tma_supported(const cc_plan* plan) {
     const DevParams& p = plan->dp;
     if (p.L != TT_L || p.N_s > TT_L || p.Q > 2 || p.R > 1 || p.pair_mode == CC_PAIRS_CROSS_ONLY || plan->N_f < 1)
         return false;
-    const int64_t al = p.store == CC_STORE_BF16 ? 4 : 2;
-    if (p.N_s % al || p.N_tau % al) return false;
+    // N_s a multiple of 16: one pair phase per thread (and 16-byte aligned rows)
+    if (p.N_s % 16) return false;
     TmaWork q;
     size_t bytes;
     if (!tma_layout(plan, &q, &bytes)) return false;
