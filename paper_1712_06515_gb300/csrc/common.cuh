@@ -70,7 +70,7 @@ struct DevParams {
     const int* coset_m;              // [N_f] position in the coset's L-point transform
     const float2* twL;               // exp(-2 pi i j / L), j < L
     const float2* twc;               // [C][N_s]: exp(-2 pi i ((b0 + c) s mod N_FFT) / N_FFT)
-    const float2* tw2;               // [16][16]: exp(-2 pi i (L/256) k r / L), second radix-16 pass
+    const float2* twk;               // [C][272]: coset twiddles of the 4096-point kernel's passes (plan.cu)
     unsigned* err;                   // device error word: bit 0 set by a kernel whose bounded wait ran out
     const float* ltaps;              // [LEARNED_NODES][LEARNED_TAPS] learned taps (null until set)
     float ham[MAX_TAPS];             // Hamming window, 2D+1 taps

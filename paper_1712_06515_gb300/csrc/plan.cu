@@ -375,15 +375,6 @@ cc_status crosscorr_plan(const cc_config* cfg, const cc_detector* dets, cc_plan*
         double ang = -2.0 * M_PI * (double)j / (double)L;
         tw[j] = make_float2((float)cos(ang), (float)sin(ang));
     }
-    // second radix-16 pass of an L-point transform (Stockham, 16 butterfly classes k):
-    // tw2[r][k] = exp(-2 pi i (L / 256) k r / L), r, k < 16
-    std::vector<float2> tw2(256);
-    for (int64_t r = 0; r < 16; ++r)
-        for (int64_t k = 0; k < 16; ++k) {
-            const int64_t j = ((L / 256) * k * r) % L;
-            const double ang = -2.0 * M_PI * (double)j / (double)L;
-            tw2[r * 16 + k] = make_float2((float)cos(ang), (float)sin(ang));
-        }
     const unsigned zero_word = 0;
     p->coset_off = off;
     // per-coset twiddles of the segment-local sample index (FP64 phase, exact integer index)
@@ -397,13 +388,35 @@ cc_status crosscorr_plan(const cc_config* cfg, const cc_detector* dets, cc_plan*
             twc[(size_t)c2 * p->N_s + r] = make_float2((float)cos(ang), (float)sin(ang));
         }
     }
+    // Coset twiddles of the radix-16 passes of the persistent 4096-point kernel, per coset
+    // c (bc = b0 + c): the coset twiddle W_N^(bc s) of sample s = t + 256 r (thread t of
+    // the first pass) splits into W_N^(256 bc r), applied in the first pass, and the
+    // thread factor W_N^(bc t), which passes through the first pass's DFT into the second
+    // pass (element r' of second-pass thread j came from first-pass thread (j >> 4) + 16 r'):
+    // its part W_N^(16 bc r') joins that pass's twiddle W_L^(16 k r') (k = j mod 16), and
+    // its part W_N^(bc (j >> 4)) reaches the last pass as W_N^(bc r3) on element r3.
+    // twk[c][r], r < 16: W_N^(256 bc r); twk[c][16 + 16 r + k]: W_N^(16 r (C k + bc)).
+    std::vector<float2> twk((size_t)C * 272);
+    for (int64_t c2 = 0; c2 < C; ++c2) {
+        const uint64_t bc = (uint64_t)((b0 + c2) % N);
+        for (uint64_t r = 0; r < 16; ++r) {
+            const uint64_t j = (256 * bc * r) % (uint64_t)N;
+            const double ang = -2.0 * M_PI * (double)j / (double)N;
+            twk[(size_t)c2 * 272 + r] = make_float2((float)cos(ang), (float)sin(ang));
+            for (uint64_t k = 0; k < 16; ++k) {
+                const uint64_t j2 = (16 * r * ((uint64_t)C * k + bc)) % (uint64_t)N;
+                const double a2 = -2.0 * M_PI * (double)j2 / (double)N;
+                twk[(size_t)c2 * 272 + 16 + 16 * r + k] = make_float2((float)cos(a2), (float)sin(a2));
+            }
+        }
+    }
     cc_status st;
     if ((st = upload(p, twc.data(), twc.size(), &dp.twc)) != CC_OK ||
         (st = upload(p, off.data(), off.size(), &dp.coset_off)) != CC_OK ||
         (st = upload(p, ck.data(), ck.size(), &dp.coset_k)) != CC_OK ||
         (st = upload(p, cm.data(), cm.size(), &dp.coset_m)) != CC_OK ||
         (st = upload(p, tw.data(), tw.size(), &dp.twL)) != CC_OK ||
-        (st = upload(p, tw2.data(), tw2.size(), &dp.tw2)) != CC_OK ||
+        (st = upload(p, twk.data(), twk.size(), &dp.twk)) != CC_OK ||
         (st = upload(p, &zero_word, 1, (const unsigned**)&dp.err)) != CC_OK) {
         crosscorr_plan_destroy(p);
         return st;

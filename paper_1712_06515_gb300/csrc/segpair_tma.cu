@@ -24,9 +24,12 @@
 //     bin: Re(conj(F_K) F_(K-1)) = Re(conj(T_K) T_(K-1) theta(m)), and the same-segment
 //     terms carry no phase.  With N_s a multiple of 16, theta(m + 256) = theta(m), so each
 //     thread needs one theta for its eight bins m = tid + 256 r;
-//   * the second pass takes its 15 twiddles from a 16 x 16 table, the last pass's four
-//     base twiddles (which depend only on the thread) are loaded once, and the last pass
-//     computes only the 8 outputs m < L/2 that hold output bins.
+//   * coset twiddles without a per-sample table: the twiddle W_N^((b0+c) s) of sample
+//     s = tid + 256 r splits into a factor per r (16 values per coset, applied in the first
+//     pass) and a factor per thread, which passes through the first pass's DFT and is
+//     absorbed into the second pass's table twiddles and the last pass's base twiddles
+//     (the plan's twk table); the last pass computes only the 8 outputs m < L/2 that hold
+//     output bins.
 //
 // Waits on the mbarrier are bounded (about one second of clock): a wait that runs out
 // sets bit 0 of the plan's device error word, every thread of the CTA agrees on it at
@@ -131,9 +134,6 @@ segpair_tma_kernel(DevParams p, TmaWork q, const void* __restrict__ ab, const fl
     __syncthreads();
     uint32_t phase = 0;
     int my_c = (int)(sm_id() % (unsigned)C), tries = 0;   // thread 0's queue position
-    // last pass (NS = 256): thread tid's twiddles are W_L^(tid r), formed from these four
-    const float2 b1 = __ldg(p.twL + tid), b2 = __ldg(p.twL + ((2 * tid) & (L - 1)));
-    const float2 b4 = __ldg(p.twL + ((4 * tid) & (L - 1))), b8 = __ldg(p.twL + ((8 * tid) & (L - 1)));
 
     for (;;) {
         if (tid == 0) {
@@ -159,9 +159,14 @@ segpair_tma_kernel(DevParams p, TmaWork q, const void* __restrict__ ab, const fl
         const int64_t Kb = imin64(M, Ka + q.chunk_len);
         const int64_t Kl = imax64(0, Ka - R);
         const uint64_t bc = ((uint64_t)p.b0 + (uint64_t)c) & mask;
-        const float2* __restrict__ twr = p.twc + (size_t)c * N_s;
+        const float2* __restrict__ twk = p.twk + (size_t)c * 272;
         // pair phase of this thread's bins: theta = W_N^(-(bc + C tid) N_s)
-        const float2 theta = twiddle_N((N - ((bc + (uint64_t)C * tid) * (uint64_t)N_s & mask)) & mask, N);
+        const uint64_t ct = bc + (uint64_t)C * tid;
+        const float2 theta = twiddle_N((N - (ct * (uint64_t)N_s & mask)) & mask, N);
+        // last pass (NS = 256): element r3 of thread tid takes W_L^(tid r3) W_N^(bc r3) =
+        // W_N^(ct r3), formed from these four powers
+        const float2 b1 = twiddle_N(ct & mask, N), b2 = twiddle_N((2 * ct) & mask, N);
+        const float2 b4 = twiddle_N((4 * ct) & mask, N), b8 = twiddle_N((8 * ct) & mask, N);
         const float4* __restrict__ nt = norm + (size_t)t * Q * M;
         // element offset of (template t, detector X, weight w) row
         const size_t abt = (size_t)t * Q * 2 * N_tau + (size_t)w * N_tau;
@@ -221,21 +226,19 @@ segpair_tma_kernel(DevParams p, TmaWork q, const void* __restrict__ ab, const fl
                 const bool ok = mbar_wait(bar, phase);
                 phase ^= 1;
                 // first radix-16 pass: sample s = tid + 256 r of the segment (zero beyond
-                // N_s) times the coset twiddle
+                // N_s) times the coset factor W_N^(256 bc r)
                 {
-                    float2 x[16], tw[16];
 #pragma unroll
                     for (int r = 0; r < 16; ++r) {
                         const int s = tid + r * 256;
                         const bool in = s < (int)N_s;
                         if constexpr (BF16)
-                            x[r] = in ? __bfloat1622float2(((const __nv_bfloat162*)stage)[s]) : make_float2(0.f, 0.f);
+                            v[r] = in ? __bfloat1622float2(((const __nv_bfloat162*)stage)[s]) : make_float2(0.f, 0.f);
                         else
-                            x[r] = in ? ((const float2*)stage)[s] : make_float2(0.f, 0.f);
-                        tw[r] = in ? __ldg(twr + s) : make_float2(0.f, 0.f);
+                            v[r] = in ? ((const float2*)stage)[s] : make_float2(0.f, 0.f);
                     }
 #pragma unroll
-                    for (int r = 0; r < 16; ++r) v[r] = cmul(x[r], tw[r]);
+                    for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], __ldg(twk + r));
                     dft16(v);
                     float2* d = Y + 17 * tid;   // padi(16 tid + r)
 #pragma unroll
@@ -254,14 +257,15 @@ segpair_tma_kernel(DevParams p, TmaWork q, const void* __restrict__ ab, const fl
                     return;
                 }
                 if (more && tid == 0) issue(nK, nX);
-                // second pass (NS = 16): Y -> Z, twiddles W_L^(16 k r) from the table
+                // second pass (NS = 16): Y -> Z, twiddles W_L^(16 k r) W_N^(16 bc r) from the
+                // table (the thread factor of the first pass's source threads)
                 {
                     const int k = tid & 15;
                     const float2* s = Y + padi(tid);
 #pragma unroll
                     for (int r = 0; r < 16; ++r) v[r] = s[r * pstride<256>()];
 #pragma unroll
-                    for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], __ldg(p.tw2 + r * 16 + k));
+                    for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], __ldg(twk + 16 + r * 16 + k));
                     dft16(v);
                     float2* d = Z + padi((tid - k) * 16 + k);
 #pragma unroll
