@@ -34,13 +34,15 @@ sys.path.insert(0, ROOT)
 METRIC = "CrossCorr rho templates*freq-bins/sec on 1 GB300 (+% HBM roofline) vs plain FP32 at stated rho error"
 UNIT = "template*bins/s"
 GRID_TEMPLATES = 8000
-# DRAM bytes read + written per template by segpair_kernel<4096> on this workload, from
+# DRAM bytes read + written per template by the spectrum kernel of this workload, from
 # an ncu capture of one launch on 8 templates (its summary is kept with the profiles;
 # the reads of a_r, b_r grow with the templates of a launch).  None once the kernel
 # changes.
-SEGPAIR_DRAM_BYTES_PER_TEMPLATE = (1.770469e9 + 74.267904e6) / 8
+SEGPAIR_DRAM_BYTES_PER_TEMPLATE = None
 SM_COUNT = 152
 FP32_LANES = 128
+# days of the 120-day band in the bounded CPU samples (both CPU legs use the same sample)
+CPU_SAMPLE_DAYS = 12.0
 
 
 def parse():
@@ -76,8 +78,10 @@ def parse():
     ap.add_argument("--batch-templates", type=int, default=0,
                     help="work split: templates per two-pass batch (0: library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-days", type=float, default=120.0,
-                    help="days of data in the bounded CPU oracle sample")
+    ap.add_argument("--cpu-days", type=float, default=CPU_SAMPLE_DAYS,
+                    help="days of data in the bounded CPU oracle sample (both CPU legs)")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the variant measurements (stencils, long lag, multi-band) of the default run")
     ap.add_argument("--e2e-steps", type=int, default=1)
     return ap.parse_args()
 
@@ -88,6 +92,30 @@ def load_peaks():
             return json.load(f), "measured"
     except OSError:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_peak(cc, clk):
+    """(peak TFLOP/s, how): the lower of the FP32 FMA throughput measured on this GPU now
+    (the library's full-occupancy FMA-chain kernel) and the derived SM count x 128 FP32
+    lanes x 2 flop x maximum SM clock."""
+    clk_max = float((clk or {}).get("sm_max_mhz") or 2070.0)
+    derived = SM_COUNT * FP32_LANES * 2 * clk_max * 1e6 / 1e12
+    try:
+        measured = cc.measure_fp32_peak()
+    except Exception:   # noqa: BLE001 - reported, the derived figure stands
+        measured = None
+    if measured and measured < derived:
+        return measured, (f"measured: {measured:.2f} TFLOP/s FP32 FMA throughput on this GPU "
+                          f"(derived {derived:.2f}: {SM_COUNT} SMs x {FP32_LANES} lanes x 2 x {clk_max:g} MHz)")
+    return derived, (f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 flop x {clk_max:g} MHz"
+                     + (f" (measured {measured:.2f})" if measured else ""))
+
+
+def spectrum_kernel_name(info):
+    """The two-pass path's spectrum + pair-sum kernel for this plan's geometry."""
+    if info["L"] == 4096 and info["N_s"] <= 4096 and info["N_s"] % 16 == 0 and info["R"] <= 1:
+        return "segpair_tma_kernel"
+    return "segpair_grouped_kernel" if info["L"] <= 2048 else "segpair_kernel"
 
 
 # ---------------------------------------------------------------------------
@@ -142,6 +170,26 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle on a bounded sample
 # ---------------------------------------------------------------------------
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for line in r.stdout.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def cpu_oracle_sample(days, seed=1002):
     """The FP64 oracle, as it stands, on one template over the first `days` of the
     workload; returns (seconds, template*bins processed scaled to the full 120 d)."""
@@ -156,15 +204,26 @@ def cpu_oracle_sample(days, seed=1002):
     return dt, units
 
 
+def cpu_oracle_baseline(days, min_seconds=10.0):
+    """The oracle on the bounded sample, repeated until about min_seconds of CPU work."""
+    tot_t, tot_u, n = 0.0, 0.0, 0
+    while tot_t < min_seconds or n == 0:
+        dt, u = cpu_oracle_sample(days)
+        tot_t += dt
+        tot_u += u
+        n += 1
+    return tot_u / tot_t, tot_t, n
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     for _ in range(args.warmup):
-        cpu_oracle_sample(args.cpu_days / 3.0)
+        cpu_oracle_sample(args.cpu_days)
     tot_t, tot_u = 0.0, 0.0
     for _ in range(args.steps):
-        dt, units = cpu_oracle_sample(args.cpu_days / 3.0)
+        dt, units = cpu_oracle_sample(args.cpu_days)
         tot_t += dt
         tot_u += units
     value = tot_u / tot_t
@@ -174,9 +233,10 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": "o1_band: 2 det, 120 d at 60% duty, 0.5 Hz at 150 Hz, T_max=T_short=3600 s",
-                   "sample": f"1 template x 12356 bins over the first {args.cpu_days / 3.0:g} d, scaled to 120 d"},
+                   "sample": f"1 template x 12356 bins over the first {args.cpu_days:g} d, scaled to 120 d"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"1 template, first {args.cpu_days / 3.0:g} of 120 days, linear in T_obs"},
+                         "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+                         "sample": f"1 template, first {args.cpu_days:g} of 120 days, linear in T_obs"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -331,16 +391,15 @@ def run_gpu(args):
         # the fused path the one-pass kernel (all flops).  Against the FP32-ALU roofline
         # from the SM count, FP32 lanes and the maximum SM clock.
         if path == cc.PATH_TWO_PASS:
-            kname, kflops = "segpair_kernel", costs["fft_flops"] + costs["pair_flops"]
+            kname, kflops = spectrum_kernel_name(info), costs["fft_flops"] + costs["pair_flops"]
         else:
             kname, kflops = "fused_kernel", costs["total_flops"]
         achieved = kflops * B * args.steps / (fused_ms / 1e3) / 1e12
-        clk_max = float((clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0))
-        peak = SM_COUNT * FP32_LANES * 2 * clk_max * 1e6 / 1e12
+        peak, peak_how = fp32_peak(cc, clk)
         other_ms = max(0.0, 1e3 * elapsed - fused_ms) / (B * args.steps)
         traffic = None
         if path == cc.PATH_TWO_PASS and SEGPAIR_DRAM_BYTES_PER_TEMPLATE is not None and fused_launches \
-                and not long_lag:
+                and not long_lag and kname == "segpair_tma_kernel" and not learned and args.pair_mode == "unordered":
             traffic = SEGPAIR_DRAM_BYTES_PER_TEMPLATE * B * args.steps / fused_launches
         # the staged stage kernels are HBM-bound: algorithmic bytes (input read once,
         # output written once) over their event-timed duration, against the measured copy peak
@@ -355,7 +414,7 @@ def run_gpu(args):
         roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                 "traffic_unit": "bytes per launch (ncu capture, scaled by templates per launch)",
-                "peak_kind": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 flop x {clk_max:g} MHz",
+                "peak_kind": peak_how,
                 "flops_per_template": kflops,
                 "kernel_ms_per_launch": fused_ms / max(fused_launches, 1),
                 "kernel_launches": fused_launches, "kernel_share_of_step": fused_ms / (1e3 * elapsed),
@@ -390,15 +449,180 @@ def run_gpu(args):
                     "h2d_bytes_per_step": int(x_host.numel() * 8 + tm_pin.numel() * 8),
                     "d2h_bytes_per_step": int(rho_host.numel() * 4)},
         }
+        if world == 1 and not args.no_variants and args.workload == "o1_band":
+            out["variants"] = run_variants(args, ds, x, tm_host, plan, peak)
         if world == 1 and not args.no_cpu_baseline:
-            dt, u = cpu_oracle_sample(args.cpu_days)
-            out["cpu_baseline"] = {"value": u / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            v, dt, n = cpu_oracle_baseline(args.cpu_days)
+            out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                   "cpu_model": cpu_model(), "nproc": os.cpu_count(),
                                    "sample": f"1 template x {N_f} bins over the first {args.cpu_days:g} "
-                                             f"of 120 days ({dt:.1f} s), scaled linearly to 120 d"}
+                                             f"of 120 days, {n} runs ({dt:.1f} s), scaled linearly to 120 d"}
         print(json.dumps(out), flush=True)
     plan.close()
     if dist:
         dist.destroy_process_group()
+
+
+def _time_search(plan, x, tm, steps, warmup=1):
+    """ms per search of `tm` (CUDA events on the current stream) and the spectrum kernel's
+    share, after `warmup` untimed searches."""
+    import torch
+    stream = torch.cuda.current_stream()
+    rho = torch.empty((tm.shape[0], plan.N_f), dtype=torch.float32, device=x.device)
+    for _ in range(warmup):
+        plan.search(x, tm, rho)
+    plan.kernel_time()
+    plan.set_kernel_timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        plan.search(x, tm, rho)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plan.set_kernel_timing(False)
+    kms, _ = plan.kernel_time()
+    plan.check()
+    return e0.elapsed_time(e1) / steps, kms / steps, rho
+
+
+def variant_stencils(args, ds, x, tm_host, plan, peak):
+    """Learned 8-tap interpolation against the exact 17-tap windowed sinc on the 120-day
+    band: speed on the first 512 templates of the grid, and accuracy on a noiseless
+    injection against the widest exact stencil (D = 32, 65 taps) as the judge."""
+    import torch
+    import synth
+    import paper_1712_06515_gb300 as cc
+    dev = x.device
+    B = min(512, tm_host.shape[0])
+    tm = torch.from_numpy(np.ascontiguousarray(tm_host[:B])).to(dev)
+    res = {"templates": B}
+    with cc.CrossCorrPlan(ds.cfg, ds.dets, interp=cc.INTERP_LEARNED) as lp:
+        for name, pl, learned in (("exact_d8", plan, False), ("learned", lp, True)):
+            ms, kms, _ = _time_search(pl, x, tm, steps=2)
+            kfl = algorithmic_costs(pl.info, pl.Q, 1, ds.cfg.D, learned)
+            res[name] = {"value": B * pl.N_f / (ms / 1e3), "unit": UNIT, "ms_per_template": ms / B,
+                         "other_kernels_ms_per_template": (ms - kms) / B,
+                         "spectrum_frac": (kfl["fft_flops"] + kfl["pair_flops"]) * B / (kms / 1e3) / 1e12 / peak}
+    # accuracy: noiseless injection, the injected template and three grid neighbours
+    dn = synth.o1_band(seed=1002, noise=False)
+    inj = dn.injection
+    ap = np.linspace(1.36, 1.52, 40)
+    ta = inj.T_asc + np.linspace(-300.0, 300.0, 200)
+    pick = np.array([[inj.a_p, inj.T_asc, inj.P], [ap[19], ta[99], inj.P], [ap[20], ta[101], inj.P],
+                     [ap[21], ta[100], inj.P]])
+    tmi = torch.from_numpy(np.ascontiguousarray(np.concatenate([pick, np.zeros((4, 2))], axis=1))).to(dev)
+    xn = torch.from_numpy(dn.x64).to(dev)
+    out = {}
+    for name, D, interp in (("judge_exact_d32", 32, cc.INTERP_EXACT), ("exact_d8", 8, cc.INTERP_EXACT),
+                            ("learned", 8, cc.INTERP_LEARNED)):
+        cfg = dataclass_replace(dn.cfg, D=D)
+        with cc.CrossCorrPlan(cfg, dn.dets, interp=interp) as pl:
+            out[name] = pl.search(xn, tmi).cpu().numpy().astype(np.float64)
+            pl.check()
+    judge = out["judge_exact_d32"]
+    peak_rho = float(np.abs(judge).max())
+    for name in ("exact_d8", "learned"):
+        err = np.abs(out[name] - judge).max(axis=1)
+        res[name]["rho_err_vs_judge"] = float(err.max())
+        res[name]["rel_err_vs_judge"] = float(err.max() / peak_rho)
+        res[name]["argmax_equal"] = bool(np.unravel_index(np.argmax(out[name]), judge.shape)
+                                         == np.unravel_index(np.argmax(judge), judge.shape))
+    res["judge"] = "exact windowed sinc D = 32 (65 taps), noiseless injection, max rho %.2f" % peak_rho
+    res["learned_faster"] = res["learned"]["value"] > res["exact_d8"]["value"]
+    res["learned_at_least_as_accurate"] = res["learned"]["rho_err_vs_judge"] <= res["exact_d8"]["rho_err_vs_judge"]
+    return res
+
+
+def variant_long_lag(args, peak):
+    """The long-lag precision variant: T_max = T_short = 36000 s (N_FFT = 2^18, 123564
+    bins) with BF16 storage of the resampled series, 64 templates of the grid; rho error
+    of BF16 storage against FP32 storage (the FP32 path's own oracle parity is 1e-4)."""
+    import torch
+    import synth
+    import paper_1712_06515_gb300 as cc
+    dev = torch.device("cuda", torch.cuda.current_device())
+    dl = synth.o1_band(seed=1002, T_max=36000.0)
+    B = 64
+    tm = torch.from_numpy(np.ascontiguousarray(np.concatenate([dl.templates[:B], np.zeros((B, 2))], axis=1))).to(dev)
+    x = torch.from_numpy(dl.x64).to(dev)
+    res = {"templates": B}
+    with cc.CrossCorrPlan(dl.cfg, dl.dets, store=cc.STORE_BF16) as pl:
+        ms, kms, _ = _time_search(pl, x, tm, steps=2)
+        kfl = algorithmic_costs(pl.info, pl.Q, 1, dl.cfg.D, False)
+        res.update({"value": B * pl.N_f / (ms / 1e3), "unit": UNIT, "ms_per_template": ms / B,
+                    "kernel": spectrum_kernel_name(pl.info),
+                    "spectrum_frac": (kfl["fft_flops"] + kfl["pair_flops"]) * B / (kms / 1e3) / 1e12 / peak,
+                    "spectrum_share": kms / ms, "N_f": pl.N_f, "N_FFT": pl.info["N_FFT"]})
+        inj = dl.injection
+        two = torch.from_numpy(np.array([[inj.a_p, inj.T_asc, inj.P, 0.0, 0.0],
+                                         [1.52, inj.T_asc + 300.0, inj.P, 0.0, 0.0]])).to(dev)
+        bf = pl.search(x, two).cpu().numpy().astype(np.float64)
+        pl.check()
+    with cc.CrossCorrPlan(dl.cfg, dl.dets, store=cc.STORE_FP32) as pf:
+        f32 = pf.search(x, two).cpu().numpy().astype(np.float64)
+        pf.check()
+    err = np.abs(bf - f32).max(axis=1)
+    lim = np.maximum(1.0, np.abs(f32).max(axis=1))
+    res["rho_err_bf16_vs_fp32"] = [float(e) for e in err]
+    res["rel_err_bf16_vs_fp32"] = [float(e) for e in err / lim]
+    return res
+
+
+def variant_multiband(args, peak, scale=0.05):
+    """The batched multi-band workload at a reduced template scale: one CUDA graph launch
+    per step over 32 bands after per-band autotuning."""
+    import torch
+    import synth
+    import paper_1712_06515_gb300 as cc
+    from paper_1712_06515_gb300.multiband import MultiBandSearch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    datasets = synth.multiband(template_scale=scale)
+    bands = [(d.cfg, d.dets, torch.from_numpy(d.x64).to(dev), torch.from_numpy(d.templates).to(dev))
+             for d in datasets]
+    mb = MultiBandSearch(bands, tune=True, tune_templates=32).capture()
+    stream = torch.cuda.current_stream()
+    mb.run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(2):
+        mb.run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1000.0 / 2
+    flops = sum(algorithmic_costs(p.info, p.Q, tm.shape[0], cfg.D, False)["total_flops"]
+                for p, (cfg, _, _, tm) in zip(mb.plans, bands))
+    res = {"template_scale": scale, "templates": int(sum(t.shape[0] for (_, _, _, t) in bands)),
+           "value": mb.units / sec, "unit": UNIT, "ms_per_step": 1e3 * sec,
+           "graph_frac": flops / sec / 1e12 / peak, "kernels_per_step": mb.kernels_per_run}
+    mb.close()
+    return res
+
+
+def run_variants(args, ds, x, tm_host, plan, peak):
+    """Variants measured after the headline in the same process and under one clock
+    sampler (rank 0, one GPU): learned vs exact stencil, long-lag BF16, multi-band."""
+    import torch
+    res = {}
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    for name, fn in (("stencils", lambda: variant_stencils(args, ds, x, tm_host, plan, peak)),
+                     ("long_lag_bf16", lambda: variant_long_lag(args, peak)),
+                     ("multiband", lambda: variant_multiband(args, peak))):
+        t0 = time.perf_counter()
+        try:
+            res[name] = fn()
+        except Exception as e:   # noqa: BLE001 - a failed variant is reported, the headline stands
+            res[name] = {"error": f"{type(e).__name__}: {e}"}
+        res[name]["wall_s"] = round(time.perf_counter() - t0, 1)
+        torch.cuda.empty_cache()
+    res["clocks"] = clocks.stop()
+    return res
+
+
+def dataclass_replace(cfg, **kw):
+    import dataclasses
+    return dataclasses.replace(cfg, **kw)
 
 
 def run_multiband(args):

@@ -380,6 +380,13 @@ cc_status crosscorr_plan_set_kernel_timing(cc_plan* plan, int on);
  * their number; waits for those launches to finish, then clears the record. */
 cc_status crosscorr_plan_kernel_time(cc_plan* plan, double* ms, int64_t* launches);
 
+/* Diagnostic: the measured FP32 fused-multiply-add throughput of the current device in
+ * TFLOP/s (2 flop per FMA), from a full-occupancy grid of independent FMA chains timed
+ * with CUDA events on `stream` (best of three launches after one warm-up; synchronises
+ * the stream, about 0.1 s).  The spectrum kernels are bound by the plain FP32 pipes and
+ * report their fraction of this figure.  No counterpart in the paper. */
+cc_status crosscorr_measure_fp32_peak(double* tflops, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -91,6 +91,14 @@ def lattice(g, mu: float, lo, hi) -> np.ndarray:
     return out[:, :3].copy()
 
 
+def measure_fp32_peak(stream=None) -> float:
+    """Measured FP32 FMA throughput of the current device in TFLOP/s (diagnostic)."""
+    lib = load()
+    v = c_double()
+    check("crosscorr_measure_fp32_peak", lib.crosscorr_measure_fp32_peak(byref(v), _stream_handle(stream)))
+    return v.value
+
+
 def sfts_to_series(band, block_sft, T_sft: float, f_h: float, stream=None):
     """Heterodyned, downsampled series [n_blocks * N'] (CUDA complex64) from SFT bands
     band [n_sft, N'] (CUDA complex64) and block_sft [n_blocks] (CUDA int64, -1 = gap):

@@ -21,7 +21,7 @@ LIBDIR = os.path.join(PKG, "lib")
 LIBPATH = os.path.join(LIBDIR, "libcrosscorr.so")
 
 SOURCES = ["plan.cu", "stages.cu", "search.cu", "topk.cu", "fused.cu", "fused_l64_256.cu", "fused_l512_1024.cu",
-           "fused_l2048.cu", "fused_l4096.cu", "noalloc.cu", "learned.cu", "segpair.cu", "segpair_tma.cu", "demod.cu", "sftseries.cu", "lattice.cu"]
+           "fused_l2048.cu", "fused_l4096.cu", "noalloc.cu", "learned.cu", "segpair.cu", "segpair_tma.cu", "peak.cu", "demod.cu", "sftseries.cu", "lattice.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 
@@ -146,6 +146,7 @@ SIGNATURES = {
     "crosscorr_plan_search_path": (c_int, [c_void_p, POINTER(c_int)]),
     "crosscorr_plan_kernel_time": (c_int, [c_void_p, POINTER(c_double), POINTER(c_int64)]),
     "crosscorr_plan_check": (c_int, [c_void_p, c_void_p]),
+    "crosscorr_measure_fp32_peak": (c_int, [POINTER(c_double), c_void_p]),
 }
 
 _LIB = None
