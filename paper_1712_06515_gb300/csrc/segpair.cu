@@ -464,7 +464,8 @@ static cudaError_t launch_segpair(const DevParams& p, const SegPairLayout& lay, 
 
 // Template batch of the two-pass search and the workspace it needs.
 static int64_t two_pass_batch_templates(const cc_plan* plan, int64_t n_t) {
-    const size_t per_ab = (size_t)plan->Q * 2 * plan->N_tau * (plan->cfg.store == CC_STORE_BF16 ? 4 : 8);
+    const size_t per_ab = (size_t)plan->Q * 2 * plan->N_tau * (plan->cfg.store == CC_STORE_BF16 ? 4 : 8) +
+                          (segpair_tma_supported(plan) ? segpair_tma_fold_bytes(plan) : 0);
     int64_t b = plan->tuning.batch_templates > 0 ? plan->tuning.batch_templates
                                                  : (int64_t)std::max<size_t>(1, TWO_PASS_WS_BUDGET / per_ab);
     return std::max<int64_t>(1, std::min<int64_t>({b, n_t, 65535}));
@@ -475,7 +476,8 @@ static void two_pass_batch(const cc_plan* plan, int64_t n_t, const SegPairLayout
     const size_t per_ab = (size_t)plan->Q * 2 * plan->N_tau * (plan->cfg.store == CC_STORE_BF16 ? 4 : 8);
     const int64_t b = two_pass_batch_templates(plan, n_t);
     *batch = b;
-    *bytes = al256(per_ab * b) + al256((size_t)plan->Q * plan->M * sizeof(float4) * b) +
+    const size_t zb = segpair_tma_supported(plan) ? segpair_tma_fold_bytes(plan) : 0;
+    *bytes = al256(per_ab * b) + al256(zb * b) + al256((size_t)plan->Q * plan->M * sizeof(float4) * b) +
              al256((size_t)b * sizeof(double)) + al256((size_t)b * 2 * lay.n_chunks * plan->N_f * sizeof(float)) +
              al256((size_t)b * plan->Q * knot_rows(plan) * sizeof(KnotRec)) + al256((size_t)plan->C * sizeof(int));
 }
@@ -507,6 +509,9 @@ cc_status search_two_pass(cc_plan* plan, const cc_template* t_dev, int64_t n_t, 
     char* w = (char*)plan->ws;
     void* ab = w;
     w += al256(per_ab * batch);
+    const bool tma = segpair_tma_supported(plan);
+    void* zf = w;   // folded segments: the fold kernel's output
+    w += al256((tma ? segpair_tma_fold_bytes(plan) : 0) * batch);
     float* nrm = (float*)w;
     w += al256((size_t)plan->Q * plan->M * sizeof(float4) * batch);
     double* D = (double*)w;
@@ -517,7 +522,7 @@ cc_status search_two_pass(cc_plan* plan, const cc_template* t_dev, int64_t n_t, 
     w += al256((size_t)batch * plan->Q * knot_rows(plan) * sizeof(KnotRec));
     int* counters = (int*)w;   // unit counters of the persistent kernel
     const int64_t nkn = knot_rows(plan);
-    const bool tma = segpair_tma_supported(plan);
+    const bool fold = tma && segpair_tma_folded(plan);
     const DevParams& p = plan->dp;
     for (int64_t t0 = 0; t0 < n_t; t0 += batch) {
         const int64_t nb = std::min(batch, n_t - t0);
@@ -531,7 +536,8 @@ cc_status search_two_pass(cc_plan* plan, const cc_template* t_dev, int64_t n_t, 
         timing_pair(plan, &ev0, &ev1);
         if (ev0) cudaEventRecord(ev0, st);
         if (tma) {
-            s = launch_segpair_tma(plan, lb, nb, ab, (const float4*)nrm, raw, counters, st);
+            if (fold) s = launch_fold(plan, nb, ab, (const float4*)nrm, zf, st);
+            if (s == CC_OK) s = launch_segpair_tma(plan, lb, nb, fold ? zf : ab, (const float4*)nrm, raw, counters, st);
             if (ev1) cudaEventRecord(ev1, st);
             if (s != CC_OK) return s;
         } else {

@@ -24,5 +24,10 @@ bool segpair_tma_supported(const cc_plan* plan);
 int segpair_tma_chunks(const cc_plan* plan, int64_t n_t);
 cc_status launch_segpair_tma(cc_plan* plan, const SegPairLayout& lay, int64_t n_t, const void* ab,
                              const float4* norm, float* raw, int* counters, cudaStream_t st);
+// Segments longer than the 4096-point transform: the fold kernel's output (bytes per
+// template) and its launch over a template batch (z then feeds launch_segpair_tma).
+bool segpair_tma_folded(const cc_plan* plan);
+size_t segpair_tma_fold_bytes(const cc_plan* plan);
+cc_status launch_fold(cc_plan* plan, int64_t n_t, const void* ab, const float4* norm, void* z, cudaStream_t st);
 
 }  // namespace cc

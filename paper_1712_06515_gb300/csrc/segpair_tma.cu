@@ -46,6 +46,8 @@ namespace {
 constexpr int TT_THREADS = 256;
 constexpr int TT_L = 4096;
 constexpr long long WAIT_LIMIT_CYCLES = 2000000000LL;   // ~1 s at 2 GHz
+constexpr int FOLD_MAX_F = 16;     // folds of a long segment onto the 4096 positions
+constexpr int FOLD_MAX_C = 1024;   // cosets of a folded plan
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -100,12 +102,15 @@ struct TmaWork {
     int64_t chunk_len;
     int64_t units;        // (template, weight, chunk) units per coset
     uint32_t off_y, off_z, off_h, off_stage, off_bar;
-    uint32_t stage_bytes;   // N_s samples of one (detector, weight, segment) row
+    uint32_t stage_bytes;   // one staged row: N_s samples, or L folded positions
+    int folded;             // N_s > L: rows of the fold kernel's output Z instead of a_r, b_r
+    int n_in;               // valid positions of a staged row (N_s, or L when folded)
 };
 
-// ab: [n_t][Q][2][N_tau] complex64 (bf16 pairs with BF16 storage), norm: [n_t][Q][M]
-// (hat-A, hat-B, hat-C, 0), raw: [n_t][2 * n_chunks][N_f] partial pair sums, counters:
-// [C] unit counters (zero at launch).
+// ab: [n_t][Q][2][N_tau] complex64 (bf16 pairs with BF16 storage), or with folded
+// segments (N_s > L) the fold kernel's Z [n_t][Q][2][M][C][L] in the same type; norm:
+// [n_t][Q][M] (hat-A, hat-B, hat-C, 0), raw: [n_t][2 * n_chunks][N_f] partial pair
+// sums, counters: [C] unit counters (zero at launch).
 template <bool BF16>
 __global__ void __launch_bounds__(TT_THREADS, 2)
 segpair_tma_kernel(DevParams p, TmaWork q, const void* __restrict__ ab, const float4* __restrict__ norm,
@@ -196,9 +201,13 @@ segpair_tma_kernel(DevParams p, TmaWork q, const void* __restrict__ ab, const fl
             }
             return false;
         };
+        // folded segments: the row Z_q of coset c is q = (b0 + c) mod C
+        const size_t zq = (size_t)(((uint64_t)p.b0 + (uint64_t)c) & (uint64_t)(C - 1));
         auto issue = [&](int64_t K, int X) {   // thread 0, after a barrier that ends every read of the stage
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            const char* src = (const char*)ab + (abt + (size_t)X * 2 * N_tau + (size_t)(K * N_s)) * ESZ;
+            const size_t el = q.folded ? ((((size_t)t * Q + X) * 2 + w) * M + K) * C * L + zq * L
+                                       : abt + (size_t)X * 2 * N_tau + (size_t)(K * N_s);
+            const char* src = (const char*)ab + el * ESZ;
             mbar_arrive_expect_tx(bar, q.stage_bytes);
             tma_load_1d(stage, src, q.stage_bytes, bar);
         };
@@ -231,7 +240,7 @@ segpair_tma_kernel(DevParams p, TmaWork q, const void* __restrict__ ab, const fl
 #pragma unroll
                     for (int r = 0; r < 16; ++r) {
                         const int s = tid + r * 256;
-                        const bool in = s < (int)N_s;
+                        const bool in = s < q.n_in;
                         if constexpr (BF16)
                             v[r] = in ? __bfloat1622float2(((const __nv_bfloat162*)stage)[s]) : make_float2(0.f, 0.f);
                         else
@@ -339,13 +348,69 @@ segpair_tma_kernel(DevParams p, TmaWork q, const void* __restrict__ ab, const fl
     }
 }
 
+// Fold of a long segment (N_s > L) onto the L = 4096 positions of the coset transforms
+// (Sec. III B 4 with a segment longer than the on-chip transform): position p of coset c
+// takes sum_f x[p + f L] W_N^((b0+c)(p + f L)) = W_N^((b0+c) p) Z_q[p] with
+// Z_q[p] = sum_f x[p + f L] W_C^(q f) and q = (b0 + c) mod C (W_N^L = W_C), a C-point
+// DFT over the fold index f computed once per (template, detector, weight, segment) for
+// every q, instead of each coset re-reading and re-twiddling the whole segment.  The
+// persistent kernel applies W_N^((b0+c) p) as it does for whole segments.
+// grid: x = segment K, y = detector X * 2 + weight w, z = template of the batch.
+// ab: [n_t][Q][2][N_tau], z: [n_t][Q][2][M][C][L] (both in the plan's storage type).
+template <bool BF16>
+__global__ void __launch_bounds__(TT_THREADS)
+fold_kernel(DevParams p, const void* __restrict__ ab, const float4* __restrict__ norm, void* __restrict__ z) {
+    __shared__ float2 wc[FOLD_MAX_C];   // W_C^n
+    constexpr int L = TT_L;
+    const int64_t K = blockIdx.x;
+    const int X = blockIdx.y >> 1, w = blockIdx.y & 1;
+    const int64_t t = blockIdx.z;
+    const int Q = p.Q, C = p.C, tid = threadIdx.x;
+    const int64_t N_s = p.N_s, M = p.M;
+    const float4 nm = norm[((size_t)t * Q + X) * M + K];
+    if (!(nm.x + nm.y > 0.f)) return;   // no weight in the segment: the row is never read
+    for (int n = tid; n < C; n += TT_THREADS) {
+        float sn, cs;
+        sincospif(-2.0f * (float)n / (float)C, &sn, &cs);
+        wc[n] = make_float2(cs, sn);
+    }
+    __syncthreads();
+    const int F = (int)((N_s + L - 1) / L);
+    const size_t row = (((size_t)t * Q + X) * 2 + w) * p.N_tau + (size_t)(K * N_s);
+    const size_t zrow = ((((size_t)t * Q + X) * 2 + w) * M + K) * C * L;
+    for (int i = 0; i < L / TT_THREADS; ++i) {
+        const int pp = tid + TT_THREADS * i;
+        float2 a[FOLD_MAX_F];
+#pragma unroll
+        for (int f = 0; f < FOLD_MAX_F; ++f) {
+            const int64_t sidx = pp + (int64_t)f * L;
+            a[f] = make_float2(0.f, 0.f);
+            if (f < F && sidx < N_s) {
+                if constexpr (BF16) a[f] = __bfloat1622float2(((const __nv_bfloat162*)ab)[row + sidx]);
+                else a[f] = __ldg((const float2*)ab + row + sidx);
+            }
+        }
+        for (int qq = 0; qq < C; ++qq) {
+            float2 acc = a[0];
+#pragma unroll
+            for (int f = 1; f < FOLD_MAX_F; ++f)
+                if (f < F) acc = cadd(acc, cmul(a[f], wc[(qq * f) & (C - 1)]));
+            const size_t o = zrow + (size_t)qq * L + pp;
+            if constexpr (BF16) ((__nv_bfloat162*)z)[o] = __float22bfloat162_rn(acc);
+            else ((float2*)z)[o] = acc;
+        }
+    }
+}
+
 size_t al128(size_t b) { return (b + 127) & ~(size_t)127; }
 
 bool tma_layout(const cc_plan* plan, TmaWork* q, size_t* bytes) {
     const DevParams& p = plan->dp;
     const int esz = p.store == CC_STORE_BF16 ? 4 : 8;
     q->mmax = (int)((plan->kbar.back() - plan->k0) / p.C);
-    q->stage_bytes = (uint32_t)(p.N_s * esz);
+    q->folded = p.N_s > TT_L ? 1 : 0;
+    q->n_in = q->folded ? TT_L : (int)p.N_s;
+    q->stage_bytes = (uint32_t)(q->n_in * esz);
     size_t o = 0;
     q->off_stage = (uint32_t)o;
     o = al128(o + q->stage_bytes);
@@ -374,13 +439,14 @@ int occupancy(size_t smem) {
 
 }  // namespace
 
-// Coset length 4096 with whole segments (N_s <= 4096) of a multiple of 16 samples (rows
-// then start on 16-byte boundaries for the bulk copies, and the pair phase repeats every
-// 256 bins), Q <= 2, R <= 1, the output bins in the lower half of each coset transform.
+// Coset length 4096, segments of a multiple of 16 samples (rows then start on 16-byte
+// boundaries for the bulk copies, and the pair phase repeats every 256 bins), Q <= 2,
+// R <= 1, the output bins in the lower half of each coset transform; segments longer
+// than 4096 samples are folded first (at most FOLD_MAX_F folds and FOLD_MAX_C cosets).
 bool segpair_tma_supported(const cc_plan* plan) {
     const DevParams& p = plan->dp;
-    if (p.L != TT_L || p.N_s > TT_L || p.Q > 2 || p.R > 1 || p.pair_mode == CC_PAIRS_CROSS_ONLY || plan->N_f < 1)
-        return false;
+    if (p.L != TT_L || p.Q > 2 || p.R > 1 || p.pair_mode == CC_PAIRS_CROSS_ONLY || plan->N_f < 1) return false;
+    if (p.N_s > TT_L && (p.C > FOLD_MAX_C || (p.N_s + TT_L - 1) / TT_L > FOLD_MAX_F)) return false;
     // N_s a multiple of 16: one pair phase per thread (and 16-byte aligned rows)
     if (p.N_s % 16) return false;
     TmaWork q;
@@ -401,6 +467,28 @@ int segpair_tma_chunks(const cc_plan* plan, int64_t n_t) {
     const int64_t want = (per_cta * ctas_per_coset + 2 * n_t - 1) / (2 * n_t);
     const int64_t maxch = std::max<int64_t>(1, p.M / (4 * p.R + 1));
     return (int)std::max<int64_t>(1, std::min<int64_t>({want, maxch, 32767}));
+}
+
+bool segpair_tma_folded(const cc_plan* plan) { return plan->dp.N_s > TT_L; }
+
+// Bytes of the fold kernel's output per template (0 for whole segments).
+size_t segpair_tma_fold_bytes(const cc_plan* plan) {
+    if (!segpair_tma_folded(plan)) return 0;
+    const DevParams& p = plan->dp;
+    return (size_t)p.Q * 2 * p.M * p.C * TT_L * (p.store == CC_STORE_BF16 ? 4 : 8);
+}
+
+cc_status launch_fold(cc_plan* plan, int64_t n_t, const void* ab, const float4* norm, void* z, cudaStream_t st) {
+    const DevParams& p = plan->dp;
+    if (n_t > 65535 || p.M > 0x7fffffff) return fail(CC_ERR_UNSUPPORTED, "fold launch size");
+    const dim3 grid((unsigned)p.M, (unsigned)(2 * p.Q), (unsigned)n_t);
+    if (p.store == CC_STORE_BF16)
+        fold_kernel<true><<<grid, TT_THREADS, 0, st>>>(p, ab, norm, z);
+    else
+        fold_kernel<false><<<grid, TT_THREADS, 0, st>>>(p, ab, norm, z);
+    count_launch();
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? CC_OK : cuda_fail(e, "fold launch");
 }
 
 cc_status launch_segpair_tma(cc_plan* plan, const SegPairLayout& lay, int64_t n_t, const void* ab,

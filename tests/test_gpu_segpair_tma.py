@@ -72,6 +72,36 @@ def test_coset4096_bf16_storage():
     assert_close(got, ref, 1e-2)
 
 
+FOLD = {
+    # N_s = 8000 on 4096 positions (two folds, 16 cosets)
+    "F2": dict(n_samples=8000 * 8, T_sft=400.0, T_max=8000.0, T_short=8000.0, f_band=0.05, f_h=150.0,
+               duty=0.6, mean_lock_s=20000.0),
+    # N_s = 36000 (nine folds, 64 cosets): the long-lag segment geometry
+    "F9": dict(n_samples=36000 * 4, T_sft=360.0, T_max=36000.0, T_short=36000.0, f_band=0.02, f_h=150.0,
+               duty=0.7, mean_lock_s=40000.0),
+}
+
+
+@pytest.mark.parametrize("name", sorted(FOLD))
+def test_folded_segments_bf16(name):
+    """Segments longer than the 4096-point transform (BF16 storage): the fold kernel's
+    C-point DFT over the fold index, then the persistent kernel, against the oracle at the
+    BF16 bar, and against the staged path (same storage) to a tighter bound."""
+    ds = synth.tiny(seed=43, n_templates=2, **FOLD[name])
+    ref = oracle.rho(ds)
+    with cc.CrossCorrPlan(ds.cfg, ds.dets, store=cc.STORE_BF16) as plan:
+        assert plan.info["L"] == 4096 and plan.info["N_s"] > 4096
+        assert plan.search_path == cc.PATH_TWO_PASS
+        x = torch.from_numpy(ds.x64).to(DEV)
+        tm = torch.from_numpy(ds.templates).to(DEV)
+        got = plan.search(x, tm).cpu().numpy().astype(np.float64)
+        plan.check()
+        plan.set_path(cc.PATH_STAGED)
+        staged = plan.search(x, tm).cpu().numpy().astype(np.float64)
+    assert_close(got, ref, 1e-2)
+    assert_close(got, staged, 3e-3)
+
+
 def test_coset4096_loud_injection_topk():
     """A loud injection on a template of the batch: the top-10 (template, bin) list equals
     the oracle's."""
