@@ -111,10 +111,15 @@ def fp32_peak(cc, clk):
                      + (f" (measured {measured:.2f})" if measured else ""))
 
 
-def spectrum_kernel_name(info):
-    """The two-pass path's spectrum + pair-sum kernel for this plan's geometry."""
-    if info["L"] == 4096 and info["N_s"] <= 4096 and info["N_s"] % 16 == 0 and info["R"] <= 1:
-        return "segpair_tma_kernel"
+def spectrum_kernel_name(info, bf16=False):
+    """The two-pass path's spectrum + pair-sum kernel(s) for this plan's geometry (the
+    event pair of the plan's kernel timing brackets all of them)."""
+    if info["L"] == 4096 and info["N_s"] % 16 == 0 and info["R"] <= 1:
+        if info["N_s"] <= 4096:
+            return "segpair_tma_kernel"
+        if bf16:   # folded segments: the persistent kernel's shared memory holds a BF16 stage
+            return ("fold64_kernel + segpair_tma_kernel" if info["C"] == 64
+                    else "fold_kernel + segpair_tma_kernel")
     return "segpair_grouped_kernel" if info["L"] <= 2048 else "segpair_kernel"
 
 
@@ -391,7 +396,7 @@ def run_gpu(args):
         # the fused path the one-pass kernel (all flops).  Against the FP32-ALU roofline
         # from the SM count, FP32 lanes and the maximum SM clock.
         if path == cc.PATH_TWO_PASS:
-            kname, kflops = spectrum_kernel_name(info), costs["fft_flops"] + costs["pair_flops"]
+            kname, kflops = spectrum_kernel_name(info, long_lag), costs["fft_flops"] + costs["pair_flops"]
         else:
             kname, kflops = "fused_kernel", costs["total_flops"]
         achieved = kflops * B * args.steps / (fused_ms / 1e3) / 1e12
@@ -550,7 +555,7 @@ def variant_long_lag(args, peak):
         ms, kms, _ = _time_search(pl, x, tm, steps=2)
         kfl = algorithmic_costs(pl.info, pl.Q, 1, dl.cfg.D, False)
         res.update({"value": B * pl.N_f / (ms / 1e3), "unit": UNIT, "ms_per_template": ms / B,
-                    "kernel": spectrum_kernel_name(pl.info),
+                    "kernel": spectrum_kernel_name(pl.info, True),
                     "spectrum_frac": (kfl["fft_flops"] + kfl["pair_flops"]) * B / (kms / 1e3) / 1e12 / peak,
                     "spectrum_share": kms / ms, "N_f": pl.N_f, "N_FFT": pl.info["N_FFT"]})
         inj = dl.injection

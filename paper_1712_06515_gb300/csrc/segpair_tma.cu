@@ -402,6 +402,60 @@ fold_kernel(DevParams p, const void* __restrict__ ab, const float4* __restrict__
     }
 }
 
+// fold_kernel for C = 64 cosets (the long-lag band: N_FFT = 2^18 = 64 x 4096) and at most
+// 16 folds, by a radix-8 split of the 64-point DFT over the fold index: with q = u + 8 v
+// and f = f1 + 8 f2, W_64^(q f) = W_8^(v f1) W_64^(u f1) W_8^(u f2), so
+// Z_(u+8v) = DFT8_v[ W_64^(u f1) (a_(f1) + a_(f1+8) W_8^u) ]: per residue u a twiddle and
+// one register 8-point DFT instead of 64 x F products.
+template <bool BF16>
+__global__ void __launch_bounds__(TT_THREADS)
+fold64_kernel(DevParams p, const void* __restrict__ ab, const float4* __restrict__ norm, void* __restrict__ z) {
+    __shared__ float2 w64[64];   // W_64^n = W_4096^(64 n)
+    constexpr int L = TT_L, C = 64;
+    const int64_t K = blockIdx.x;
+    const int X = blockIdx.y >> 1, w = blockIdx.y & 1;
+    const int64_t t = blockIdx.z;
+    const int Q = p.Q, tid = threadIdx.x;
+    const int64_t N_s = p.N_s, M = p.M;
+    const float4 nm = norm[((size_t)t * Q + X) * M + K];
+    if (!(nm.x + nm.y > 0.f)) return;   // no weight in the segment: the row is never read
+    if (tid < C) w64[tid] = __ldg(p.twL + 64 * tid);
+    __syncthreads();
+    const int F = (int)((N_s + L - 1) / L);
+    const size_t row = (((size_t)t * Q + X) * 2 + w) * p.N_tau + (size_t)(K * N_s);
+    const size_t zrow = ((((size_t)t * Q + X) * 2 + w) * M + K) * C * L;
+    for (int i = 0; i < L / TT_THREADS; ++i) {
+        const int pp = tid + TT_THREADS * i;
+        float2 a[16];
+#pragma unroll
+        for (int f = 0; f < 16; ++f) {
+            const int64_t sidx = pp + (int64_t)f * L;
+            a[f] = make_float2(0.f, 0.f);
+            if (f < F && sidx < N_s) {
+                if constexpr (BF16) a[f] = __bfloat1622float2(((const __nv_bfloat162*)ab)[row + sidx]);
+                else a[f] = __ldg((const float2*)ab + row + sidx);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            float2 v[16];
+#pragma unroll
+            for (int f1 = 0; f1 < 8; ++f1) {
+                float2 b = a[f1];
+                if (f1 + 8 < F) b = cadd(b, u == 0 ? a[f1 + 8] : cmul(a[f1 + 8], w64[8 * u]));
+                v[f1] = (u == 0 || f1 == 0) ? b : cmul(b, w64[(u * f1) & 63]);
+            }
+            dft8(v);   // v[j] = sum_f1 W_8^(j f1) (...): Z_(u + 8 j)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const size_t o = zrow + (size_t)(u + 8 * j) * L + pp;
+                if constexpr (BF16) ((__nv_bfloat162*)z)[o] = __float22bfloat162_rn(v[j]);
+                else ((float2*)z)[o] = v[j];
+            }
+        }
+    }
+}
+
 size_t al128(size_t b) { return (b + 127) & ~(size_t)127; }
 
 bool tma_layout(const cc_plan* plan, TmaWork* q, size_t* bytes) {
@@ -482,10 +536,14 @@ cc_status launch_fold(cc_plan* plan, int64_t n_t, const void* ab, const float4* 
     const DevParams& p = plan->dp;
     if (n_t > 65535 || p.M > 0x7fffffff) return fail(CC_ERR_UNSUPPORTED, "fold launch size");
     const dim3 grid((unsigned)p.M, (unsigned)(2 * p.Q), (unsigned)n_t);
-    if (p.store == CC_STORE_BF16)
-        fold_kernel<true><<<grid, TT_THREADS, 0, st>>>(p, ab, norm, z);
-    else
-        fold_kernel<false><<<grid, TT_THREADS, 0, st>>>(p, ab, norm, z);
+    const bool bf16 = p.store == CC_STORE_BF16;
+    if (p.C == 64) {
+        if (bf16) fold64_kernel<true><<<grid, TT_THREADS, 0, st>>>(p, ab, norm, z);
+        else fold64_kernel<false><<<grid, TT_THREADS, 0, st>>>(p, ab, norm, z);
+    } else {
+        if (bf16) fold_kernel<true><<<grid, TT_THREADS, 0, st>>>(p, ab, norm, z);
+        else fold_kernel<false><<<grid, TT_THREADS, 0, st>>>(p, ab, norm, z);
+    }
     count_launch();
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? CC_OK : cuda_fail(e, "fold launch");
