@@ -248,6 +248,181 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# Timed CPU baseline: a plain FP32 implementation of the same algorithm on the host cores
+# ---------------------------------------------------------------------------
+CPU_KNOT = 128          # FP64 timing at knots every 128 samples, a cubic between them
+CPU_SEG_CHUNK = 256     # segments processed together (bounds the working set per thread)
+
+
+def _cpu_plan(cfg):
+    """Plan quantities of Sec. III B 2-4 (FP64): segment length, pair window, metric
+    resolution, zero-padded FFT size, decimation and output bins, with the same readings
+    as the GPU plan (T_short = max(T_max, T_sft) unless given, floor for "lround", the
+    remainder with its final |b|, f_FFT = f_h + f_r* - 1/(2 dt'))."""
+    dt = float(cfg.dt)
+    T_short = float(cfg.T_short) if cfg.T_short > 0 else max(float(cfg.T_max), float(cfg.T_sft))
+    N_s = int(round(T_short / dt))
+    R = int(math.floor(cfg.T_max / T_short + 1e-9))
+    M = int(cfg.n_samples) // N_s
+    T_coh = 2.0 * cfg.T_max + T_short
+    dlf = math.sqrt(6.0 * cfg.mu_f / math.pi) / T_coh
+    N0 = (1.0 / dt / dlf) * math.ceil(dlf * T_coh)
+    N = 1
+    while N < N0:
+        N *= 2
+    T_FFT = N * dt
+    nu_R = dlf * dt * N
+    N_f = int(math.floor(cfg.f_band / dlf))
+    a, b = -cfg.f_band / 2.0, 1.0 / T_FFT
+    f_r = 0.0 if a == 0.0 else a - math.copysign(1.0, a) * math.floor(abs(a) / b) * b
+    f_FFT = cfg.f_h + f_r - 0.5 / dt
+    k0 = int(math.floor((cfg.f_h - cfg.f_band / 2.0 - f_FFT) * T_FFT + 1e-9))
+    kbar = k0 + np.floor(nu_R * np.arange(N_f)).astype(np.int64)
+    return dict(N_s=N_s, R=R, M=M, N=N, N_f=N_f, f_r=f_r, T_short=T_short,
+                idx=np.mod(kbar - N // 2, N), dfreq=(f_r - 0.5 / dt) + kbar / T_FFT)
+
+
+def _cpu_lerp(t0, step, tab, t):
+    u = (t - t0) / step
+    i = np.clip(np.floor(u), 0, len(tab) - 2).astype(np.int64)
+    f = u - i
+    return tab[i] + f * (tab[i + 1] - tab[i])
+
+
+def _cpu_detector(x, det, cfg, pl, a_p, tasc_rel, P):
+    """Spectra F_a, F_b [M][N_f] (complex64) and segment norms [3][M] of one detector for
+    one circular-orbit template: FP64 timing at knots (Eqs. t-ssb-equation, tau-equation)
+    with an FP64 cubic between knots, FP32 windowed-sinc interpolation (2D+1 Hamming taps)
+    and heterodyne correction, FP32 weights a/sigma^2, b/sigma^2, and complex64 zero-padded
+    FFTs (SciPy pocketfft) of each segment at the output bins."""
+    import scipy.fft
+    dt, D, N_t = cfg.dt, cfg.D, x.shape[0]
+    N_s, M, N, N_f = pl["N_s"], pl["M"], pl["N"], pl["N_f"]
+    nsft = int(round(cfg.T_sft / dt))
+    n = M * N_s
+    # FP64 knots tau_k = (k - 1) CPU_KNOT dt: the binary delay b = R/c at u = tau + b and the
+    # SSB delay Delta at t = u - Delta, each by fixed point; d = tau - t = Delta - b
+    nk = (n + CPU_KNOT - 1) // CPU_KNOT + 3
+    tk = (np.arange(nk, dtype=np.float64) - 1.0) * CPU_KNOT * dt
+    bk = np.zeros(nk)
+    for _ in range(8):
+        bk = a_p * np.sin(2.0 * np.pi * ((tk + bk - tasc_rel) / P))
+    dl = _cpu_lerp(det.eph_t0, det.eph_dt, det.ssb_delay, tk + bk)
+    for _ in range(8):
+        dl = _cpu_lerp(det.eph_t0, det.eph_dt, det.ssb_delay, tk + bk - dl)
+    dk = dl - bk
+    w = (0.54 - 0.46 * np.cos(2.0 * np.pi * np.arange(2 * D + 1) / (2 * D))).astype(np.float32)
+    sig = np.asarray(det.sigma, np.float64)
+    pre = np.exp(-2j * np.pi * ((pl["f_r"] * np.arange(N_s) * dt) % 1.0)).astype(np.complex64)
+    Fa = np.empty((M, N_f), np.complex64)
+    Fb = np.empty((M, N_f), np.complex64)
+    norms = np.empty((3, M), np.float32)
+    for K0 in range(0, M, CPU_SEG_CHUNK):
+        K1 = min(M, K0 + CPU_SEG_CHUNK)
+        r = np.arange(K0 * N_s, K1 * N_s, dtype=np.int64)
+        k = r // CPU_KNOT
+        h = (r - k * CPU_KNOT) / CPU_KNOT
+        d = (-h * (h - 1) * (h - 2) / 6.0 * dk[k] + (h + 1) * (h - 1) * (h - 2) / 2.0 * dk[k + 1]
+             - (h + 1) * h * (h - 2) / 2.0 * dk[k + 2] + (h + 1) * h * (h - 1) / 6.0 * dk[k + 3])
+        g = 0.5 - d / dt                         # t/dt = r - d/dt; j* = round half up
+        fl = np.floor(g)
+        jstar = r + fl.astype(np.int64)
+        delta = ((g - 0.5) - fl).astype(np.float32)
+        # windowed sinc with sin(pi (delta - m)) = (-1)^m sin(pi delta)
+        sp = (np.sin(np.float32(np.pi) * delta) / np.float32(np.pi)).astype(np.float32)
+        zero = delta == 0.0
+        acc = np.zeros(r.shape, np.complex64)
+        for m in range(-D, D + 1):
+            j = jstar + m
+            ok = (j >= 0) & (j < N_t)
+            xv = np.where(ok, x[np.clip(j, 0, N_t - 1)], np.complex64(0))
+            with np.errstate(divide="ignore", invalid="ignore"):
+                c = w[m + D] * ((-sp if m & 1 else sp) / (delta - np.float32(m)))
+            c = np.where(zero, np.float32(1.0 if m == 0 else 0.0), c).astype(np.float32)
+            acc += xv * c
+        acc *= np.exp(-2j * np.pi * ((cfg.f_h * d) % 1.0)).astype(np.complex64)
+        # weights at the detector time (j* + delta) dt
+        tt = (jstar + delta.astype(np.float64)) * dt
+        a = _cpu_lerp(det.ab_t0, det.ab_dt, det.a_tab, tt).astype(np.float32)
+        b = _cpu_lerp(det.ab_t0, det.ab_dt, det.b_tab, tt).astype(np.float32)
+        q = np.floor_divide(jstar, nsft)
+        blk = np.where((jstar - q * nsft == 0) & (delta < 0), q - 1, q)
+        ok = (blk >= 0) & (blk < len(sig))
+        s = np.where(ok, sig[np.clip(blk, 0, len(sig) - 1)], 0.0).astype(np.float32)
+        s2 = s * s
+        inv = np.where(s > 0, 1.0 / np.where(s > 0, s2, 1.0), 0.0).astype(np.float32)
+        al, be = a * inv, b * inv
+        nseg = K1 - K0
+        norms[0, K0:K1] = (al * al * s2).reshape(nseg, N_s).sum(axis=1)
+        norms[1, K0:K1] = (be * be * s2).reshape(nseg, N_s).sum(axis=1)
+        norms[2, K0:K1] = (al * be * s2).reshape(nseg, N_s).sum(axis=1)
+        ph = np.exp(-2j * np.pi * (np.outer(np.arange(K0, K1) * pl["T_short"], pl["dfreq"]) % 1.0))
+        ph = ph.astype(np.complex64)
+        for wt, out in ((al, Fa), (be, Fb)):
+            y = (acc * wt).reshape(nseg, N_s) * pre
+            out[K0:K1] = scipy.fft.fft(y, n=N, axis=1, workers=1)[:, pl["idx"]] * ph
+    return Fa, Fb, norms
+
+
+def _cpu_pairs(F, norms, Q, M, R, mode):
+    """Re sum over the pair set of conj(F_a,XK) F_a,YL + conj(F_b,XK) F_b,YL (FP32) and the
+    normalisation sum of A_K A_L + B_K B_L + 2 C_K C_L (Eq. final-formatted-rho; each
+    unordered pair once unless mode = 2, every ordered pair, or 1, cross-detector only)."""
+    N_f = F[0][0].shape[1]
+    raw = np.zeros(N_f, np.float32)
+    Dn = 0.0
+    for X in range(Q):
+        for Y in range(Q):
+            for lag in range(-R, R + 1):
+                if not (mode == 2 or X < Y or (X == Y and mode == 0 and lag >= 1)):
+                    continue
+                a, b = max(0, -lag), min(M, M - lag)
+                if a >= b:
+                    continue
+                for c in (0, 1):
+                    raw += (np.conj(F[X][c][a:b]) * F[Y][c][a + lag:b + lag]).real.sum(axis=0, dtype=np.float32)
+                nx, ny = norms[X], norms[Y]
+                Dn += float(np.sum(nx[0][a:b] * ny[0][a + lag:b + lag] + nx[1][a:b] * ny[1][a + lag:b + lag]
+                                   + 2.0 * nx[2][a:b] * ny[2][a + lag:b + lag], dtype=np.float64))
+    return raw, Dn
+
+
+def cpu_fp32_rho(ds, templates, threads=None):
+    """rho [template][bin] by the plain FP32 CPU implementation, templates spread over
+    `threads` host threads (default: every core).  Circular orbits."""
+    from concurrent.futures import ThreadPoolExecutor
+    cfg = ds.cfg
+    pl = _cpu_plan(cfg)
+    xs = [np.ascontiguousarray(np.asarray(ds.x[q]).astype(np.complex64)) for q in range(len(ds.dets))]
+    tm = np.asarray(templates, np.float64)
+
+    def one(row):
+        F, nm = [], []
+        for q, det in enumerate(ds.dets):
+            Fa, Fb, norms = _cpu_detector(xs[q], det, cfg, pl, float(row[0]), float(row[1]) - cfg.t0, float(row[2]))
+            F.append((Fa, Fb))
+            nm.append(norms)
+        raw, Dn = _cpu_pairs(F, nm, len(ds.dets), pl["M"], pl["R"], cfg.pair_mode)
+        return (math.sqrt(2.0) * raw / math.sqrt(Dn)).astype(np.float32) if Dn > 0 else np.zeros_like(raw)
+
+    with ThreadPoolExecutor(max_workers=threads or os.cpu_count()) as ex:
+        return np.stack(list(ex.map(one, tm)))
+
+
+def cpu_fp32_baseline(ds, n_templates=16):
+    """Time the FP32 CPU implementation on the first n_templates of the workload's grid,
+    every core busy (templates are independent, so the rate scales per template)."""
+    threads = min(os.cpu_count() or 1, n_templates)
+    t = time.perf_counter()
+    rho = cpu_fp32_rho(ds, ds.templates[:n_templates], threads)
+    sec = time.perf_counter() - t
+    return {"value": rho.size / sec, "unit": UNIT, "cores": threads, "kind": "fp32_pocketfft",
+            "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+            "sample": f"{n_templates} templates x {rho.shape[1]} bins of the full workload ({sec:.1f} s), "
+                      f"one template per thread"}
+
+
+# ---------------------------------------------------------------------------
 # GPU run
 # ---------------------------------------------------------------------------
 def algorithmic_costs(plan_info, Q, n_t, D=8, learned=False):
@@ -456,6 +631,9 @@ def run_gpu(args):
         }
         if world == 1 and not args.no_variants and args.workload == "o1_band":
             out["variants"] = run_variants(args, ds, x, tm_host, plan, peak)
+        if world == 1 and not args.no_cpu_baseline and args.workload == "o1_band" and not learned \
+                and args.eccentricity == 0.0:
+            out["cpu_fp32_baseline"] = cpu_fp32_baseline(ds)
         if world == 1 and not args.no_cpu_baseline:
             v, dt, n = cpu_oracle_baseline(args.cpu_days)
             out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
