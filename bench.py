@@ -234,6 +234,7 @@ def run_reference(args):
     value = tot_u / tot_t
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "ranks_seen": int(os.environ.get("WORLD_SIZE", "1")),
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot_t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
@@ -467,9 +468,13 @@ def run_gpu(args):
 
     long_lag = args.workload == "o1_long"
     ds = synth.o1_band(seed=1002, T_max=36000.0 if long_lag else 3600.0)
+    from paper_1712_06515_gb300 import sharding
     B = args.templates
     grid = ds.templates
-    idx = (np.arange(B) + rank * B) % grid.shape[0]
+    # weak scaling: rank r takes its contiguous block of a global batch of world x B
+    # templates (the grid repeated as needed)
+    t_start, t_stop = sharding.shard_range(world * B, rank, world)
+    idx = np.arange(t_start, t_stop) % grid.shape[0]
     # template rows (a_p, T_asc, P, e, omega): the circular grid with e = omega = 0
     tm_host = np.ascontiguousarray(np.concatenate([grid[idx], np.zeros((B, 2))], axis=1))
     if args.eccentricity:
@@ -561,6 +566,13 @@ def run_gpu(args):
     e2e_s = e0.elapsed_time(e1) / 1000.0
     e2e_value = world * B * N_f * args.e2e_steps / e2e_s
 
+    # the one collective: every rank's top-k (global template indices) merged on the host
+    k_hits = 16
+    local = plan.topk(rho, k_hits)
+    hits = np.zeros(len(local), sharding.HIT_DTYPE)
+    for f in ("tmpl", "bin", "freq", "rho"):
+        hits[f] = local[f]
+    merged = sharding.merge_topk(sharding.globalize(hits, t_start), k_hits)
     peaks, peak_kind = load_peaks()
     out = None
     if rank == 0:
@@ -624,6 +636,10 @@ def run_gpu(args):
                        "eccentricity": args.eccentricity},
             "roofline": roof,
             "clocks": clk,
+            "topk": {"k": k_hits, "merged_from_ranks": world,
+                     "best": {"template": int(merged["tmpl"][0]), "grid_template": int(merged["tmpl"][0]) % grid.shape[0],
+                              "bin": int(merged["bin"][0]), "freq": float(merged["freq"][0]),
+                              "rho": float(merged["rho"][0])}},
             "gpu_launches": int(launches),
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(x_host.numel() * 8 + tm_pin.numel() * 8),
@@ -1032,8 +1048,23 @@ def run_sft_series(args):
     print(json.dumps(out), flush=True)
 
 
+def launch_ranks(argv, n):
+    """`--gpus N` with N > 1 outside a launcher: run this script again under
+    torch.distributed.run with N ranks on this node (one per GPU, rendezvous on 127.0.0.1)
+    and return its exit status."""
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__), *argv]
+    return subprocess.call(cmd)
+
+
 def main():
     args = parse()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(launch_ranks(sys.argv[1:], args.gpus))
     if args.impl == "reference":
         run_reference(args)
         return
