@@ -22,8 +22,9 @@
 //     segment-start phase W_N^(k seg0_K) of bin k = b0 + c + C m.  In a pair of
 //     consecutive segments that phase leaves theta(m) = W_N^(-k N_s), one constant per
 //     bin: Re(conj(F_K) F_(K-1)) = Re(conj(T_K) T_(K-1) theta(m)), and the same-segment
-//     terms carry no phase.  With N_s a multiple of 16, theta(m + 256) = theta(m), so each
-//     thread needs one theta for its eight bins m = tid + 256 r;
+//     terms carry no phase.  theta(m + 256) = theta(m) psi with psi = exp(2 pi i N_s / 16),
+//     so each thread keeps theta of its first bin m = tid and steps by psi through its
+//     eight bins m = tid + 256 r (psi = 1 when 16 divides N_s);
 //   * coset twiddles without a per-sample table: the twiddle W_N^((b0+c) s) of sample
 //     s = tid + 256 r splits into a factor per r (16 values per coset, applied in the first
 //     pass) and a factor per thread, which passes through the first pass's DFT and is
@@ -168,6 +169,9 @@ segpair_tma_kernel(DevParams p, TmaWork q, const void* __restrict__ ab, const fl
         // pair phase of this thread's bins: theta = W_N^(-(bc + C tid) N_s)
         const uint64_t ct = bc + (uint64_t)C * tid;
         const float2 theta = twiddle_N((N - (ct * (uint64_t)N_s & mask)) & mask, N);
+        const bool psi_one = (N_s & 15) == 0;
+        float2 psi;
+        sincospif(0.125f * (float)(N_s & 15), &psi.y, &psi.x);   // exp(2 pi i (N_s mod 16) / 16)
         // last pass (NS = 256): element r3 of thread tid takes W_L^(tid r3) W_N^(bc r3) =
         // W_N^(ct r3), formed from these four powers
         const float2 b1 = twiddle_N(ct & mask, N), b2 = twiddle_N((2 * ct) & mask, N);
@@ -312,8 +316,9 @@ segpair_tma_kernel(DevParams p, TmaWork q, const void* __restrict__ ab, const fl
                 }
             }
             // pair terms of segment K (F = 0 for a detector with no weight in it); prevP
-            // holds the previous segment's detector sum times theta
+            // holds the previous segment's detector sum times theta of its bin
             const bool acc_on = K >= Ka;
+            float2 th = theta;
 #pragma unroll
             for (int r = 0; r < SLP; ++r) {
                 const int m = tid + NSL * r;
@@ -329,8 +334,9 @@ segpair_tma_kernel(DevParams p, TmaWork q, const void* __restrict__ ab, const fl
                     const float term = p.pair_mode == CC_PAIRS_ALL_ORDERED ? fmaf(2.f, redot(S, P), redot(S, S))
                                                                            : redot(S, P) + redot(F1, F0);
                     if (acc_on) kahan_add(accP[r], cmpP[r], term);
-                    if (R > 0) prevP[r] = cmul(S, theta);
+                    if (R > 0) prevP[r] = cmul(S, th);
                 }
+                if (R > 0 && !psi_one) th = cmul(th, psi);
             }
         }
         // partial sums of this (template, weight, chunk) row for the coset's bins, staged
@@ -493,16 +499,16 @@ int occupancy(size_t smem) {
 
 }  // namespace
 
-// Coset length 4096, segments of a multiple of 16 samples (rows then start on 16-byte
-// boundaries for the bulk copies, and the pair phase repeats every 256 bins), Q <= 2,
-// R <= 1, the output bins in the lower half of each coset transform; segments longer
-// than 4096 samples are folded first (at most FOLD_MAX_F folds and FOLD_MAX_C cosets).
+// Coset length 4096, segments of an even number of samples (a multiple of 4 with BF16
+// storage: rows then start on 16-byte boundaries for the bulk copies), Q <= 2, R <= 1, the
+// output bins in the lower half of each coset transform; segments longer than 4096
+// samples are folded first (at most FOLD_MAX_F folds and FOLD_MAX_C cosets).
 bool segpair_tma_supported(const cc_plan* plan) {
     const DevParams& p = plan->dp;
     if (p.L != TT_L || p.Q > 2 || p.R > 1 || p.pair_mode == CC_PAIRS_CROSS_ONLY || plan->N_f < 1) return false;
     if (p.N_s > TT_L && (p.C > FOLD_MAX_C || (p.N_s + TT_L - 1) / TT_L > FOLD_MAX_F)) return false;
-    // N_s a multiple of 16: one pair phase per thread (and 16-byte aligned rows)
-    if (p.N_s % 16) return false;
+    // rows start on 16-byte boundaries for the bulk copies
+    if (p.N_s % (p.store == CC_STORE_BF16 ? 4 : 2)) return false;
     TmaWork q;
     size_t bytes;
     if (!tma_layout(plan, &q, &bytes)) return false;

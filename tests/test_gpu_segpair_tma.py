@@ -33,6 +33,8 @@ CASES = {
     "R1_D16": dict(D=16),
     "R1_ragged": dict(n_samples=3600 * 14 + 1802),   # partial last segment dropped
     "R1_odd_Ns": dict(T_max=3599.0, T_short=3599.0),   # odd segment length: the older kernel
+    "R1_Ns3000": dict(n_samples=3000 * 16, T_max=3000.0, T_short=3000.0),   # 16 does not divide N_s
+    "R1_Ns2180": dict(n_samples=2180 * 20, T_max=2180.0, T_short=2180.0, T_sft=218.0),
 }
 
 
