@@ -60,7 +60,7 @@ def parse():
                          "bands over 20-250 Hz from one CUDA graph launch")
     ap.add_argument("--template-scale", type=float, default=0.25,
                     help="multiband: fraction of the 4.1e5-template grid per step")
-    ap.add_argument("--method", default="resampled", choices=["resampled", "demod", "sft_series"],
+    ap.add_argument("--method", default="resampled", choices=["resampled", "demod", "sft_series", "dft_gemm"],
                     help="resampled: the paper's method (default); demod: the detector-frame "
                          "statistic it replaces, on the same workload, for the speed comparison; "
                          "sft_series: the SFT-to-series input preparation of the 120-day band")
@@ -1048,6 +1048,53 @@ def run_sft_series(args):
     print(json.dumps(out), flush=True)
 
 
+def run_dft_gemm(args):
+    """The tensor-core question for short segments, by measurement: a batched DFT-as-GEMM
+    (cuBLAS BF16 through torch.matmul, FP32 accumulation) of the exact shape the direct
+    DFT of a segment at the output bins needs -- the real form [2 N_f x 2 N_s] times
+    [2 N_s x (segments x detectors x weights x templates)] -- against the library's own
+    spectrum + pair-sum kernel on the same band, per template.  The GEMM alone covers only
+    the spectra (no pair sums, no resampling) and is single-pass BF16 (the 1e-2 bar; the
+    FP32 bar would need a split into several passes)."""
+    import torch
+    import synth
+    import paper_1712_06515_gb300 as cc
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    rows = []
+    for b in (0, 2, 6):   # the shortest-segment bands: coset lengths 256 and 512
+        ds = synth.multiband_band(b, template_scale=0.25, max_templates=64)
+        n_t = ds.templates.shape[0]
+        with cc.CrossCorrPlan(ds.cfg, ds.dets) as plan:
+            info = plan.info
+            x = torch.from_numpy(ds.x64).to(dev)
+            tm = torch.from_numpy(ds.templates).to(dev)
+            ms, kms, _ = _time_search(plan, x, tm, steps=3)
+        N_s, N_f, M, Q = info["N_s"], info["N_f"], info["M"], plan.Q
+        cols = M * Q * 2 * n_t
+        A = torch.randn(2 * N_f, 2 * N_s, device=dev, dtype=torch.bfloat16)
+        B = torch.randn(2 * N_s, cols, device=dev, dtype=torch.bfloat16)
+        for _ in range(3):
+            torch.mm(A, B)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        reps = 5
+        for _ in range(reps):
+            C = torch.mm(A, B)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        gms = e0.elapsed_time(e1) / reps
+        flops = 2.0 * (2 * N_f) * (2 * N_s) * cols
+        rows.append({"band": b, "L": info["L"], "N_s": N_s, "N_f": N_f, "N_FFT": info["N_FFT"], "templates": n_t,
+                     "library_spectrum_pair_ms_per_template": kms / n_t, "library_search_ms_per_template": ms / n_t,
+                     "dft_gemm_bf16_ms_per_template": gms / n_t, "dft_gemm_tflops": flops / (gms / 1e3) / 1e12,
+                     "gemm_flops_over_fft_flops": (4.0 * N_f * N_s) / (5.0 * info["N_FFT"] * math.log2(info["N_FFT"]))})
+        del A, B, C
+    print(json.dumps({"metric": "DFT-as-GEMM vs FFT spectrum kernel, ms per template", "data": "synthetic",
+                      "peaks": load_peaks()[0], "bands": rows}), flush=True)
+
+
 def launch_ranks(argv, n):
     """`--gpus N` with N > 1 outside a launcher: run this script again under
     torch.distributed.run with N ranks on this node (one per GPU, rendezvous on 127.0.0.1)
@@ -1076,6 +1123,9 @@ def main():
         return
     if args.method == "sft_series":
         run_sft_series(args)
+        return
+    if args.method == "dft_gemm":
+        run_dft_gemm(args)
         return
     run_gpu(args)
 
