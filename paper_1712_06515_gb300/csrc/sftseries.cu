@@ -1,7 +1,9 @@
 // Heterodyned, downsampled series from SFT bands (Appendix B): per SFT an N'-point
 // inverse DFT of the band around k_h with the half-band index shift, the (-1)^j' sign and
 // the SFT-start phase exp(-2 pi i f_h (t_K - T_sft/2)) that keeps the SFTs in phase.
-// The input preparation of the search (once per dataset, not per template).
+// The input preparation of the search (once per dataset, not per template).  N' with
+// prime factors 2, 3 and 5 only takes a mixed-radix FFT; any other N' the direct DFT.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -52,6 +54,148 @@ sft_to_series_kernel(const float2* __restrict__ band, const int64_t* __restrict_
     }
 }
 
+// Mixed-radix transform of N' = product of radices 2, 3, 4, 5 (the 120-day band's
+// N' = 360 = 4 x 2 x 3 x 3 x 5): an out-of-place Stockham FFT in shared memory, one pass
+// per radix (pass p: butterfly j, k = j mod NS with NS the product of the earlier radices,
+// inputs j + r N'/R times W_(NS R)^(k r), outputs at (j - k) R + k + r NS), natural order
+// out.  The inverse DFT of Eq. shifted-for-fft is the conjugate of the forward DFT of the
+// conjugated band.  N' log N' work instead of the direct DFT's N'^2.
+constexpr int SS_MAX_PASSES = 16;
+struct Radices {
+    int n;
+    int r[SS_MAX_PASSES];
+};
+
+constexpr float kC3 = 0.866025403784438647f;    // sin(2 pi / 3)
+constexpr float kC51 = 0.309016994374947424f;   // cos(2 pi / 5)
+constexpr float kC52 = -0.809016994374947424f;  // cos(4 pi / 5)
+constexpr float kS51 = 0.951056516295153572f;   // sin(2 pi / 5)
+constexpr float kS52 = 0.587785252292473129f;   // sin(4 pi / 5)
+
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 f2scale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 f2negi(float2 a) { return make_float2(a.y, -a.x); }   // -i a
+
+// forward DFT of radix R in place on v[0 .. R-1] (exp(-2 pi i n k / R))
+__device__ __forceinline__ void dft_small(float2 (&v)[5], int R) {
+    if (R == 2) {
+        const float2 a = v[0];
+        v[0] = f2add(a, v[1]);
+        v[1] = f2sub(a, v[1]);
+    } else if (R == 3) {
+        const float2 s = f2add(v[1], v[2]), d = f2sub(v[1], v[2]);
+        const float2 t = f2sub(v[0], f2scale(s, 0.5f)), u = f2negi(f2scale(d, kC3));
+        v[0] = f2add(v[0], s);
+        v[1] = f2add(t, u);
+        v[2] = f2sub(t, u);
+    } else if (R == 4) {
+        const float2 s0 = f2add(v[0], v[2]), d0 = f2sub(v[0], v[2]);
+        const float2 s1 = f2add(v[1], v[3]), d1 = f2negi(f2sub(v[1], v[3]));
+        v[0] = f2add(s0, s1);
+        v[2] = f2sub(s0, s1);
+        v[1] = f2add(d0, d1);
+        v[3] = f2sub(d0, d1);
+    } else {   // R == 5
+        const float2 a14 = f2add(v[1], v[4]), d14 = f2sub(v[1], v[4]);
+        const float2 a23 = f2add(v[2], v[3]), d23 = f2sub(v[2], v[3]);
+        const float2 p1 = make_float2(v[0].x + kC51 * a14.x + kC52 * a23.x, v[0].y + kC51 * a14.y + kC52 * a23.y);
+        const float2 p2 = make_float2(v[0].x + kC52 * a14.x + kC51 * a23.x, v[0].y + kC52 * a14.y + kC51 * a23.y);
+        const float2 q1 = f2negi(make_float2(kS51 * d14.x + kS52 * d23.x, kS51 * d14.y + kS52 * d23.y));
+        const float2 q2 = f2negi(make_float2(kS52 * d14.x - kS51 * d23.x, kS52 * d14.y - kS51 * d23.y));
+        v[0] = f2add(v[0], f2add(a14, a23));
+        v[1] = f2add(p1, q1);
+        v[4] = f2sub(p1, q1);
+        v[2] = f2add(p2, q2);
+        v[3] = f2sub(p2, q2);
+    }
+}
+
+// `groups` T_sft blocks per CTA, one group of blockDim.x / groups threads each (the
+// passes and barriers are common to the CTA); twf: forward twiddles exp(-2 pi i e / N').
+// A gap block's group writes zeros and idles through the passes.
+__global__ void __launch_bounds__(SS_THREADS)
+sft_fft_kernel(const float2* __restrict__ band, const int64_t* __restrict__ block_sft, int64_t n_blocks,
+               int n_prime, double T_sft, double f_h, const float2* __restrict__ twf, Radices rad, int groups,
+               float2* __restrict__ x) {
+    extern __shared__ __align__(16) float2 sb[];   // per group two buffers of N'
+    const int gs = blockDim.x / groups, g = threadIdx.x / gs;
+    const int tid = threadIdx.x % gs, nt = gs;
+    const int64_t b = (int64_t)blockIdx.x * groups + g;
+    const bool have = b < n_blocks;
+    const int64_t s = have ? block_sft[b] : -1;
+    float2* xo = x + b * (int64_t)n_prime;
+    if (have && s < 0)
+        for (int j = tid; j < n_prime; j += nt) xo[j] = make_float2(0.f, 0.f);
+    const bool work = s >= 0;
+    float2* src = sb + (size_t)g * 2 * n_prime;
+    float2* dst = src + n_prime;
+    if (work) {
+        const float2* __restrict__ zs = band + s * (int64_t)n_prime;
+        for (int m = tid; m < n_prime; m += nt) {
+            const float2 z = __ldg(zs + m);
+            src[m] = make_float2(z.x, -z.y);   // conjugated band
+        }
+    }
+    __syncthreads();
+    int ns = 1;
+    for (int p = 0; p < rad.n; ++p) {
+        const int R = rad.r[p], nb = n_prime / R, tstep = n_prime / (ns * R);
+        for (int j = tid; work && j < nb; j += nt) {
+            const int k = j % ns;
+            float2 v[5];
+#pragma unroll
+            for (int r = 0; r < 5; ++r)
+                if (r < R) v[r] = src[j + r * nb];
+            if (ns > 1) {
+#pragma unroll
+                for (int r = 1; r < 5; ++r)
+                    if (r < R) {
+                        const float2 w = __ldg(twf + k * r * tstep);
+                        v[r] = make_float2(v[r].x * w.x - v[r].y * w.y, v[r].x * w.y + v[r].y * w.x);
+                    }
+            }
+            dft_small(v, R);
+            float2* d = dst + (j - k) * R + k;
+#pragma unroll
+            for (int r = 0; r < 5; ++r)
+                if (r < R) d[r * ns] = v[r];
+        }
+        __syncthreads();
+        float2* t = src;
+        src = dst;
+        dst = t;
+        ns *= R;
+    }
+    if (!work) return;
+    // SFT-start phase in FP64, reduced to cycles; output (-1)^j conj(X_j) / T_sft times it
+    const double cyc = f_h * ((double)b * T_sft);
+    const float c = (float)(cyc - floor(cyc));
+    float sn, cs;
+    sincospif(2.0f * c, &sn, &cs);
+    const float2 rot = make_float2(cs, -sn);
+    const float scale = (float)(1.0 / T_sft);
+    for (int j = tid; j < n_prime; j += nt) {
+        const float sg = (j & 1) ? -scale : scale;
+        const float2 a = make_float2(src[j].x * sg, -src[j].y * sg);
+        xo[j] = make_float2(fmaf(a.x, rot.x, -a.y * rot.y), fmaf(a.x, rot.y, a.y * rot.x));
+    }
+}
+
+// N' as radices 4, 2, 3, 5 (fours first); false if another prime divides it.
+bool factor_radices(int64_t n, Radices* rad) {
+    rad->n = 0;
+    int64_t m = n;
+    for (int R : {4, 2, 3, 5}) {
+        while (m % R == 0) {
+            if (rad->n == SS_MAX_PASSES) return false;
+            rad->r[rad->n++] = R;
+            m /= R;
+        }
+    }
+    return m == 1;
+}
+
 }  // namespace
 }  // namespace cc
 
@@ -65,10 +209,14 @@ extern "C" cc_status crosscorr_sfts_to_series(const void* band_dev, const int64_
     if (n_blocks == 0) return CC_OK;
     if (!band_dev || !block_sft_dev || !x_dev) return fail(CC_ERR_INVALID, "null device pointer");
     if (n_blocks > 2147483647) return fail(CC_ERR_UNSUPPORTED, "more than 2^31 - 1 blocks");
+    Radices rad;
+    // the FFT holds two N'-point buffers in shared memory (up to 12800 points)
+    const bool fft = n_prime <= 12800 && factor_radices(n_prime, &rad) && rad.n > 0;
+    // twiddles: exp(+2 pi i j / N') for the direct DFT, exp(-2 pi i j / N') for the FFT
     std::vector<float2> tw(n_prime);
     for (int64_t j = 0; j < n_prime; ++j) {
         const double a = 2.0 * M_PI * (double)j / (double)n_prime;
-        tw[j] = make_float2((float)cos(a), (float)sin(a));
+        tw[j] = make_float2((float)cos(a), (float)(fft ? -sin(a) : sin(a)));
     }
     cudaStream_t st = (cudaStream_t)stream;
     float2* tw_dev = nullptr;
@@ -79,16 +227,38 @@ extern "C" cc_status crosscorr_sfts_to_series(const void* band_dev, const int64_
         cudaFreeAsync(tw_dev, st);
         return cuda_fail(e, "sfts_to_series twiddles");
     }
-    const size_t smem = sizeof(float2) * n_prime;
-    if (smem > 48 * 1024 &&
-        (e = cudaFuncSetAttribute(sft_to_series_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-            cudaSuccess) {
-        cudaFreeAsync(tw_dev, st);
-        return cuda_fail(e, "sfts_to_series smem attribute");
+    if (fft) {
+        // per block a group of threads (a quarter of the widest pass's butterflies, whole
+        // warps, at most 256) and two N'-point buffers; as many blocks per 256-thread CTA
+        // as fit in 48 KB of shared memory
+        int rmin = 5;
+        for (int i = 0; i < rad.n; ++i) rmin = std::min(rmin, rad.r[i]);
+        const int gs = (int)std::min<int64_t>(SS_THREADS, std::max<int64_t>(32, ((n_prime / rmin / 4 + 31) / 32) * 32));
+        const size_t per = 2 * sizeof(float2) * n_prime;
+        const int groups = (int)std::max<int64_t>(1, std::min<int64_t>(SS_THREADS / gs, (48 * 1024) / per));
+        const size_t smem = per * groups;
+        if (smem > 48 * 1024 &&
+            (e = cudaFuncSetAttribute(sft_fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+                cudaSuccess) {
+            cudaFreeAsync(tw_dev, st);
+            return cuda_fail(e, "sfts_to_series smem attribute");
+        }
+        const int64_t ctas = (n_blocks + groups - 1) / groups;
+        sft_fft_kernel<<<(unsigned)ctas, gs * groups, smem, st>>>((const float2*)band_dev, block_sft_dev, n_blocks,
+                                                                  (int)n_prime, T_sft, f_h, tw_dev, rad, groups,
+                                                                  (float2*)x_dev);
+    } else {
+        const size_t smem = sizeof(float2) * n_prime;
+        if (smem > 48 * 1024 &&
+            (e = cudaFuncSetAttribute(sft_to_series_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem)) != cudaSuccess) {
+            cudaFreeAsync(tw_dev, st);
+            return cuda_fail(e, "sfts_to_series smem attribute");
+        }
+        sft_to_series_kernel<<<(unsigned)n_blocks, SS_THREADS, smem, st>>>((const float2*)band_dev, block_sft_dev,
+                                                                         (int)n_prime, T_sft, f_h, tw_dev,
+                                                                         (float2*)x_dev);
     }
-    sft_to_series_kernel<<<(unsigned)n_blocks, SS_THREADS, smem, st>>>((const float2*)band_dev, block_sft_dev,
-                                                                     (int)n_prime, T_sft, f_h, tw_dev,
-                                                                     (float2*)x_dev);
     count_launch();
     e = cudaGetLastError();
     cudaFreeAsync(tw_dev, st);   // stream-ordered: freed after the kernel

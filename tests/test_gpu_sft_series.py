@@ -16,7 +16,11 @@ DEV = torch.device("cuda:0")
 
 
 @pytest.mark.parametrize("n_prime,T_sft,f_h", [(360, 360.0, 150.0), (64, 64.0, 120.0), (1440, 1440.0, 99.5),
-                                               (64, 64.0, 120.015625)])   # odd heterodyne bin 7681
+                                               (64, 64.0, 120.015625),    # odd heterodyne bin 7681
+                                               (225, 225.0, 101.0), (750, 750.0, 88.0),   # radices 3 and 5
+                                               (7, 7.0, 100.0), (1, 1.0, 100.0),          # direct DFT
+                                               (12800, 1280.0, 150.0),    # the largest mixed-radix size
+                                               (14400, 1440.0, 150.0)])   # too large for it: direct DFT
 def test_sfts_to_series_matches_oracle(n_prime, T_sft, f_h):
     rng = np.random.default_rng(n_prime)
     n_blocks = 40
