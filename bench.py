@@ -888,7 +888,8 @@ def run_multiband(args):
                                "240-3600 s, 10 d at 60% duty, one CUDA graph launch per step",
                    "templates_per_step": int(sum(t.shape[0] for (_, _, _, t) in bands)),
                    "template_scale": args.template_scale,
-                   "paths": [{1: "fused", 2: "two-pass"}[t["path"]] + f"/w{t['chunk_waves']}" for t in mb.tuning],
+                   "paths": [{1: "fused", 2: "two-pass"}[t["path"]] + (f"/L{t['transform_len']}" if t.get("transform_len") else "")
+                             + f"/w{t['chunk_waves']}" for t in mb.tuning],
                    # per band, from the autotuner's timing of its first 64 templates: coset
                    # length, ms per template, fraction of the FP32 peak (algorithmic flops)
                    "bands": [{"L": int(pl.info["L"]), "ms_per_template": round(t["ms"] / min(64, tt.shape[0]), 4),

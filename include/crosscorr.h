@@ -285,7 +285,11 @@ typedef struct {
     int32_t chunk_waves;      /* fused and two-pass: split each template's segments into
                                  chunks until the launch has about this many CTA waves
                                  (0: 4 for fused, 40 for two-pass) */
-    int32_t reserved;         /* 0 */
+    int32_t transform_len;    /* two-pass, segments of at most 4096 samples: 0 takes the
+                                 plan's coset length (the power of two covering a segment),
+                                 4096 the persistent kernel's 4096-point coset transforms
+                                 with the segment zero-padded (needs N_FFT >= 4096: fewer
+                                 cosets, more transform work, a faster kernel) */
 } cc_tuning;
 cc_status crosscorr_plan_set_tuning(cc_plan* plan, const cc_tuning* tuning);
 

@@ -300,10 +300,11 @@ class CrossCorrPlan:
               self._lib.crosscorr_plan_set_workspace(self._h, c_void_p(_dptr(ws)), ws.numel()))
         self._ws = ws
 
-    def set_tuning(self, batch_templates: int = 0, chunk_waves: int = 0):
+    def set_tuning(self, batch_templates: int = 0, chunk_waves: int = 0, transform_len: int = 0):
         """Work split of search(): templates per two-pass batch, target CTA waves of the
-        segment-chunk split (0: defaults)."""
-        t = CcTuning(int(batch_templates), int(chunk_waves), 0)
+        segment-chunk split, and the two-pass coset transform length (0: the plan's; 4096:
+        the persistent kernel's, segments zero-padded) (0: defaults)."""
+        t = CcTuning(int(batch_templates), int(chunk_waves), int(transform_len))
         check("crosscorr_plan_set_tuning", self._lib.crosscorr_plan_set_tuning(self._h, byref(t)))
 
     def demod_prepare(self, x, n_bin: int = 2, doppler_max: float = 0.0, stream=None):

@@ -110,7 +110,7 @@ class CcLearnedInterp(ctypes.Structure):
 
 
 class CcTuning(ctypes.Structure):
-    _fields_ = [("batch_templates", c_int64), ("chunk_waves", c_int32), ("reserved", c_int32)]
+    _fields_ = [("batch_templates", c_int64), ("chunk_waves", c_int32), ("transform_len", c_int32)]
 
 
 # every symbol the header declares, with its signature

@@ -70,7 +70,11 @@ struct DevParams {
     const int* coset_m;              // [N_f] position in the coset's L-point transform
     const float2* twL;               // exp(-2 pi i j / L), j < L
     const float2* twc;               // [C][N_s]: exp(-2 pi i ((b0 + c) s mod N_FFT) / N_FFT)
-    const float2* twk;               // [C][272]: coset twiddles of the 4096-point kernel's passes (plan.cu)
+    const float2* twk;               // [C4][272]: coset twiddles of the 4096-point kernel's passes (plan.cu)
+    int C4;                          // cosets of the 4096-point decomposition (N_FFT / 4096; 0 if N_FFT < 4096)
+    const int* coset4_off;           // [C4+1], and the bin lists of that decomposition
+    const int* coset4_k;
+    const int* coset4_m;
     unsigned* err;                   // device error word: bit 0 set by a kernel whose bounded wait ran out
     const float* ltaps;              // [LEARNED_NODES][LEARNED_TAPS] learned taps (null until set)
     float ham[MAX_TAPS];             // Hamming window, 2D+1 taps
@@ -132,6 +136,7 @@ struct cc_plan {
     float* learned_taps = nullptr;
     int search_path = CC_PATH_AUTO;           // crosscorr_plan_set_path
     cc_tuning tuning = {0, 0, 0};             // crosscorr_plan_set_tuning
+    int kbar_span4 = 0;                       // largest transform position of a bin, 4096-point cosets
     bool ws_external = false;                 // ws is caller memory (crosscorr_plan_set_workspace)
     // diagnostic event pairs around fused-kernel launches (crosscorr_plan_set_kernel_timing)
     bool kernel_timing = false;

@@ -136,8 +136,11 @@ cc_status crosscorr_plan_set_workspace(cc_plan* plan, void* ws_dev, size_t ws_by
 
 cc_status crosscorr_plan_set_tuning(cc_plan* plan, const cc_tuning* tuning) {
     if (!plan || !tuning) return cc::fail(CC_ERR_INVALID, "null argument to crosscorr_plan_set_tuning");
-    if (tuning->batch_templates < 0 || tuning->chunk_waves < 0 || tuning->chunk_waves > 1000 || tuning->reserved)
-        return cc::fail(CC_ERR_INVALID, "batch_templates >= 0, 0 <= chunk_waves <= 1000, reserved = 0");
+    if (tuning->batch_templates < 0 || tuning->chunk_waves < 0 || tuning->chunk_waves > 1000 ||
+        (tuning->transform_len != 0 && tuning->transform_len != 4096))
+        return cc::fail(CC_ERR_INVALID, "batch_templates >= 0, 0 <= chunk_waves <= 1000, transform_len 0 or 4096");
+    if (tuning->transform_len == 4096 && plan->dp.C4 < 1)
+        return cc::fail(CC_ERR_UNSUPPORTED, "transform_len 4096 needs N_FFT >= 4096");
     plan->tuning = *tuning;
     return CC_OK;
 }
@@ -395,19 +398,37 @@ cc_status crosscorr_plan(const cc_config* cfg, const cc_detector* dets, cc_plan*
     // pass (element r' of second-pass thread j came from first-pass thread (j >> 4) + 16 r'):
     // its part W_N^(16 bc r') joins that pass's twiddle W_L^(16 k r') (k = j mod 16), and
     // its part W_N^(bc (j >> 4)) reaches the last pass as W_N^(bc r3) on element r3.
-    // twk[c][r], r < 16: W_N^(256 bc r); twk[c][16 + 16 r + k]: W_N^(16 r (C k + bc)).
-    std::vector<float2> twk((size_t)C * 272);
-    for (int64_t c2 = 0; c2 < C; ++c2) {
+    // twk[c][r], r < 16: W_N^(256 bc r); twk[c][16 + 16 r + k]: W_N^(16 r (C4 k + bc)), for the
+    // C4 = N_FFT / 4096 cosets of that kernel (C4 = C when the plan's coset length is 4096;
+    // a plan with shorter cosets may still take it, its segments zero-padded to 4096).
+    const int64_t C4 = N >= 4096 ? N / 4096 : 0;
+    std::vector<float2> twk((size_t)std::max<int64_t>(C4, 1) * 272);
+    for (int64_t c2 = 0; c2 < C4; ++c2) {
         const uint64_t bc = (uint64_t)((b0 + c2) % N);
         for (uint64_t r = 0; r < 16; ++r) {
             const uint64_t j = (256 * bc * r) % (uint64_t)N;
             const double ang = -2.0 * M_PI * (double)j / (double)N;
             twk[(size_t)c2 * 272 + r] = make_float2((float)cos(ang), (float)sin(ang));
             for (uint64_t k = 0; k < 16; ++k) {
-                const uint64_t j2 = (16 * r * ((uint64_t)C * k + bc)) % (uint64_t)N;
+                const uint64_t j2 = (16 * r * ((uint64_t)C4 * k + bc)) % (uint64_t)N;
                 const double a2 = -2.0 * M_PI * (double)j2 / (double)N;
                 twk[(size_t)c2 * 272 + 16 + 16 * r + k] = make_float2((float)cos(a2), (float)sin(a2));
             }
+        }
+    }
+    // coset maps of the 4096-point decomposition (the same as the plan's when L = 4096)
+    std::vector<int> off4, ck4, cm4;
+    if (C4 > 0 && C4 != C) {
+        off4.assign(C4 + 1, 0);
+        ck4.resize(p->N_f);
+        cm4.resize(p->N_f);
+        for (int64_t k = 0; k < p->N_f; ++k) off4[(p->kbar[k] - p->k0) % C4 + 1]++;
+        for (int64_t c2 = 0; c2 < C4; ++c2) off4[c2 + 1] += off4[c2];
+        std::vector<int> fill4(off4.begin(), off4.end() - 1);
+        for (int64_t k = 0; k < p->N_f; ++k) {
+            const int64_t kp = p->kbar[k] - p->k0;
+            ck4[fill4[kp % C4]] = (int)k;
+            cm4[fill4[kp % C4]++] = (int)(kp / C4);
         }
     }
     cc_status st;
@@ -417,6 +438,9 @@ cc_status crosscorr_plan(const cc_config* cfg, const cc_detector* dets, cc_plan*
         (st = upload(p, cm.data(), cm.size(), &dp.coset_m)) != CC_OK ||
         (st = upload(p, tw.data(), tw.size(), &dp.twL)) != CC_OK ||
         (st = upload(p, twk.data(), twk.size(), &dp.twk)) != CC_OK ||
+        (!off4.empty() && ((st = upload(p, off4.data(), off4.size(), &dp.coset4_off)) != CC_OK ||
+                           (st = upload(p, ck4.data(), ck4.size(), &dp.coset4_k)) != CC_OK ||
+                           (st = upload(p, cm4.data(), cm4.size(), &dp.coset4_m)) != CC_OK)) ||
         (st = upload(p, &zero_word, 1, (const unsigned**)&dp.err)) != CC_OK) {
         crosscorr_plan_destroy(p);
         return st;
@@ -430,6 +454,13 @@ cc_status crosscorr_plan(const cc_config* cfg, const cc_detector* dets, cc_plan*
     dp.ltaps = nullptr;   // crosscorr_plan_set_learned_interp fills it
     dp.L = (int)L;
     dp.C = (int)C;
+    dp.C4 = (int)C4;
+    if (C4 == C) {
+        dp.coset4_off = dp.coset_off;
+        dp.coset4_k = dp.coset_k;
+        dp.coset4_m = dp.coset_m;
+    }
+    p->kbar_span4 = C4 > 0 ? (int)((p->kbar.back() - p->k0) / C4) : 0;
     dp.log2L = log2L;
     dp.nsft = (int)nsft;
     cc::magic_for((uint32_t)nsft, &dp.nsft_m, &dp.nsft_s);

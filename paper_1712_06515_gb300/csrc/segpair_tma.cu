@@ -127,7 +127,7 @@ segpair_tma_kernel(DevParams p, TmaWork q, const void* __restrict__ ab, const fl
     uint64_t* bar = (uint64_t*)(sm + q.off_bar);
     __shared__ int s_unit, s_coset;
 
-    const int tid = threadIdx.x, Q = p.Q, C = p.C;
+    const int tid = threadIdx.x, Q = p.Q, C = p.C4;   // cosets of the 4096-point decomposition
     const int64_t N_s = p.N_s, R = p.R, M = p.M, N_tau = p.N_tau;
     const uint64_t N = (uint64_t)p.N_FFT, mask = N - 1;
     constexpr uint32_t ESZ = BF16 ? 4 : 8;
@@ -347,9 +347,9 @@ segpair_tma_kernel(DevParams p, TmaWork q, const void* __restrict__ ab, const fl
         for (int r = 0; r < SLP; ++r)
             if (tid + NSL * r <= q.mmax) accm[tid + NSL * r] = accP[r];
         __syncthreads();
-        const int o = __ldg(p.coset_off + c), nbc = __ldg(p.coset_off + c + 1) - o;
+        const int o = __ldg(p.coset4_off + c), nbc = __ldg(p.coset4_off + c + 1) - o;
         float* outp = raw + ((size_t)t * 2 * q.n_chunks + (size_t)w * q.n_chunks + chunk) * p.N_f;
-        for (int i = tid; i < nbc; i += TT_THREADS) outp[__ldg(p.coset_k + o + i)] = accm[__ldg(p.coset_m + o + i)];
+        for (int i = tid; i < nbc; i += TT_THREADS) outp[__ldg(p.coset4_k + o + i)] = accm[__ldg(p.coset4_m + o + i)];
         // the next unit's first pass rewrites Y: the unit fetch's barrier orders it
     }
 }
@@ -371,7 +371,7 @@ fold_kernel(DevParams p, const void* __restrict__ ab, const float4* __restrict__
     const int64_t K = blockIdx.x;
     const int X = blockIdx.y >> 1, w = blockIdx.y & 1;
     const int64_t t = blockIdx.z;
-    const int Q = p.Q, C = p.C, tid = threadIdx.x;
+    const int Q = p.Q, C = p.C4, tid = threadIdx.x;
     const int64_t N_s = p.N_s, M = p.M;
     const float4 nm = norm[((size_t)t * Q + X) * M + K];
     if (!(nm.x + nm.y > 0.f)) return;   // no weight in the segment: the row is never read
@@ -467,7 +467,7 @@ size_t al128(size_t b) { return (b + 127) & ~(size_t)127; }
 bool tma_layout(const cc_plan* plan, TmaWork* q, size_t* bytes) {
     const DevParams& p = plan->dp;
     const int esz = p.store == CC_STORE_BF16 ? 4 : 8;
-    q->mmax = (int)((plan->kbar.back() - plan->k0) / p.C);
+    q->mmax = p.C4 > 0 ? (int)((plan->kbar.back() - plan->k0) / p.C4) : TT_L;
     q->folded = p.N_s > TT_L ? 1 : 0;
     q->n_in = q->folded ? TT_L : (int)p.N_s;
     q->stage_bytes = (uint32_t)(q->n_in * esz);
@@ -505,8 +505,10 @@ int occupancy(size_t smem) {
 // samples are folded first (at most FOLD_MAX_F folds and FOLD_MAX_C cosets).
 bool segpair_tma_supported(const cc_plan* plan) {
     const DevParams& p = plan->dp;
-    if (p.L != TT_L || p.Q > 2 || p.R > 1 || p.pair_mode == CC_PAIRS_CROSS_ONLY || plan->N_f < 1) return false;
-    if (p.N_s > TT_L && (p.C > FOLD_MAX_C || (p.N_s + TT_L - 1) / TT_L > FOLD_MAX_F)) return false;
+    const bool padded = p.L < TT_L && plan->tuning.transform_len == TT_L && p.C4 > 0;   // N_s <= L < 4096
+    if ((p.L != TT_L && !padded) || p.Q > 2 || p.R > 1 || p.pair_mode == CC_PAIRS_CROSS_ONLY || plan->N_f < 1)
+        return false;
+    if (p.N_s > TT_L && (p.C4 > FOLD_MAX_C || (p.N_s + TT_L - 1) / TT_L > FOLD_MAX_F)) return false;
     // rows start on 16-byte boundaries for the bulk copies
     if (p.N_s % (p.store == CC_STORE_BF16 ? 4 : 2)) return false;
     TmaWork q;
@@ -523,7 +525,7 @@ int segpair_tma_chunks(const cc_plan* plan, int64_t n_t) {
     int dev = 0, sms = 152;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t per_cta = plan->tuning.chunk_waves > 0 ? plan->tuning.chunk_waves : 24;
-    const int64_t ctas_per_coset = std::max<int64_t>(1, 2 * (int64_t)sms / p.C);
+    const int64_t ctas_per_coset = std::max<int64_t>(1, 2 * (int64_t)sms / p.C4);
     const int64_t want = (per_cta * ctas_per_coset + 2 * n_t - 1) / (2 * n_t);
     const int64_t maxch = std::max<int64_t>(1, p.M / (4 * p.R + 1));
     return (int)std::max<int64_t>(1, std::min<int64_t>({want, maxch, 32767}));
@@ -535,7 +537,7 @@ bool segpair_tma_folded(const cc_plan* plan) { return plan->dp.N_s > TT_L; }
 size_t segpair_tma_fold_bytes(const cc_plan* plan) {
     if (!segpair_tma_folded(plan)) return 0;
     const DevParams& p = plan->dp;
-    return (size_t)p.Q * 2 * p.M * p.C * TT_L * (p.store == CC_STORE_BF16 ? 4 : 8);
+    return (size_t)p.Q * 2 * p.M * p.C4 * TT_L * (p.store == CC_STORE_BF16 ? 4 : 8);
 }
 
 cc_status launch_fold(cc_plan* plan, int64_t n_t, const void* ab, const float4* norm, void* z, cudaStream_t st) {
@@ -543,7 +545,7 @@ cc_status launch_fold(cc_plan* plan, int64_t n_t, const void* ab, const float4* 
     if (n_t > 65535 || p.M > 0x7fffffff) return fail(CC_ERR_UNSUPPORTED, "fold launch size");
     const dim3 grid((unsigned)p.M, (unsigned)(2 * p.Q), (unsigned)n_t);
     const bool bf16 = p.store == CC_STORE_BF16;
-    if (p.C == 64) {
+    if (p.C4 == 64) {
         if (bf16) fold64_kernel<true><<<grid, TT_THREADS, 0, st>>>(p, ab, norm, z);
         else fold64_kernel<false><<<grid, TT_THREADS, 0, st>>>(p, ab, norm, z);
     } else {
@@ -572,8 +574,8 @@ cc_status launch_segpair_tma(cc_plan* plan, const SegPairLayout& lay, int64_t n_
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_fail(e, "device attributes");
-    const int64_t grid = std::min<int64_t>((int64_t)occ * sms, q.units * p.C);
-    if ((e = cudaMemsetAsync(counters, 0, sizeof(int) * p.C, st)) != cudaSuccess)
+    const int64_t grid = std::min<int64_t>((int64_t)occ * sms, q.units * p.C4);
+    if ((e = cudaMemsetAsync(counters, 0, sizeof(int) * p.C4, st)) != cudaSuccess)
         return cuda_fail(e, "unit counters");
     if (bf16)
         segpair_tma_kernel<true><<<(unsigned)grid, TT_THREADS, bytes, st>>>(p, q, ab, norm, raw, counters);

@@ -23,34 +23,40 @@ CHUNK_WAVES = (5, 10, 20, 40, 80)
 
 def autotune(plan: CrossCorrPlan, x, templates, reps: int = 2, chunk_waves: Sequence[int] = CHUNK_WAVES,
              stream=None) -> dict:
-    """Time every (path, chunk_waves) the plan supports on `templates` and keep the fastest.
+    """Time every (path, transform length, chunk split) the plan supports on `templates`
+    and keep the fastest.  The transform length is the tile shape of the two-pass
+    spectrum kernel: the plan's own coset length, or 4096-point cosets (the persistent
+    kernel) with the segments zero-padded when the plan's cosets are shorter.
 
-    Returns {"path", "chunk_waves", "ms"} of the choice and leaves the plan set to it."""
+    Returns {"path", "transform_len", "chunk_waves", "ms"} of the choice and leaves the
+    plan set to it."""
     import torch
     stream = stream or torch.cuda.current_stream()
     rho = torch.empty((templates.shape[0], plan.N_f), dtype=torch.float32, device=templates.device)
     best = None
+    lens = (0, 4096) if plan.info["L"] < 4096 <= plan.info["N_FFT"] else (0,)
     for path in (PATH_TWO_PASS, PATH_FUSED):
         try:
             plan.set_path(path)
         except CrossCorrError:
             continue
-        for w in chunk_waves:
-            plan.set_tuning(chunk_waves=w)
-            plan.search(x, templates, rho, stream=stream)        # warm-up (workspace, caches)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(reps):
-                plan.search(x, templates, rho, stream=stream)
-            e1.record(stream)
-            e1.synchronize()
-            ms = e0.elapsed_time(e1) / reps
-            if best is None or ms < best["ms"]:
-                best = {"path": path, "chunk_waves": w, "ms": ms}
+        for tl in (lens if path == PATH_TWO_PASS else (0,)):
+            for w in chunk_waves:
+                plan.set_tuning(chunk_waves=w, transform_len=tl)
+                plan.search(x, templates, rho, stream=stream)        # warm-up (workspace, caches)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(reps):
+                    plan.search(x, templates, rho, stream=stream)
+                e1.record(stream)
+                e1.synchronize()
+                ms = e0.elapsed_time(e1) / reps
+                if best is None or ms < best["ms"]:
+                    best = {"path": path, "transform_len": tl, "chunk_waves": w, "ms": ms}
     if best is None:
         raise CrossCorrError("crosscorr_plan_set_path", 5)
     plan.set_path(best["path"])
-    plan.set_tuning(chunk_waves=best["chunk_waves"])
+    plan.set_tuning(chunk_waves=best["chunk_waves"], transform_len=best["transform_len"])
     return best
 
 
@@ -76,7 +82,7 @@ class MultiBandSearch:
             if tune:
                 self.tuning.append(autotune(p, x, t[:tune_templates]))
             else:
-                self.tuning.append({"path": p.search_path, "chunk_waves": 0, "ms": None})
+                self.tuning.append({"path": p.search_path, "transform_len": 0, "chunk_waves": 0, "ms": None})
         # one shared workspace for the whole batch of bands
         need = max(p.workspace_size(t.shape[0]) for p, t in zip(self.plans, self.templates))
         self.workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)

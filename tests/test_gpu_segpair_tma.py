@@ -104,6 +104,36 @@ def test_folded_segments_bf16(name):
     assert_close(got, staged, 3e-3)
 
 
+PADDED = {
+    "L2048": dict(n_samples=1800 * 12, T_max=1800.0, T_short=1800.0),
+    "L1024": dict(n_samples=900 * 24, T_max=900.0, T_short=900.0, T_sft=300.0),
+    "L512": dict(n_samples=480 * 40, T_max=480.0, T_short=480.0, T_sft=240.0),
+    "L2048_R0": dict(n_samples=2000 * 10, T_max=0.0, T_short=2000.0, T_sft=400.0),
+    "L2048_Q1_all_ordered": dict(n_samples=1800 * 12, T_max=1800.0, T_short=1800.0, n_det=1, pair_mode=2),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PADDED))
+def test_shorter_cosets_padded_to_4096(name):
+    """A plan whose own coset length is below 4096 (segments of at most 2048 samples) takes
+    the persistent kernel's 4096-point cosets when tuned to (transform_len = 4096): the
+    segments are zero-padded, fewer cosets cover the band.  Both tilings match the oracle."""
+    kw = dict(BASE)
+    kw.update(PADDED[name])
+    ds = synth.tiny(seed=47, n_templates=3, **kw)
+    ref = oracle.rho(ds)
+    with cc.CrossCorrPlan(ds.cfg, ds.dets) as plan:
+        assert plan.info["L"] < 4096 <= plan.info["N_FFT"] and plan.search_path == cc.PATH_TWO_PASS
+        x = torch.from_numpy(ds.x64).to(DEV)
+        tm = torch.from_numpy(ds.templates).to(DEV)
+        own = plan.search(x, tm).cpu().numpy().astype(np.float64)
+        plan.set_tuning(transform_len=4096)
+        padded = plan.search(x, tm).cpu().numpy().astype(np.float64)
+        plan.check()
+    assert_close(own, ref, 1e-4)
+    assert_close(padded, ref, 1e-4)
+
+
 def test_coset4096_loud_injection_topk():
     """A loud injection on a template of the batch: the top-10 (template, bin) list equals
     the oracle's."""
