@@ -350,6 +350,13 @@ cc_status crosscorr_lattice(const double* g, double mu, const double* lo, const 
  * check.  No counterpart in the paper: error reporting of this implementation. */
 cc_status crosscorr_plan_check(cc_plan* plan, void* stream);
 
+/* Diagnostic for the bounded waits (no counterpart in the paper): with on != 0, every CTA
+ * of the persistent spectrum kernel leaves the bulk copy of its first transform unissued,
+ * so that wait runs out after about one second; the CTA records the timeout and returns
+ * (no fault, no hang) and crosscorr_plan_check then reports CC_ERR_TIMEOUT.  The rho of
+ * such a search is invalid.  Off (0) by default; for tests of the error path. */
+cc_status crosscorr_plan_set_wait_test(cc_plan* plan, int on);
+
 /* The k largest rho over (template, bin) of a device float[n_t][N_f] array,
  * descending, ties by (template, bin) ascending; hits_host receives
  * min(k, n_t*N_f) records.  Synchronises the stream.  1 <= k <= 4096.

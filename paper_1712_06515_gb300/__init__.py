@@ -340,6 +340,11 @@ class CrossCorrPlan:
         the last check (the rho of those searches is then invalid)."""
         check("crosscorr_plan_check", self._lib.crosscorr_plan_check(self._h, _stream_handle(stream)))
 
+    def set_wait_test(self, on: bool = True):
+        """Diagnostic: make the persistent kernel's first bounded wait in every CTA run out
+        (tests of the timeout path; the search's rho is then invalid)."""
+        check("crosscorr_plan_set_wait_test", self._lib.crosscorr_plan_set_wait_test(self._h, int(on)))
+
     def topk(self, rho, k, stream=None):
         """k best (template, bin, freq, rho), descending, ties by (template, bin)."""
         import torch

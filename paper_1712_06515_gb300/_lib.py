@@ -146,6 +146,7 @@ SIGNATURES = {
     "crosscorr_plan_search_path": (c_int, [c_void_p, POINTER(c_int)]),
     "crosscorr_plan_kernel_time": (c_int, [c_void_p, POINTER(c_double), POINTER(c_int64)]),
     "crosscorr_plan_check": (c_int, [c_void_p, c_void_p]),
+    "crosscorr_plan_set_wait_test": (c_int, [c_void_p, c_int]),
     "crosscorr_measure_fp32_peak": (c_int, [POINTER(c_double), c_void_p]),
 }
 

@@ -76,6 +76,7 @@ struct DevParams {
     const int* coset4_k;
     const int* coset4_m;
     unsigned* err;                   // device error word: bit 0 set by a kernel whose bounded wait ran out
+    int wait_test;                   // crosscorr_plan_set_wait_test: skip each CTA's first bulk copy
     const float* ltaps;              // [LEARNED_NODES][LEARNED_TAPS] learned taps (null until set)
     float ham[MAX_TAPS];             // Hamming window, 2D+1 taps
 };

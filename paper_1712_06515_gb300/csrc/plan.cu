@@ -168,6 +168,12 @@ cc_status crosscorr_plan_kernel_time(cc_plan* plan, double* ms, int64_t* launche
     return CC_OK;
 }
 
+cc_status crosscorr_plan_set_wait_test(cc_plan* plan, int on) {
+    if (!plan) return cc::fail(CC_ERR_INVALID, "plan is null");
+    plan->dp.wait_test = on != 0;
+    return CC_OK;
+}
+
 cc_status crosscorr_plan_check(cc_plan* plan, void* stream) {
     if (!plan) return cc::fail(CC_ERR_INVALID, "plan is null");
     cudaStream_t st = (cudaStream_t)stream;

@@ -176,3 +176,26 @@ def test_coset4096_repeatable_and_split_independent():
             got = plan.search(x, tm).cpu().numpy()
             assert np.abs(got - staged).max() <= lim, waves
         plan.check()
+
+
+def test_bounded_wait_runs_out_reports_timeout_and_context_survives():
+    """The persistent kernel bounds every wait on its bulk copies (about one second of
+    clock).  With the wait test on, each CTA's first copy is never issued: the wait runs
+    out, the CTA records it and returns, crosscorr_plan_check raises CC_ERR_TIMEOUT once,
+    and the next search on the same context gives the same bits as before."""
+    ds = case("R1")
+    with cc.CrossCorrPlan(ds.cfg, ds.dets) as plan:
+        x = torch.from_numpy(ds.x64).to(DEV)
+        tm = torch.from_numpy(ds.templates).to(DEV)
+        good = plan.search(x, tm).cpu().numpy()
+        plan.check()
+        plan.set_wait_test(True)
+        plan.search(x, tm)
+        with pytest.raises(cc.CrossCorrError) as e:
+            plan.check()
+        assert e.value.status == 4   # CC_ERR_TIMEOUT
+        plan.check()                 # the error word was cleared
+        plan.set_wait_test(False)
+        again = plan.search(x, tm).cpu().numpy()
+        plan.check()
+    assert np.array_equal(again, good)
