@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "crosscorr.h"
 
 namespace cc {
@@ -159,6 +161,16 @@ struct cc_plan {
 };
 
 namespace cc {
+
+// An NVTX range over one C-ABI call (named in Nsight timelines; without a profiler
+// attached the push and pop return at once).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define CC_NVTX_RANGE(name) ::cc::NvtxRange cc_nvtx_range_(name)
 
 // ---------------------------------------------------------------------------
 // Host helpers (plan.cu)

@@ -246,6 +246,7 @@ using namespace cc;
 
 extern "C" cc_status crosscorr_demod_prepare(cc_plan* plan, const void* const* x_dev, int32_t n_bin,
                                              double doppler_max, void* stream) {
+    CC_NVTX_RANGE("crosscorr_demod_prepare");
     if (!plan) return fail(CC_ERR_INVALID, "plan is null");
     if (n_bin != 2) return fail(CC_ERR_UNSUPPORTED, "demodulation search implemented for n_bin = 2");
     if (!(doppler_max >= 0) || doppler_max > 0.01) return fail(CC_ERR_INVALID, "doppler_max must be in [0, 0.01]");
@@ -325,6 +326,7 @@ extern "C" cc_status crosscorr_demod_prepare(cc_plan* plan, const void* const* x
 
 extern "C" cc_status crosscorr_demod_search(cc_plan* plan, const cc_template* t_dev, int64_t n_t, float* rho_dev,
                                             void* stream) {
+    CC_NVTX_RANGE("crosscorr_demod_search");
     if (!plan) return fail(CC_ERR_INVALID, "plan is null");
     if (n_t < 0) return fail(CC_ERR_INVALID, "n_t must be >= 0");
     if (!plan->demod_ready) return fail(CC_ERR_INVALID, "call crosscorr_demod_prepare first");

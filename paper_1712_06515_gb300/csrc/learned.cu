@@ -58,6 +58,7 @@ learned_taps_kernel(const uint16_t* __restrict__ wbits, float nu_feat, float* __
 }  // namespace cc
 
 extern "C" cc_status crosscorr_plan_set_learned_interp(cc_plan* plan, const cc_learned_interp* li) {
+    CC_NVTX_RANGE("crosscorr_plan_set_learned_interp");
     using namespace cc;
     if (!plan || !li) return fail(CC_ERR_INVALID, "null argument to crosscorr_plan_set_learned_interp");
     if (plan->cfg.interp != CC_INTERP_LEARNED)

@@ -175,6 +175,7 @@ cc_status crosscorr_plan_set_wait_test(cc_plan* plan, int on) {
 }
 
 cc_status crosscorr_plan_check(cc_plan* plan, void* stream) {
+    CC_NVTX_RANGE("crosscorr_plan_check");
     if (!plan) return cc::fail(CC_ERR_INVALID, "plan is null");
     cudaStream_t st = (cudaStream_t)stream;
     unsigned h = 0;
@@ -203,6 +204,7 @@ void crosscorr_plan_destroy(cc_plan* p) {
 }
 
 cc_status crosscorr_plan(const cc_config* cfg, const cc_detector* dets, cc_plan** out) {
+    CC_NVTX_RANGE("crosscorr_plan");
     using cc::fail;
     if (!cfg || !dets || !out) return fail(CC_ERR_INVALID, "null argument to crosscorr_plan");
     *out = nullptr;

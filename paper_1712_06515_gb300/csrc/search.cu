@@ -100,6 +100,7 @@ extern "C" cc_status crosscorr_plan_search_path(const cc_plan* plan, int* path) 
 
 extern "C" cc_status crosscorr_search(cc_plan* plan, const void* const* x_dev, const cc_template* t_dev,
                                       int64_t n_t, float* rho_dev, void* stream) {
+    CC_NVTX_RANGE("crosscorr_search");
     using namespace cc;
     if (!plan) return fail(CC_ERR_INVALID, "plan is null");
     if (n_t < 0) return fail(CC_ERR_INVALID, "n_t must be >= 0");

@@ -202,6 +202,7 @@ bool factor_radices(int64_t n, Radices* rad) {
 extern "C" cc_status crosscorr_sfts_to_series(const void* band_dev, const int64_t* block_sft_dev, int64_t n_blocks,
                                               int64_t n_prime, double T_sft, double f_h, void* x_dev,
                                               void* stream) {
+    CC_NVTX_RANGE("crosscorr_sfts_to_series");
     using namespace cc;
     if (n_blocks < 0 || n_prime < 1 || n_prime > 16384 || !(T_sft > 0) || !std::isfinite(T_sft) ||
         !std::isfinite(f_h))

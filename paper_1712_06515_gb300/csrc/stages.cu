@@ -614,6 +614,7 @@ extern "C" {
 
 cc_status crosscorr_resample(cc_plan* plan, const void* const* x_dev, const cc_template* t_dev,
                              int64_t n_t, void* ab_dev, float* norm_dev, void* stream) {
+    CC_NVTX_RANGE("crosscorr_resample");
     using namespace cc;
     if (!plan) return fail(CC_ERR_INVALID, "plan is null");
     if (n_t < 0) return fail(CC_ERR_INVALID, "n_t must be >= 0");
@@ -637,6 +638,7 @@ cc_status crosscorr_resample(cc_plan* plan, const void* const* x_dev, const cc_t
 
 cc_status crosscorr_segment_fft(cc_plan* plan, const void* ab_dev, int64_t n_t, void* F_dev,
                                 void* stream) {
+    CC_NVTX_RANGE("crosscorr_segment_fft");
     using namespace cc;
     if (!plan) return fail(CC_ERR_INVALID, "plan is null");
     if (n_t < 0) return fail(CC_ERR_INVALID, "n_t must be >= 0");
@@ -648,6 +650,7 @@ cc_status crosscorr_segment_fft(cc_plan* plan, const void* ab_dev, int64_t n_t, 
 
 cc_status crosscorr_pair_accumulate(cc_plan* plan, const void* F_dev, const float* norm_dev,
                                     int64_t n_t, float* rho_dev, void* stream) {
+    CC_NVTX_RANGE("crosscorr_pair_accumulate");
     using namespace cc;
     if (!plan) return fail(CC_ERR_INVALID, "plan is null");
     if (n_t < 0) return fail(CC_ERR_INVALID, "n_t must be >= 0");

@@ -132,6 +132,7 @@ topk_pass2(const float* __restrict__ cv, const long long* __restrict__ ci, long 
 
 extern "C" cc_status crosscorr_rho_topk(cc_plan* plan, const float* rho_dev, int64_t n_t, int k,
                                         cc_hit* hits_host, void* stream) {
+    CC_NVTX_RANGE("crosscorr_rho_topk");
     using namespace cc;
     if (!plan) return fail(CC_ERR_INVALID, "plan is null");
     if (n_t < 0 || k < 1 || k > TOPK_MAX) return fail(CC_ERR_INVALID, "need n_t >= 0 and 1 <= k <= 4096");
