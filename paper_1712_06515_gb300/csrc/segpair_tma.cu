@@ -416,9 +416,10 @@ fold_kernel(DevParams p, const void* __restrict__ ab, const float4* __restrict__
 // and f = f1 + 8 f2, W_64^(q f) = W_8^(v f1) W_64^(u f1) W_8^(u f2), so
 // Z_(u+8v) = DFT8_v[ W_64^(u f1) (a_(f1) + a_(f1+8) W_8^u) ]: per residue u a twiddle and
 // one register 8-point DFT instead of 64 x F products.
-template <bool BF16>
-__global__ void __launch_bounds__(TT_THREADS)
+template <bool BF16, int MAXF>
+__global__ void __launch_bounds__(TT_THREADS, 3)
 fold64_kernel(DevParams p, const void* __restrict__ ab, const float4* __restrict__ norm, void* __restrict__ z) {
+    static_assert(MAXF > 8 && MAXF <= 16, "folds f = f1 + 8 f2 with f2 < 2");
     __shared__ float2 w64[64];   // W_64^n = W_4096^(64 n)
     constexpr int L = TT_L, C = 64;
     const int64_t K = blockIdx.x;
@@ -435,9 +436,9 @@ fold64_kernel(DevParams p, const void* __restrict__ ab, const float4* __restrict
     const size_t zrow = ((((size_t)t * Q + X) * 2 + w) * M + K) * C * L;
     for (int i = 0; i < L / TT_THREADS; ++i) {
         const int pp = tid + TT_THREADS * i;
-        float2 a[16];
+        float2 a[MAXF];
 #pragma unroll
-        for (int f = 0; f < 16; ++f) {
+        for (int f = 0; f < MAXF; ++f) {
             const int64_t sidx = pp + (int64_t)f * L;
             a[f] = make_float2(0.f, 0.f);
             if (f < F && sidx < N_s) {
@@ -451,7 +452,7 @@ fold64_kernel(DevParams p, const void* __restrict__ ab, const float4* __restrict
 #pragma unroll
             for (int f1 = 0; f1 < 8; ++f1) {
                 float2 b = a[f1];
-                if (f1 + 8 < F) b = cadd(b, u == 0 ? a[f1 + 8] : cmul(a[f1 + 8], w64[8 * u]));
+                if (f1 + 8 < MAXF && f1 + 8 < F) b = cadd(b, u == 0 ? a[f1 + 8] : cmul(a[f1 + 8], w64[8 * u]));
                 v[f1] = (u == 0 || f1 == 0) ? b : cmul(b, w64[(u * f1) & 63]);
             }
             dft8(v);   // v[j] = sum_f1 W_8^(j f1) (...): Z_(u + 8 j)
@@ -548,9 +549,13 @@ cc_status launch_fold(cc_plan* plan, int64_t n_t, const void* ab, const float4* 
     if (n_t > 65535 || p.M > 0x7fffffff) return fail(CC_ERR_UNSUPPORTED, "fold launch size");
     const dim3 grid((unsigned)p.M, (unsigned)(2 * p.Q), (unsigned)n_t);
     const bool bf16 = p.store == CC_STORE_BF16;
-    if (p.C4 == 64) {
-        if (bf16) fold64_kernel<true><<<grid, TT_THREADS, 0, st>>>(p, ab, norm, z);
-        else fold64_kernel<false><<<grid, TT_THREADS, 0, st>>>(p, ab, norm, z);
+    const int64_t F = (p.N_s + TT_L - 1) / TT_L;
+    if (p.C4 == 64 && F <= 9) {   // the long-lag band: nine folds
+        if (bf16) fold64_kernel<true, 9><<<grid, TT_THREADS, 0, st>>>(p, ab, norm, z);
+        else fold64_kernel<false, 9><<<grid, TT_THREADS, 0, st>>>(p, ab, norm, z);
+    } else if (p.C4 == 64) {
+        if (bf16) fold64_kernel<true, 16><<<grid, TT_THREADS, 0, st>>>(p, ab, norm, z);
+        else fold64_kernel<false, 16><<<grid, TT_THREADS, 0, st>>>(p, ab, norm, z);
     } else {
         if (bf16) fold_kernel<true><<<grid, TT_THREADS, 0, st>>>(p, ab, norm, z);
         else fold_kernel<false><<<grid, TT_THREADS, 0, st>>>(p, ab, norm, z);
