@@ -64,6 +64,9 @@ constexpr int SS_MAX_PASSES = 16;
 struct Radices {
     int n;
     int r[SS_MAX_PASSES];
+    int ns[SS_MAX_PASSES];        // product of the earlier radices
+    uint32_t nsm[SS_MAX_PASSES];  // floor(j / ns) = (j nsm) >> nss (magic_for)
+    int nss[SS_MAX_PASSES];
 };
 
 constexpr float kC3 = 0.866025403784438647f;    // sin(2 pi / 3)
@@ -111,9 +114,11 @@ __device__ __forceinline__ void dft_small(float2 (&v)[5], int R) {
     }
 }
 
-// `groups` T_sft blocks per CTA, one group of blockDim.x / groups threads each (the
-// passes and barriers are common to the CTA); twf: forward twiddles exp(-2 pi i e / N').
+// `groups` T_sft blocks per CTA, one group of blockDim.x / groups threads each;
+// twf: forward twiddles exp(-2 pi i e / N').  WARP: each group is one warp and its passes
+// synchronise the warp alone; otherwise the CTA's barriers order every group's passes.
 // A gap block's group writes zeros and idles through the passes.
+template <bool WARP>
 __global__ void __launch_bounds__(SS_THREADS)
 sft_fft_kernel(const float2* __restrict__ band, const int64_t* __restrict__ block_sft, int64_t n_blocks,
                int n_prime, double T_sft, double f_h, const float2* __restrict__ twf, Radices rad, int groups,
@@ -137,12 +142,17 @@ sft_fft_kernel(const float2* __restrict__ band, const int64_t* __restrict__ bloc
             src[m] = make_float2(z.x, -z.y);   // conjugated band
         }
     }
-    __syncthreads();
-    int ns = 1;
+    auto sync = [] {
+        if constexpr (WARP) __syncwarp();
+        else __syncthreads();
+    };
+    sync();
     for (int p = 0; p < rad.n; ++p) {
-        const int R = rad.r[p], nb = n_prime / R, tstep = n_prime / (ns * R);
+        const int R = rad.r[p], ns = rad.ns[p], nb = n_prime / R, tstep = n_prime / (ns * R);
+        const uint32_t nsm = rad.nsm[p];
+        const int nss = rad.nss[p];
         for (int j = tid; work && j < nb; j += nt) {
-            const int k = j % ns;
+            const int k = j - (int)(((uint64_t)(uint32_t)j * nsm) >> nss) * ns;   // j mod ns
             float2 v[5];
 #pragma unroll
             for (int r = 0; r < 5; ++r)
@@ -161,11 +171,10 @@ sft_fft_kernel(const float2* __restrict__ band, const int64_t* __restrict__ bloc
             for (int r = 0; r < 5; ++r)
                 if (r < R) d[r * ns] = v[r];
         }
-        __syncthreads();
+        sync();
         float2* t = src;
         src = dst;
         dst = t;
-        ns *= R;
     }
     if (!work) return;
     // SFT-start phase in FP64, reduced to cycles; output (-1)^j conj(X_j) / T_sft times it
@@ -186,10 +195,14 @@ sft_fft_kernel(const float2* __restrict__ band, const int64_t* __restrict__ bloc
 bool factor_radices(int64_t n, Radices* rad) {
     rad->n = 0;
     int64_t m = n;
+    int ns = 1;
     for (int R : {4, 2, 3, 5}) {
         while (m % R == 0) {
             if (rad->n == SS_MAX_PASSES) return false;
+            rad->ns[rad->n] = ns;
+            magic_for((uint32_t)ns, &rad->nsm[rad->n], &rad->nss[rad->n]);
             rad->r[rad->n++] = R;
+            ns *= R;
             m /= R;
         }
     }
@@ -229,25 +242,26 @@ extern "C" cc_status crosscorr_sfts_to_series(const void* band_dev, const int64_
         return cuda_fail(e, "sfts_to_series twiddles");
     }
     if (fft) {
-        // per block a group of threads (a quarter of the widest pass's butterflies, whole
-        // warps, at most 256) and two N'-point buffers; as many blocks per 256-thread CTA
-        // as fit in 48 KB of shared memory
+        // two N'-point buffers per block.  Up to 1536 points: one warp per block, as many
+        // blocks per CTA as fit in 48 KB (at most 8); larger N': one block per CTA, a group
+        // of up to 256 threads (a quarter of the widest pass's butterflies)
+        const size_t per = 2 * sizeof(float2) * n_prime;
+        const bool warp = n_prime <= 1536;
         int rmin = 5;
         for (int i = 0; i < rad.n; ++i) rmin = std::min(rmin, rad.r[i]);
-        const int gs = (int)std::min<int64_t>(SS_THREADS, std::max<int64_t>(32, ((n_prime / rmin / 4 + 31) / 32) * 32));
-        const size_t per = 2 * sizeof(float2) * n_prime;
-        const int groups = (int)std::max<int64_t>(1, std::min<int64_t>(SS_THREADS / gs, (48 * 1024) / per));
+        const int gs = warp ? 32 : (int)std::min<int64_t>(SS_THREADS, std::max<int64_t>(32, ((n_prime / rmin / 4 + 31) / 32) * 32));
+        const int groups = warp ? (int)std::max<int64_t>(1, std::min<int64_t>(SS_THREADS / 32, (48 * 1024) / per)) : 1;
         const size_t smem = per * groups;
+        auto kern = warp ? sft_fft_kernel<true> : sft_fft_kernel<false>;
         if (smem > 48 * 1024 &&
-            (e = cudaFuncSetAttribute(sft_fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-                cudaSuccess) {
+            (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) {
             cudaFreeAsync(tw_dev, st);
             return cuda_fail(e, "sfts_to_series smem attribute");
         }
         const int64_t ctas = (n_blocks + groups - 1) / groups;
-        sft_fft_kernel<<<(unsigned)ctas, gs * groups, smem, st>>>((const float2*)band_dev, block_sft_dev, n_blocks,
-                                                                  (int)n_prime, T_sft, f_h, tw_dev, rad, groups,
-                                                                  (float2*)x_dev);
+        kern<<<(unsigned)ctas, gs * groups, smem, st>>>((const float2*)band_dev, block_sft_dev, n_blocks,
+                                                        (int)n_prime, T_sft, f_h, tw_dev, rad, groups,
+                                                        (float2*)x_dev);
     } else {
         const size_t smem = sizeof(float2) * n_prime;
         if (smem > 48 * 1024 &&
