@@ -64,6 +64,8 @@ def parse():
                     help="resampled: the paper's method (default); demod: the detector-frame "
                          "statistic it replaces, on the same workload, for the speed comparison; "
                          "sft_series: the SFT-to-series input preparation of the 120-day band")
+    ap.add_argument("--demod-form", default="pairs", choices=["pairs", "separable"],
+                    help="demod: the method's pair loop (default) or the separable window-sum form")
     ap.add_argument("--pair-mode", default="unordered", choices=["unordered", "all_ordered"],
                     help="pair set: each unordered pair once (default) or every ordered pair with "
                          "auto-correlation (the F-statistic limit)")
@@ -914,7 +916,8 @@ def run_multiband(args):
 
 def run_demod(args):
     """The detector-frame (demodulation) statistic on the o1_band workload: SFTs once, then
-    a step = crosscorr_demod_search over the template batch (the pair loop of the method)."""
+    a step = crosscorr_demod_search over the template batch (the pair loop of the method, or
+    with --demod-form separable the same rho from running window sums)."""
     import torch
     import synth
     import paper_1712_06515_gb300 as cc
@@ -932,6 +935,8 @@ def run_demod(args):
     e1.record(stream)
     torch.cuda.synchronize()
     sft_ms = e0.elapsed_time(e1)
+    separable = args.demod_form == "separable"
+    plan.set_demod_form(separable)
     rho = torch.empty((B, plan.N_f), dtype=torch.float32, device=dev)
     for _ in range(args.warmup):
         plan.demod_search(tm, rho)
@@ -972,6 +977,11 @@ def run_demod(args):
     # product, the normalisation term, two accumulations) and 30 per locked SFT (two
     # sinc-weighted bins, the phase and its rotation, Xi^2)
     flops_tb = 12.0 * pairs + 30.0 * locked
+    if separable:
+        # the same 30 per locked SFT for its bin, plus 53 for the factored pair and
+        # normalisation terms and the running sums of its block, and 14 per SFT for the
+        # window update (28 per block of two detectors): no per-pair term
+        flops_tb = (30.0 + 53.0 + 14.0) * locked
     clk_max = float((clk or {}).get("sm_max_mhz") or 2070.0)
     peak = SM_COUNT * FP32_LANES * 2 * clk_max * 1e6 / 1e12
     achieved = flops_tb * units / (pair_ms / 1e3) / 1e12 if pair_ms > 0 else None
@@ -981,8 +991,9 @@ def run_demod(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "o1_band: 2 det, 120 d at 60% duty, 0.5 Hz at 150 Hz, T_sft=360 s SFTs, "
                                "T_max=3600 s", "method": "detector-frame (demodulation) CrossCorr, n_bin=2",
-                   "templates_per_step": B, "locked_sfts": locked, "sft_pairs": pairs, "sft_ms_once": sft_ms},
-        "roofline": {"bound": "alu", "kernel": "demod_pair_kernel", "achieved": achieved, "peak": peak,
+                   "demod_form": args.demod_form, "templates_per_step": B, "locked_sfts": locked, "sft_pairs": pairs, "sft_ms_once": sft_ms},
+        "roofline": {"bound": "alu", "kernel": "demod_sep_kernel" if separable else "demod_pair_kernel",
+                     "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak if achieved else None, "traffic": None,
                      "peak_kind": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 flop x {clk_max:g} MHz",
                      "flops_per_template_bin": flops_tb, "kernel_ms_per_launch": pair_ms / max(1, pair_launches),

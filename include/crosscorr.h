@@ -311,6 +311,16 @@ cc_status crosscorr_demod_prepare(cc_plan* plan, const void* const* x_dev, int32
 cc_status crosscorr_demod_search(cc_plan* plan, const cc_template* t_dev, int64_t n_t, float* rho_dev,
                                  void* stream);
 
+/* How crosscorr_demod_search sums the pairs (the same rho up to FP32 rounding):
+ *   CC_DEMOD_PAIRS      the method's pair loop, one term per partner SFT (the default; its
+ *                       cost per pair is what the paper's comparison with resampling rests on);
+ *   CC_DEMOD_SEPARABLE  the geometric filter Gamma_KL = (a^_K a^_L + b^_K b^_L)/10 factored
+ *                       into running window sums of a^_L y_L, b^_L y_L and Xi_L^2-weighted
+ *                       a^_L^2, a^_L b^_L, b^_L^2: O(1) per SFT.  An algebraic rearrangement
+ *                       of Eqs. geometric-filter and textbook-cc-rho, not a form the paper uses. */
+enum { CC_DEMOD_PAIRS = 0, CC_DEMOD_SEPARABLE = 1 };
+cc_status crosscorr_plan_set_demod_form(cc_plan* plan, int form);
+
 /* Input preparation (Appendix B): the heterodyned, downsampled series the search starts
  * from, built from short Fourier transforms.  band_dev: device complex64 [n_sft][n_prime],
  * the SFT bins k_h - n_prime/2 .. k_h + n_prime/2 - 1 of each SFT (DFT times dt, Eq.

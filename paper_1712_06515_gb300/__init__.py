@@ -313,6 +313,11 @@ class CrossCorrPlan:
         check("crosscorr_demod_prepare", self._lib.crosscorr_demod_prepare(
             self._h, xp, int(n_bin), float(doppler_max), _stream_handle(stream)))
 
+    def set_demod_form(self, separable: bool):
+        """Pair sum of demod_search: the method's pair loop (default) or the separable
+        window-sum form (the same rho up to FP32 rounding)."""
+        check("crosscorr_plan_set_demod_form", self._lib.crosscorr_plan_set_demod_form(self._h, int(bool(separable))))
+
     def demod_search(self, templates, rho=None, stream=None):
         """Detector-frame (demodulation) rho [n_t, N_f] at the plan's output frequencies."""
         import torch

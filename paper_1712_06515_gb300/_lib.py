@@ -140,6 +140,7 @@ SIGNATURES = {
     "crosscorr_sfts_to_series": (c_int, [c_void_p, c_void_p, c_int64, c_int64, c_double, c_double, c_void_p,
                                          c_void_p]),
     "crosscorr_demod_search": (c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p]),
+    "crosscorr_plan_set_demod_form": (c_int, [c_void_p, c_int]),
     "crosscorr_plan_set_workspace": (c_int, [c_void_p, c_void_p, c_size_t]),
     "crosscorr_plan_workspace_size": (c_int, [c_void_p, c_int64, POINTER(c_size_t)]),
     "crosscorr_plan_set_tuning": (c_int, [c_void_p, POINTER(CcTuning)]),

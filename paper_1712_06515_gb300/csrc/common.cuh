@@ -152,6 +152,7 @@ struct cc_plan {
     void* demod_df = nullptr;                 // [N_f] double: f - f_h of the output bins
     void* demod_kbar = nullptr;               // [N_f] int64
     bool demod_ready = false;
+    int demod_form = CC_DEMOD_PAIRS;          // crosscorr_plan_set_demod_form
     int demod_nsft = 0, demod_m_lo = 0, demod_nbins = 0, demod_nblk = 0;
     // workspace (grown on demand by staged/fused paths)
     void* ws = nullptr;

@@ -28,6 +28,7 @@ namespace {
 constexpr int SFT_THREADS = 256;
 constexpr int DM_MAX_SFT_SAMPLES = 16384;   // T_sft / dt staged in shared memory
 constexpr size_t DM_RING_BUDGET = 160 * 1024;
+constexpr size_t DM_SEP_RING = 40 * 1024;   // separable form: block-sum ring per CTA (R_s <= 10)
 
 struct DemodTiming {   // per (template, detector, SFT block): 32 bytes
     float A0, A1;       // signal bin position x = A0 + df A1 (df = f - f_h of the output bin)
@@ -239,6 +240,174 @@ __global__ void demod_pair_kernel(DevParams p, int nsft, int m_lo, int nbins, in
     if (act) rho[(size_t)t * p.N_f + k] = den > 0.f ? raw / sqrtf(2.f * den) : 0.f;
 }
 
+// The same statistic in separable form.  The geometric filter Gamma_KL = (a^_K a^_L +
+// b^_K b^_L) / 10 splits into a factor of K times one of L, so the pair sum of SFT K over
+// its partners L is 2 Re(conj(y_K) (a^_K SA + b^_K SB)) / 10 with SA = sum_L a^_L y_L and
+// SB = sum_L b^_L y_L, and the normalisation term Xi_K^2 (a^_K^2 UAA + 2 a^_K b^_K UAB +
+// b^_K^2 UBB) / 100 with UAA = sum_L Xi_L^2 a^_L^2, UAB = sum_L Xi_L^2 a^_L b^_L,
+// UBB = sum_L Xi_L^2 b^_L^2: O(1) per SFT instead of one term per partner.  The partners
+// of (block l, detector X) are every detector of blocks l - R_s .. l - 1 (window sums W)
+// and the earlier detectors of block l (running sums P).  W moves by adding the finished
+// block's sums s_l and subtracting s_(l - R_s), and is recomputed exactly every few blocks
+// so that rounding cannot drift.  s_(l - R_s) comes from a per-thread ring of block sums in
+// shared memory when R_s is small (RING), otherwise it is recomputed from the SFT bins.
+// Results equal the per-pair loop's up to FP32 rounding.
+struct SepSums {
+    float ayx, ayy, byx, byy, uaa, uab, ubb;
+};
+
+__device__ __forceinline__ void sep_zero(SepSums& a) { a = SepSums{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}; }
+
+__device__ __forceinline__ void sep_axpy(SepSums& a, const SepSums& b, float sg) {
+    a.ayx = fmaf(sg, b.ayx, a.ayx);
+    a.ayy = fmaf(sg, b.ayy, a.ayy);
+    a.byx = fmaf(sg, b.byx, a.byx);
+    a.byy = fmaf(sg, b.byy, a.byy);
+    a.uaa = fmaf(sg, b.uaa, a.uaa);
+    a.uab = fmaf(sg, b.uab, a.uab);
+    a.ubb = fmaf(sg, b.ubb, a.ubb);
+}
+
+// SFT (X, l)'s contribution (a^ y, b^ y, Xi^2 a^^2, Xi^2 a^ b^, Xi^2 b^^2) to the sums
+__device__ __forceinline__ void sep_add_sft(SepSums& a, float2 y, float xi2, float4 wk) {
+    const float xa = xi2 * wk.x, xb = xi2 * wk.y;
+    a.ayx = fmaf(wk.x, y.x, a.ayx);
+    a.ayy = fmaf(wk.x, y.y, a.ayy);
+    a.byx = fmaf(wk.y, y.x, a.byx);
+    a.byy = fmaf(wk.y, y.y, a.byy);
+    a.uaa = fmaf(xa, wk.x, a.uaa);
+    a.uab = fmaf(xa, wk.y, a.uab);
+    a.ubb = fmaf(xb, wk.y, a.ubb);
+}
+
+// The demodulated bin y of template row tr at frequency k (the pair kernel's arithmetic,
+// one SFT at a time) and the weight Xi^2 of its two-bin interpolation.
+__device__ __forceinline__ float2 demod_y(const DemodTiming& tr, float df, float kh, float kl, bool act, int m_lo,
+                                          int nbins, const float2* __restrict__ zrow, float& xi2) {
+    const float x = fmaf(df, tr.A1, tr.A0);
+    const float fm = floorf(x);
+    const float k0 = fm - x;
+    float s0, s1;
+    if (k0 == 0.f) {
+        s0 = 1.f;
+        s1 = 0.f;
+    } else {
+        const float sp = sinpif(k0) * 0.318309886183790672f;
+        s0 = __fdividef(sp, k0);
+        s1 = -__fdividef(sp, k0 + 1.f);
+    }
+    xi2 = s0 * s0 + s1 * s1;
+    const int m0 = (int)fm;
+    const int idx = m0 - m_lo;
+    float2 y = make_float2(0.f, 0.f);
+    if (act && idx >= 0 && idx + 1 < nbins) {
+        const float2 z0 = __ldg(zrow + idx), z1 = __ldg(zrow + idx + 1);
+        const float sg = (m0 & 1) ? -1.f : 1.f;
+        const float2 u = make_float2(sg * (s0 * z0.x - s1 * z1.x), sg * (s0 * z0.y - s1 * z1.y));
+        float cyc = fmaf(kl, tr.C1, fmaf(kh, tr.C128, tr.C0));
+        cyc -= floorf(cyc);
+        float sn, cs;
+        sincospif(2.0f * cyc, &sn, &cs);
+        y = make_float2(fmaf(u.x, cs, u.y * sn), fmaf(u.y, cs, -u.x * sn));
+    }
+    return y;
+}
+
+template <bool RING>
+__global__ void __launch_bounds__(128) demod_sep_kernel(DevParams p, int m_lo, int nbins, int n_blk, int Rs, int refresh,
+                                 const float2* __restrict__ z, const float4* __restrict__ wts,
+                                 const DemodTiming* __restrict__ tq, const double* __restrict__ dfreq,
+                                 const int64_t* __restrict__ kbar, int64_t t_base, float* __restrict__ rho) {
+    extern __shared__ __align__(16) float sring[];     // RING: [R_s + 1][7][nthr] block sums, thread-private
+    const int nthr = blockDim.x, tid = threadIdx.x;
+    const int Q = p.Q;
+    const int64_t t = t_base + blockIdx.y;
+    const int k = blockIdx.x * nthr + tid;
+    const bool act = k < (int)p.N_f;
+    const DemodTiming* trow = tq + (size_t)(t - t_base) * Q * n_blk;
+    if (RING)
+        for (int j = 0; j < (Rs + 1) * 7; ++j) sring[(size_t)j * nthr + tid] = 0.f;
+    const float df = act ? (float)__ldg(dfreq + k) : 0.f;
+    const int64_t kb = act ? __ldg(kbar + k) : 0;
+    const float kh = (float)(kb >> 7), kl = (float)(kb & 127);
+    // sums of one whole block from its SFT bins
+    auto block_sums = [&](int j, SepSums& s) {
+        sep_zero(s);
+        for (int X = 0; X < Q; ++X) {
+            const float4 wk = __ldg(wts + (size_t)X * n_blk + j);
+            if (wk.z == 0.f) continue;
+            float xi2;
+            const float2 y = demod_y(trow[(size_t)X * n_blk + j], df, kh, kl, act, m_lo, nbins,
+                                     z + ((size_t)X * n_blk + j) * nbins, xi2);
+            sep_add_sft(s, y, xi2, wk);
+        }
+    };
+    float raw = 0.f, rawc = 0.f, den = 0.f, denc = 0.f;
+    SepSums W;
+    sep_zero(W);
+    for (int l = 0; l < n_blk; ++l) {
+        SepSums P;
+        sep_zero(P);
+        for (int X = 0; X < Q; ++X) {
+            const float4 wk = __ldg(wts + (size_t)X * n_blk + l);
+            if (wk.z == 0.f) continue;                 // gap: no SFT (the same for the whole CTA)
+            float xi2;
+            const float2 y = demod_y(trow[(size_t)X * n_blk + l], df, kh, kl, act, m_lo, nbins,
+                                     z + ((size_t)X * n_blk + l) * nbins, xi2);
+            const float sax = W.ayx + P.ayx, say = W.ayy + P.ayy, sbx = W.byx + P.byx, sby = W.byy + P.byy;
+            const float gx = fmaf(wk.x, sax, wk.y * sbx), gy = fmaf(wk.x, say, wk.y * sby);
+            const float pr = 0.2f * fmaf(y.x, gx, y.y * gy);          // 2 Re(conj(y) g) / 10
+            const float nq = fmaf(wk.x * wk.x, W.uaa + P.uaa,
+                                  fmaf(2.f * wk.x * wk.y, W.uab + P.uab, wk.y * wk.y * (W.ubb + P.ubb)));
+            kahan_add(raw, rawc, pr);
+            kahan_add(den, denc, 0.01f * xi2 * nq);
+            sep_add_sft(P, y, xi2, wk);
+        }
+        if (Rs == 0) continue;
+        // the window of block l + 1: blocks l + 1 - R_s .. l
+        if (RING) {
+            float* slot = sring + (size_t)(l % (Rs + 1)) * 7 * nthr + tid;
+            const float* old = sring + (size_t)((l + 1) % (Rs + 1)) * 7 * nthr + tid;   // s_(l - R_s)
+            const SepSums so{old[0], old[nthr], old[2 * nthr], old[3 * nthr], old[4 * nthr], old[5 * nthr],
+                             old[6 * nthr]};
+            slot[0] = P.ayx;
+            slot[nthr] = P.ayy;
+            slot[2 * nthr] = P.byx;
+            slot[3 * nthr] = P.byy;
+            slot[4 * nthr] = P.uaa;
+            slot[5 * nthr] = P.uab;
+            slot[6 * nthr] = P.ubb;
+            if ((l + 1) % refresh == 0) {
+                sep_zero(W);
+                for (int j = 0; j <= Rs; ++j) {
+                    if (j == (l + 1) % (Rs + 1)) continue;
+                    const float* r = sring + (size_t)j * 7 * nthr + tid;
+                    const SepSums sj{r[0], r[nthr], r[2 * nthr], r[3 * nthr], r[4 * nthr], r[5 * nthr], r[6 * nthr]};
+                    sep_axpy(W, sj, 1.f);
+                }
+            } else {
+                sep_axpy(W, P, 1.f);
+                sep_axpy(W, so, -1.f);
+            }
+        } else if ((l + 1) % refresh == 0) {
+            W = P;
+            for (int j = max(0, l + 1 - Rs); j < l; ++j) {
+                SepSums sj;
+                block_sums(j, sj);
+                sep_axpy(W, sj, 1.f);
+            }
+        } else {
+            sep_axpy(W, P, 1.f);
+            if (l - Rs >= 0) {
+                SepSums so;
+                block_sums(l - Rs, so);
+                sep_axpy(W, so, -1.f);
+            }
+        }
+    }
+    if (act) rho[(size_t)t * p.N_f + k] = den > 0.f ? raw / sqrtf(2.f * den) : 0.f;
+}
+
 }  // namespace
 }  // namespace cc
 
@@ -324,6 +493,13 @@ extern "C" cc_status crosscorr_demod_prepare(cc_plan* plan, const void* const* x
     return CC_OK;
 }
 
+extern "C" cc_status crosscorr_plan_set_demod_form(cc_plan* plan, int form) {
+    if (!plan) return fail(CC_ERR_INVALID, "plan is null");
+    if (form != CC_DEMOD_PAIRS && form != CC_DEMOD_SEPARABLE) return fail(CC_ERR_INVALID, "unknown demodulation form");
+    plan->demod_form = form;
+    return CC_OK;
+}
+
 extern "C" cc_status crosscorr_demod_search(cc_plan* plan, const cc_template* t_dev, int64_t n_t, float* rho_dev,
                                             void* stream) {
     CC_NVTX_RANGE("crosscorr_demod_search");
@@ -337,10 +513,19 @@ extern "C" cc_status crosscorr_demod_search(cc_plan* plan, const cc_template* t_
     const double Tsft = nsft * plan->cfg.dt;
     const int Rs = (int)std::floor(plan->cfg.T_max / Tsft + 1e-9);
     const int W = (Rs + 1) * p.Q;
-    int nthr = 256;
-    auto ring_bytes = [&](int nt) { return (size_t)W * nt * 12 + (size_t)W * 12 + 64; };
+    const bool sep = plan->demod_form == CC_DEMOD_SEPARABLE;
+    // separable form: 128 threads, the ring of block sums while it stays within DM_SEP_RING
+    const bool sep_ring = sep && (size_t)(Rs + 1) * 7 * 128 * sizeof(float) <= DM_SEP_RING;
+    int nthr = sep ? 128 : 256;
+    auto ring_bytes = [&](int nt) {
+        return sep ? (sep_ring ? (size_t)(Rs + 1) * 7 * nt * sizeof(float) : 0)
+                   : (size_t)W * nt * 12 + (size_t)W * 12 + 64;
+    };
     while (nthr > 32 && ring_bytes(nthr) > DM_RING_BUDGET) nthr /= 2;
     if (ring_bytes(nthr) > DM_RING_BUDGET) return fail(CC_ERR_UNSUPPORTED, "T_max / T_sft too large for the pair ring");
+    // exact window recomputation every `refresh` blocks: each R_s + 1 with the ring (a sum
+    // over the ring), 4 (R_s + 1) without (a recomputation from the bins)
+    const int refresh = sep_ring ? Rs + 1 : 4 * (Rs + 1);
     // timing records for a batch of templates
     const size_t per_t = sizeof(DemodTiming) * (size_t)p.Q * n_blk;
     const int64_t batch = std::max<int64_t>(1, std::min<int64_t>({n_t, (int64_t)((size_t)2 << 30) / (int64_t)per_t, 65535}));
@@ -350,8 +535,8 @@ extern "C" cc_status crosscorr_demod_search(cc_plan* plan, const cc_template* t_
     cudaError_t e;
     const size_t smem = ring_bytes(nthr);
     if (smem > 48 * 1024 &&
-        (e = cudaFuncSetAttribute(demod_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-            cudaSuccess)
+        (e = cudaFuncSetAttribute(sep ? (const void*)demod_sep_kernel<true> : (const void*)demod_pair_kernel,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return cuda_fail(e, "demodulation smem attribute");
     const double df0 = plan->f_r - 0.5 / plan->cfg.dt, dK = 1.0 / plan->T_FFT;
     for (int64_t t0 = 0; t0 < n_t; t0 += batch) {
@@ -362,10 +547,22 @@ extern "C" cc_status crosscorr_demod_search(cc_plan* plan, const cc_template* t_
         cudaEvent_t ev0, ev1;   // diagnostic timing of the pair loop (crosscorr_plan_set_kernel_timing)
         timing_pair(plan, &ev0, &ev1);
         if (ev0) cudaEventRecord(ev0, st);
-        demod_pair_kernel<<<dim3((unsigned)((plan->N_f + nthr - 1) / nthr), (unsigned)nb), nthr, smem, st>>>(
-            p, nsft, plan->demod_m_lo, plan->demod_nbins, n_blk, Rs, (const float2*)plan->demod_z,
-            (const float4*)plan->demod_w, (const DemodTiming*)plan->ws, (const double*)plan->demod_df,
-            (const int64_t*)plan->demod_kbar, t0, rho_dev);
+        const dim3 grid((unsigned)((plan->N_f + nthr - 1) / nthr), (unsigned)nb);
+        if (sep_ring)
+            demod_sep_kernel<true><<<grid, nthr, smem, st>>>(
+                p, plan->demod_m_lo, plan->demod_nbins, n_blk, Rs, refresh, (const float2*)plan->demod_z,
+                (const float4*)plan->demod_w, (const DemodTiming*)plan->ws, (const double*)plan->demod_df,
+                (const int64_t*)plan->demod_kbar, t0, rho_dev);
+        else if (sep)
+            demod_sep_kernel<false><<<grid, nthr, 0, st>>>(
+                p, plan->demod_m_lo, plan->demod_nbins, n_blk, Rs, refresh, (const float2*)plan->demod_z,
+                (const float4*)plan->demod_w, (const DemodTiming*)plan->ws, (const double*)plan->demod_df,
+                (const int64_t*)plan->demod_kbar, t0, rho_dev);
+        else
+            demod_pair_kernel<<<grid, nthr, smem, st>>>(
+                p, nsft, plan->demod_m_lo, plan->demod_nbins, n_blk, Rs, (const float2*)plan->demod_z,
+                (const float4*)plan->demod_w, (const DemodTiming*)plan->ws, (const double*)plan->demod_df,
+                (const int64_t*)plan->demod_kbar, t0, rho_dev);
         count_launch();
         if (ev1) cudaEventRecord(ev1, st);
     }

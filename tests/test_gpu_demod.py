@@ -1,5 +1,7 @@
 """The detector-frame ("demodulation") CrossCorr on the GPU, through the C ABI, against
-the FP64 oracle (oracle/demod.py): per template max |drho| <= 1e-4 max(1, max|rho|)."""
+the FP64 oracle (oracle/demod.py): per template max |drho| <= 1e-4 max(1, max|rho|).
+Both pair sums are covered: the method's pair loop (the default) and the separable
+window-sum form (crosscorr_plan_set_demod_form)."""
 import ctypes
 
 import numpy as np
@@ -29,21 +31,25 @@ def assert_close(got, ref, tol=TOL):
         assert err <= lim, f"template {t}: max |drho| = {err:.3e} > {lim:.3e}"
 
 
-def gpu_demod(ds, templates=None):
+def gpu_demod(ds, templates=None, separable=False):
     tm = ds.templates if templates is None else templates
     with cc.CrossCorrPlan(ds.cfg, ds.dets) as plan:
         x = torch.from_numpy(ds.x64).to(DEV)
         plan.demod_prepare(x)
+        plan.set_demod_form(separable)
         return plan.demod_search(torch.from_numpy(np.ascontiguousarray(tm)).to(DEV)).cpu().numpy().astype(np.float64)
 
 
 @pytest.mark.parametrize("kw", [dict(), dict(T_max=0.0, T_short=64.0), dict(T_max=256.0, T_short=128.0),
                                 dict(n_det=1), dict(n_det=3), dict(n_samples=4096 + 77),
-                                dict(T_sft=32.0, T_max=160.0, T_short=160.0)])
-def test_demod_parity(kw):
+                                dict(T_sft=32.0, T_max=160.0, T_short=160.0),
+                                # R_s = 32 lags: the separable form recomputes leaving blocks
+                                dict(T_sft=16.0, T_max=512.0, T_short=512.0)])
+@pytest.mark.parametrize("separable", [False, True], ids=["pairs", "separable"])
+def test_demod_parity(kw, separable):
     ds = synth.tiny(seed=33, n_templates=3, injection=INJ, **kw)
     ref = np.stack([demod.demod_rho(ds, t) for t in ds.templates])
-    got = gpu_demod(ds)
+    got = gpu_demod(ds, separable=separable)
     assert got.shape == ref.shape
     assert_close(got, ref)
 
@@ -56,15 +62,32 @@ def test_demod_injection_argmax_matches_oracle():
     assert np.unravel_index(got.argmax(), got.shape) == np.unravel_index(ref.argmax(), ref.shape)
 
 
-def test_demod_o1_band_30_days_injected_template():
-    """30 days of the O1-shaped band (T_sft = 360 s SFTs, T_max = 3600 s: ten SFT lags)."""
+@pytest.mark.parametrize("separable", [False, True], ids=["pairs", "separable"])
+def test_demod_o1_band_30_days_injected_template(separable):
+    """30 days of the O1-shaped band (T_sft = 360 s SFTs, T_max = 3600 s: ten SFT lags).
+    The separable form's window sums run over 7200 blocks here, through many add/subtract
+    steps between their exact recomputations."""
     ds = synth.o1_band(n_ap=1, n_tasc=1, days=30)
     inj = ds.injection
     tm = np.array([[inj.a_p, inj.T_asc, inj.P]])
     ref = np.stack([demod.demod_rho(ds, t) for t in tm])
-    got = gpu_demod(ds, tm)
+    got = gpu_demod(ds, tm, separable=separable)
     assert_close(got, ref)
     assert int(got[0].argmax()) == int(ref[0].argmax())
+
+
+def test_demod_forms_agree_to_rounding():
+    """Pair loop and separable form on the same plan: the same rho up to FP32 rounding
+    (a bound ten times tighter than the oracle bar), including gaps and a ragged end."""
+    ds = synth.tiny(seed=35, n_templates=4, injection=INJ, n_samples=8192 + 301, duty=0.6)
+    with cc.CrossCorrPlan(ds.cfg, ds.dets) as plan:
+        x = torch.from_numpy(ds.x64).to(DEV)
+        tm = torch.from_numpy(ds.templates).to(DEV)
+        plan.demod_prepare(x)
+        pairs = plan.demod_search(tm).cpu().numpy().astype(np.float64)
+        plan.set_demod_form(True)
+        sep = plan.demod_search(tm).cpu().numpy().astype(np.float64)
+    assert_close(sep, pairs, 1e-5)
 
 
 def test_demod_argument_errors():
@@ -76,6 +99,7 @@ def test_demod_argument_errors():
         st = lib.crosscorr_demod_search(plan._h, ctypes.c_void_p(int(tm.data_ptr())), 1,
                                         ctypes.c_void_p(int(rho.data_ptr())), None)
         assert st == 1                          # not prepared
+        assert lib.crosscorr_plan_set_demod_form(plan._h, 2) == 1   # unknown form
         x = torch.from_numpy(ds.x64).to(DEV)
         with pytest.raises(cc.CrossCorrError) as e:
             plan.demod_prepare(x, n_bin=3)
