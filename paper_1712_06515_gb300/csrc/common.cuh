@@ -151,6 +151,9 @@ struct cc_plan {
     void* demod_tw = nullptr;                 // [nsft] float2
     void* demod_df = nullptr;                 // [N_f] double: f - f_h of the output bins
     void* demod_kbar = nullptr;               // [N_f] int64
+    void* demod_list = nullptr;               // [n_list] int: locked SFTs in time order, 4 l + X
+    void* demod_boff = nullptr;               // [n_blk + 1] int: first list entry of each block
+    int demod_nlist = 0;
     bool demod_ready = false;
     int demod_form = CC_DEMOD_PAIRS;          // crosscorr_plan_set_demod_form
     int demod_nsft = 0, demod_m_lo = 0, demod_nbins = 0, demod_nblk = 0;

@@ -92,13 +92,8 @@ sft_kernel(DevParams p, int nsft, int m_lo, int nbins, int n_blk, const float2* 
 
 // Per (template, detector, SFT block): the signal's heterodyned bin position and phase as
 // functions of the output bin, in FP64 reduced to FP32 pieces.
-__global__ void demod_timing_kernel(DevParams p, const cc_template* __restrict__ tm, int nsft, int n_blk,
-                                    double df0, double dK, DemodTiming* __restrict__ out) {
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
-    const int X = blockIdx.y;
-    const int64_t t = blockIdx.z;
-    if (l >= n_blk) return;
-    const cc_template T = tm[t];
+__device__ DemodTiming demod_timing(const DevParams& p, const cc_template& T, int nsft, int l, int X, double df0,
+                                    double dK) {
     const double tmid = ((double)l * nsft + 0.5 * nsft) * p.dt;   // relative to t0
     // Delta_X(t) and its slope (linear interpolation of the table)
     const double u = (tmid - p.eph_t0[X]) * p.inv_eph_dt[X];
@@ -146,7 +141,34 @@ __global__ void demod_timing_kernel(DevParams p, const cc_template* __restrict__
     r.C1 = (float)(c1 - floor(c1));
     r.C128 = (float)(c128 - floor(c128));
     r.pad0 = r.pad1 = r.pad2 = 0.f;
-    out[((size_t)t * p.Q + X) * n_blk + l] = r;
+    return r;
+}
+
+__global__ void demod_timing_kernel(DevParams p, const cc_template* __restrict__ tm, int nsft, int n_blk,
+                                    double df0, double dK, DemodTiming* __restrict__ out) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    const int X = blockIdx.y;
+    const int64_t t = blockIdx.z;
+    if (l >= n_blk) return;
+    out[((size_t)t * p.Q + X) * n_blk + l] = demod_timing(p, tm[t], nsft, l, X, df0, dK);
+}
+
+// The separable kernel's records: one per locked SFT of the time-ordered list, the timing
+// of demod_timing with the SFT's filter weights and list key (4 l + X) in the spare words.
+__global__ void demod_timing_list_kernel(DevParams p, const cc_template* __restrict__ tm, int nsft, int n_blk,
+                                         double df0, double dK, const int* __restrict__ list, int n_list,
+                                         const float4* __restrict__ wts, DemodTiming* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t t = blockIdx.y;
+    if (i >= n_list) return;
+    const int key = __ldg(list + i);
+    const int l = key >> 2, X = key & 3;
+    DemodTiming r = demod_timing(p, tm[t], nsft, l, X, df0, dK);
+    const float4 wk = __ldg(wts + (size_t)X * n_blk + l);
+    r.pad0 = wk.x;
+    r.pad1 = wk.y;
+    r.pad2 = __int_as_float(key);
+    out[(size_t)t * n_list + i] = r;
 }
 
 // One thread per (template, output bin): the pair loop over time-ordered SFTs.  The ring
@@ -280,130 +302,207 @@ __device__ __forceinline__ void sep_add_sft(SepSums& a, float2 y, float xi2, flo
     a.ubb = fmaf(xb, wk.y, a.ubb);
 }
 
-// The demodulated bin y of template row tr at frequency k (the pair kernel's arithmetic,
-// one SFT at a time) and the weight Xi^2 of its two-bin interpolation.
-__device__ __forceinline__ float2 demod_y(const DemodTiming& tr, float df, float kh, float kl, bool act, int m_lo,
-                                          int nbins, const float2* __restrict__ zrow, float& xi2) {
-    const float x = fmaf(df, tr.A1, tr.A0);
-    const float fm = floorf(x);
-    const float k0 = fm - x;
-    float s0, s1;
-    if (k0 == 0.f) {
-        s0 = 1.f;
-        s1 = 0.f;
-    } else {
-        const float sp = sinpif(k0) * 0.318309886183790672f;
-        s0 = __fdividef(sp, k0);
-        s1 = -__fdividef(sp, k0 + 1.f);
-    }
-    xi2 = s0 * s0 + s1 * s1;
-    const int m0 = (int)fm;
-    const int idx = m0 - m_lo;
-    float2 y = make_float2(0.f, 0.f);
-    if (act && idx >= 0 && idx + 1 < nbins) {
-        const float2 z0 = __ldg(zrow + idx), z1 = __ldg(zrow + idx + 1);
-        const float sg = (m0 & 1) ? -1.f : 1.f;
-        const float2 u = make_float2(sg * (s0 * z0.x - s1 * z1.x), sg * (s0 * z0.y - s1 * z1.y));
-        float cyc = fmaf(kl, tr.C1, fmaf(kh, tr.C128, tr.C0));
-        cyc -= floorf(cyc);
-        float sn, cs;
-        sincospif(2.0f * cyc, &sn, &cs);
-        y = make_float2(fmaf(u.x, cs, u.y * sn), fmaf(u.y, cs, -u.x * sn));
-    }
-    return y;
+// One SFT's inputs for the separable kernel, fetched ahead of its arithmetic: the signal
+// bin position (floor m0 and kappa = m0 - x), the heterodyne phase in cycles, and the two
+// bins m0, m0 + 1 (zero when out of the stored band).
+struct SftIn {
+    float k0, cyc;
+    int m0;
+    float2 z0, z1;
+};
+
+// sin(pi r) / (pi r) for |r| <= 1/2 from its Taylor series sum_n (-1)^n (pi r)^2n / (2n+1)!,
+// cut after n = 6: the first omitted term is below (pi/2)^14 / 15! = 4.2e-10.
+__device__ __forceinline__ float sinc_pi_half(float r) {
+    const float u = 9.86960440108935862f * r * r;   // (pi r)^2
+    float s = -1.f / 6227020800.f;                  // -1/13!
+    s = fmaf(s, u, 1.f / 39916800.f);               // 1/11!
+    s = fmaf(s, u, -1.f / 362880.f);                // -1/9!
+    s = fmaf(s, u, 1.f / 5040.f);                   // 1/7!
+    s = fmaf(s, u, -1.f / 120.f);                   // -1/5!
+    s = fmaf(s, u, 1.f / 6.f);                      // 1/3!
+    return fmaf(-s, u, 1.f);                        // 1 - u (1/3! - u/5! + ...)
 }
 
+// The demodulated bin y (the two-bin sinc interpolation of the pair kernel, rotated by the
+// heterodyne phase) and the interpolation weight Xi^2.  The two sinc weights
+// s0 = sin(pi kappa) / (pi kappa), s1 = -sin(pi kappa) / (pi (kappa + 1)) take the series
+// at whichever of kappa, kappa + 1 lies within 1/2 of zero and one quotient for the other
+// (its denominator at least 1/2 in size).  The rotation takes the phase in [-1/2, 1/2)
+// cycles to the fast sine/cosine, whose absolute error there (2^-21.4) is far below the
+// statistic's FP32 rounding.
+__device__ __forceinline__ float2 sft_y(const SftIn& q, float& xi2) {
+    const bool near0 = q.k0 >= -0.5f;                // kappa in [-1/2, 0]: series at kappa
+    const float r = near0 ? q.k0 : q.k0 + 1.f;
+    const float far = near0 ? q.k0 + 1.f : q.k0;
+    const float sv = sinc_pi_half(r);
+    const float other = -__fdividef(r * sv, far);
+    const float s0 = near0 ? sv : other, s1 = near0 ? other : sv;
+    xi2 = s0 * s0 + s1 * s1;
+    const float sg = (q.m0 & 1) ? -1.f : 1.f;
+    const float2 u = make_float2(sg * (s0 * q.z0.x - s1 * q.z1.x), sg * (s0 * q.z0.y - s1 * q.z1.y));
+    const float c = q.cyc >= 0.5f ? q.cyc - 1.f : q.cyc;
+    float sn, cs;
+    __sincosf(6.28318530717958648f * c, &sn, &cs);
+    return make_float2(fmaf(u.x, cs, u.y * sn), fmaf(u.y, cs, -u.x * sn));
+}
+
+// One record of the separable kernel's list: timing, weights and key of SFT i.
+struct SepRec {
+    float4 t0;   // A0, A1, C0, C1
+    float4 t1;   // C128, a^, b^, key (int bits: 4 l + X)
+};
+
+__device__ __forceinline__ SepRec load_rec(const DemodTiming* __restrict__ r) {
+    const float4* q = reinterpret_cast<const float4*>(r);
+    return SepRec{__ldg(q), __ldg(q + 1)};
+}
+
+__device__ __forceinline__ void rec_fetch(SftIn& q, const SepRec& r, float df, float kh, float kl, bool act, int m_lo,
+                                          int nbins, int n_blk, const float2* __restrict__ z) {
+    const int key = __float_as_int(r.t1.w);
+    const float x = fmaf(df, r.t0.y, r.t0.x);
+    const float fm = floorf(x);
+    q.k0 = fm - x;
+    q.m0 = (int)fm;
+    const int idx = q.m0 - m_lo;
+    const float cyc = fmaf(kl, r.t0.w, fmaf(kh, r.t1.x, r.t0.z));
+    q.cyc = cyc - floorf(cyc);
+    q.z0 = q.z1 = make_float2(0.f, 0.f);
+    if (act && idx >= 0 && idx + 1 < nbins) {
+        const float2* zr = z + ((size_t)(key & 3) * n_blk + (key >> 2)) * nbins + idx;
+        q.z0 = __ldg(zr);
+        q.z1 = __ldg(zr + 1);
+    }
+}
+
+// One thread per (template, output bin) walks the list of locked SFTs in time order (gaps
+// never enter the loop).  The SFT records of one template are shared by its CTAs.  Block
+// sums go to the window when the block index changes: one step adds s_l and subtracts
+// s_(l - R_s); a jump over empty blocks, and every R_s + 1 steps (RING) or 4 (R_s + 1)
+// steps (recomputation), sums the window exactly.
 template <bool RING>
 __global__ void __launch_bounds__(128) demod_sep_kernel(DevParams p, int m_lo, int nbins, int n_blk, int Rs, int refresh,
-                                 const float2* __restrict__ z, const float4* __restrict__ wts,
-                                 const DemodTiming* __restrict__ tq, const double* __restrict__ dfreq,
+                                 const float2* __restrict__ z, const DemodTiming* __restrict__ recs, int n_list,
+                                 const int* __restrict__ boff, const double* __restrict__ dfreq,
                                  const int64_t* __restrict__ kbar, int64_t t_base, float* __restrict__ rho) {
     extern __shared__ __align__(16) float sring[];     // RING: [R_s + 1][7][nthr] block sums, thread-private
     const int nthr = blockDim.x, tid = threadIdx.x;
-    const int Q = p.Q;
     const int64_t t = t_base + blockIdx.y;
     const int k = blockIdx.x * nthr + tid;
     const bool act = k < (int)p.N_f;
-    const DemodTiming* trow = tq + (size_t)(t - t_base) * Q * n_blk;
+    const DemodTiming* rt = recs + (size_t)(t - t_base) * n_list;
+    if (n_list == 0) {                                 // no locked SFT
+        if (act) rho[(size_t)t * p.N_f + k] = 0.f;
+        return;
+    }
     if (RING)
         for (int j = 0; j < (Rs + 1) * 7; ++j) sring[(size_t)j * nthr + tid] = 0.f;
     const float df = act ? (float)__ldg(dfreq + k) : 0.f;
     const int64_t kb = act ? __ldg(kbar + k) : 0;
     const float kh = (float)(kb >> 7), kl = (float)(kb & 127);
-    // sums of one whole block from its SFT bins
-    auto block_sums = [&](int j, SepSums& s) {
-        sep_zero(s);
-        for (int X = 0; X < Q; ++X) {
-            const float4 wk = __ldg(wts + (size_t)X * n_blk + j);
-            if (wk.z == 0.f) continue;
+    auto ring_get = [&](int slot) {
+        const float* r = sring + (size_t)slot * 7 * nthr + tid;
+        return SepSums{r[0], r[nthr], r[2 * nthr], r[3 * nthr], r[4 * nthr], r[5 * nthr], r[6 * nthr]};
+    };
+    auto ring_put = [&](int slot, const SepSums& v) {
+        float* r = sring + (size_t)slot * 7 * nthr + tid;
+        r[0] = v.ayx;
+        r[nthr] = v.ayy;
+        r[2 * nthr] = v.byx;
+        r[3 * nthr] = v.byy;
+        r[4 * nthr] = v.uaa;
+        r[5 * nthr] = v.uab;
+        r[6 * nthr] = v.ubb;
+    };
+    // block j's sums from its SFT bins (no ring)
+    auto block_sums = [&](int j, SepSums& sj) {
+        sep_zero(sj);
+        const int e = __ldg(boff + j + 1);
+        for (int i = __ldg(boff + j); i < e; ++i) {
+            const SepRec r = load_rec(rt + i);
+            SftIn q;
+            rec_fetch(q, r, df, kh, kl, act, m_lo, nbins, n_blk, z);
             float xi2;
-            const float2 y = demod_y(trow[(size_t)X * n_blk + j], df, kh, kl, act, m_lo, nbins,
-                                     z + ((size_t)X * n_blk + j) * nbins, xi2);
-            sep_add_sft(s, y, xi2, wk);
+            const float2 y = sft_y(q, xi2);
+            sep_add_sft(sj, y, xi2, make_float4(r.t1.y, r.t1.z, 1.f, 0.f));
         }
     };
     float raw = 0.f, rawc = 0.f, den = 0.f, denc = 0.f;
-    SepSums W;
+    SepSums W, P;
     sep_zero(W);
-    for (int l = 0; l < n_blk; ++l) {
-        SepSums P;
-        sep_zero(P);
-        for (int X = 0; X < Q; ++X) {
-            const float4 wk = __ldg(wts + (size_t)X * n_blk + l);
-            if (wk.z == 0.f) continue;                 // gap: no SFT (the same for the whole CTA)
-            float xi2;
-            const float2 y = demod_y(trow[(size_t)X * n_blk + l], df, kh, kl, act, m_lo, nbins,
-                                     z + ((size_t)X * n_blk + l) * nbins, xi2);
-            const float sax = W.ayx + P.ayx, say = W.ayy + P.ayy, sbx = W.byx + P.byx, sby = W.byy + P.byy;
-            const float gx = fmaf(wk.x, sax, wk.y * sbx), gy = fmaf(wk.x, say, wk.y * sby);
-            const float pr = 0.2f * fmaf(y.x, gx, y.y * gy);          // 2 Re(conj(y) g) / 10
-            const float nq = fmaf(wk.x * wk.x, W.uaa + P.uaa,
-                                  fmaf(2.f * wk.x * wk.y, W.uab + P.uab, wk.y * wk.y * (W.ubb + P.ubb)));
-            kahan_add(raw, rawc, pr);
-            kahan_add(den, denc, 0.01f * xi2 * nq);
-            sep_add_sft(P, y, xi2, wk);
-        }
-        if (Rs == 0) continue;
-        // the window of block l + 1: blocks l + 1 - R_s .. l
-        if (RING) {
-            float* slot = sring + (size_t)(l % (Rs + 1)) * 7 * nthr + tid;
-            const float* old = sring + (size_t)((l + 1) % (Rs + 1)) * 7 * nthr + tid;   // s_(l - R_s)
-            const SepSums so{old[0], old[nthr], old[2 * nthr], old[3 * nthr], old[4 * nthr], old[5 * nthr],
-                             old[6 * nthr]};
-            slot[0] = P.ayx;
-            slot[nthr] = P.ayy;
-            slot[2 * nthr] = P.byx;
-            slot[3 * nthr] = P.byy;
-            slot[4 * nthr] = P.uaa;
-            slot[5 * nthr] = P.uab;
-            slot[6 * nthr] = P.ubb;
-            if ((l + 1) % refresh == 0) {
-                sep_zero(W);
-                for (int j = 0; j <= Rs; ++j) {
-                    if (j == (l + 1) % (Rs + 1)) continue;
-                    const float* r = sring + (size_t)j * 7 * nthr + tid;
-                    const SepSums sj{r[0], r[nthr], r[2 * nthr], r[3 * nthr], r[4 * nthr], r[5 * nthr], r[6 * nthr]};
-                    sep_axpy(W, sj, 1.f);
+    sep_zero(P);
+    int steps = 0;
+    // software pipeline: the bins of SFT i + 1 and the record of SFT i + 2 load while SFT i
+    // is summed
+    SepRec rc = load_rec(rt);
+    SftIn cur;
+    rec_fetch(cur, rc, df, kh, kl, act, m_lo, nbins, n_blk, z);
+    SepRec rn = n_list > 1 ? load_rec(rt + 1) : rc;
+    int lcur = __float_as_int(rc.t1.w) >> 2;
+    for (int i = 0; i < n_list; ++i) {
+        SftIn nxt{};
+        if (i + 1 < n_list) rec_fetch(nxt, rn, df, kh, kl, act, m_lo, nbins, n_blk, z);
+        const SepRec r = rc;
+        rc = rn;
+        if (i + 2 < n_list) rn = load_rec(rt + i + 2);
+        const SftIn q = cur;
+        cur = nxt;
+        const int l = __float_as_int(r.t1.w) >> 2;
+        if (l != lcur) {                               // block lcur is complete: the window of block l
+            if (Rs > 0) {
+                if (RING) {
+                    const bool step1 = l == lcur + 1 && ++steps < refresh;
+                    const int so = l % (Rs + 1);          // s_(l - R_s - 1) = s_(lcur - R_s) on a single step
+                    if (step1) {
+                        const SepSums old = ring_get(so);
+                        sep_axpy(W, P, 1.f);
+                        sep_axpy(W, old, -1.f);
+                        ring_put(lcur % (Rs + 1), P);
+                    } else {
+                        ring_put(lcur % (Rs + 1), P);
+                        const SepSums zero{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                        const int nz = min(l - lcur - 1, Rs + 1);   // empty blocks lcur + 1 .. l - 1
+                        for (int j = 1; j <= nz; ++j) ring_put((lcur + j) % (Rs + 1), zero);
+                        sep_zero(W);
+                        for (int j = 0; j <= Rs; ++j)
+                            if (j != so) sep_axpy(W, ring_get(j), 1.f);
+                        steps = 0;
+                    }
+                } else if (l - lcur > Rs) {            // every block of the new window is empty
+                    sep_zero(W);
+                    steps = 0;
+                } else if (++steps < refresh) {        // blocks lcur - R_s .. l - R_s - 1 leave
+                    sep_axpy(W, P, 1.f);
+                    for (int j = max(0, lcur - Rs); j < l - Rs; ++j) {
+                        SepSums old;
+                        block_sums(j, old);
+                        sep_axpy(W, old, -1.f);
+                    }
+                } else {
+                    W = P;                             // blocks l - R_s .. lcur (those after are empty)
+                    for (int j = max(0, l - Rs); j < lcur; ++j) {
+                        SepSums sj;
+                        block_sums(j, sj);
+                        sep_axpy(W, sj, 1.f);
+                    }
+                    steps = 0;
                 }
-            } else {
-                sep_axpy(W, P, 1.f);
-                sep_axpy(W, so, -1.f);
             }
-        } else if ((l + 1) % refresh == 0) {
-            W = P;
-            for (int j = max(0, l + 1 - Rs); j < l; ++j) {
-                SepSums sj;
-                block_sums(j, sj);
-                sep_axpy(W, sj, 1.f);
-            }
-        } else {
-            sep_axpy(W, P, 1.f);
-            if (l - Rs >= 0) {
-                SepSums so;
-                block_sums(l - Rs, so);
-                sep_axpy(W, so, -1.f);
-            }
+            sep_zero(P);
+            lcur = l;
         }
+        const float4 wk = make_float4(r.t1.y, r.t1.z, 1.f, 0.f);
+        float xi2;
+        const float2 y = sft_y(q, xi2);
+        const float sax = W.ayx + P.ayx, say = W.ayy + P.ayy, sbx = W.byx + P.byx, sby = W.byy + P.byy;
+        const float gx = fmaf(wk.x, sax, wk.y * sbx), gy = fmaf(wk.x, say, wk.y * sby);
+        const float pr = 0.2f * fmaf(y.x, gx, y.y * gy);          // 2 Re(conj(y) g) / 10
+        const float nq = fmaf(wk.x * wk.x, W.uaa + P.uaa,
+                              fmaf(2.f * wk.x * wk.y, W.uab + P.uab, wk.y * wk.y * (W.ubb + P.ubb)));
+        kahan_add(raw, rawc, pr);
+        kahan_add(den, denc, 0.01f * xi2 * nq);
+        sep_add_sft(P, y, xi2, wk);
     }
     if (act) rho[(size_t)t * p.N_f + k] = den > 0.f ? raw / sqrtf(2.f * den) : 0.f;
 }
@@ -485,6 +584,33 @@ extern "C" cc_status crosscorr_demod_prepare(cc_plan* plan, const void* const* x
                             cudaMemcpyHostToDevice)) != cudaSuccess)
             return cuda_fail(e, "demodulation bin tables");
     }
+    // the locked SFTs in time order (key 4 l + X) and each block's first entry, for the
+    // separable form
+    {
+        std::vector<float4> w((size_t)p.Q * n_blk);
+        if ((e = cudaMemcpyAsync(w.data(), plan->demod_w, sizeof(float4) * w.size(), cudaMemcpyDeviceToHost, st)) !=
+                cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess)
+            return cuda_fail(e, "demodulation SFT weights");
+        std::vector<int> list, boff(n_blk + 1);
+        for (int64_t l = 0; l < n_blk; ++l) {
+            boff[l] = (int)list.size();
+            for (int X = 0; X < p.Q; ++X)
+                if (w[(size_t)X * n_blk + l].z != 0.f) list.push_back((int)(4 * l + X));
+        }
+        boff[n_blk] = (int)list.size();
+        for (void* ptr : {plan->demod_list, plan->demod_boff})
+            if (ptr) cudaFree(ptr);
+        plan->demod_list = plan->demod_boff = nullptr;
+        if ((e = cudaMalloc(&plan->demod_list, sizeof(int) * std::max<size_t>(1, list.size()))) != cudaSuccess ||
+            (e = cudaMalloc(&plan->demod_boff, sizeof(int) * boff.size())) != cudaSuccess ||
+            (!list.empty() && (e = cudaMemcpy(plan->demod_list, list.data(), sizeof(int) * list.size(),
+                                              cudaMemcpyHostToDevice)) != cudaSuccess) ||
+            (e = cudaMemcpy(plan->demod_boff, boff.data(), sizeof(int) * boff.size(), cudaMemcpyHostToDevice)) !=
+                cudaSuccess)
+            return cuda_fail(e, "demodulation SFT list");
+        plan->demod_nlist = (int)list.size();
+    }
     plan->demod_nsft = (int)nsft;
     plan->demod_m_lo = m_lo;
     plan->demod_nbins = nbins;
@@ -526,8 +652,10 @@ extern "C" cc_status crosscorr_demod_search(cc_plan* plan, const cc_template* t_
     // exact window recomputation every `refresh` blocks: each R_s + 1 with the ring (a sum
     // over the ring), 4 (R_s + 1) without (a recomputation from the bins)
     const int refresh = sep_ring ? Rs + 1 : 4 * (Rs + 1);
-    // timing records for a batch of templates
-    const size_t per_t = sizeof(DemodTiming) * (size_t)p.Q * n_blk;
+    // timing records for a batch of templates: every (X, l) for the pair loop, the list of
+    // locked SFTs for the separable form
+    const int n_list = plan->demod_nlist;
+    const size_t per_t = sizeof(DemodTiming) * (sep ? (size_t)std::max(1, n_list) : (size_t)p.Q * n_blk);
     const int64_t batch = std::max<int64_t>(1, std::min<int64_t>({n_t, (int64_t)((size_t)2 << 30) / (int64_t)per_t, 65535}));
     cc_status s = ensure_workspace(plan, per_t * batch);
     if (s != CC_OK) return s;
@@ -541,22 +669,22 @@ extern "C" cc_status crosscorr_demod_search(cc_plan* plan, const cc_template* t_
     const double df0 = plan->f_r - 0.5 / plan->cfg.dt, dK = 1.0 / plan->T_FFT;
     for (int64_t t0 = 0; t0 < n_t; t0 += batch) {
         const int64_t nb = std::min(batch, n_t - t0);
-        demod_timing_kernel<<<dim3((unsigned)((n_blk + 127) / 128), (unsigned)p.Q, (unsigned)nb), 128, 0, st>>>(
-            p, t_dev + t0, nsft, n_blk, df0, dK, (DemodTiming*)plan->ws);
-        count_launch();
+        if (!sep)
+            demod_timing_kernel<<<dim3((unsigned)((n_blk + 127) / 128), (unsigned)p.Q, (unsigned)nb), 128, 0, st>>>(
+                p, t_dev + t0, nsft, n_blk, df0, dK, (DemodTiming*)plan->ws);
+        else if (n_list > 0)
+            demod_timing_list_kernel<<<dim3((unsigned)((n_list + 127) / 128), (unsigned)nb), 128, 0, st>>>(
+                p, t_dev + t0, nsft, n_blk, df0, dK, (const int*)plan->demod_list, n_list,
+                (const float4*)plan->demod_w, (DemodTiming*)plan->ws);
+        if (!sep || n_list > 0) count_launch();
         cudaEvent_t ev0, ev1;   // diagnostic timing of the pair loop (crosscorr_plan_set_kernel_timing)
         timing_pair(plan, &ev0, &ev1);
         if (ev0) cudaEventRecord(ev0, st);
         const dim3 grid((unsigned)((plan->N_f + nthr - 1) / nthr), (unsigned)nb);
-        if (sep_ring)
-            demod_sep_kernel<true><<<grid, nthr, smem, st>>>(
+        if (sep)
+            (sep_ring ? demod_sep_kernel<true> : demod_sep_kernel<false>)<<<grid, nthr, smem, st>>>(
                 p, plan->demod_m_lo, plan->demod_nbins, n_blk, Rs, refresh, (const float2*)plan->demod_z,
-                (const float4*)plan->demod_w, (const DemodTiming*)plan->ws, (const double*)plan->demod_df,
-                (const int64_t*)plan->demod_kbar, t0, rho_dev);
-        else if (sep)
-            demod_sep_kernel<false><<<grid, nthr, 0, st>>>(
-                p, plan->demod_m_lo, plan->demod_nbins, n_blk, Rs, refresh, (const float2*)plan->demod_z,
-                (const float4*)plan->demod_w, (const DemodTiming*)plan->ws, (const double*)plan->demod_df,
+                (const DemodTiming*)plan->ws, n_list, (const int*)plan->demod_boff, (const double*)plan->demod_df,
                 (const int64_t*)plan->demod_kbar, t0, rho_dev);
         else
             demod_pair_kernel<<<grid, nthr, smem, st>>>(

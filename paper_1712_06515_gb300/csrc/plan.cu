@@ -195,7 +195,7 @@ void crosscorr_plan_destroy(cc_plan* p) {
     for (void* d : p->dev_allocs) cudaFree(d);
     if (p->ws && !p->ws_external) cudaFree(p->ws);
     for (cudaEvent_t e : p->timing_events) cudaEventDestroy(e);
-    for (void* d : {p->demod_z, p->demod_w, p->demod_tw, p->demod_df, p->demod_kbar})
+    for (void* d : {p->demod_z, p->demod_w, p->demod_tw, p->demod_df, p->demod_kbar, p->demod_list, p->demod_boff})
         if (d) cudaFree(d);
     if (p->learned_w) cudaFree(p->learned_w);
     if (p->learned_taps) cudaFree(p->learned_taps);
