@@ -990,7 +990,7 @@ def run_demod(args):
         "warmup": args.warmup, "ms_per_step": 1000.0 * elapsed / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "o1_band: 2 det, 120 d at 60% duty, 0.5 Hz at 150 Hz, T_sft=360 s SFTs, "
-                               "T_max=3600 s", "method": "detector-frame (demodulation) CrossCorr, n_bin=2",
+                               f"T_max={ds.cfg.T_max:g} s", "method": "detector-frame (demodulation) CrossCorr, n_bin=2",
                    "demod_form": args.demod_form, "templates_per_step": B, "locked_sfts": locked, "sft_pairs": pairs, "sft_ms_once": sft_ms},
         "roofline": {"bound": "alu", "kernel": "demod_sep_kernel" if separable else "demod_pair_kernel",
                      "achieved": achieved, "peak": peak,

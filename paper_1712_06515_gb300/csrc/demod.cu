@@ -379,8 +379,8 @@ __device__ __forceinline__ void rec_fetch(SftIn& q, const SepRec& r, float df, f
 // One thread per (template, output bin) walks the list of locked SFTs in time order (gaps
 // never enter the loop).  The SFT records of one template are shared by its CTAs.  Block
 // sums go to the window when the block index changes: one step adds s_l and subtracts
-// s_(l - R_s); a jump over empty blocks, and every R_s + 1 steps (RING) or 4 (R_s + 1)
-// steps (recomputation), sums the window exactly.
+// s_(l - R_s); a jump over empty blocks, and every 4 (R_s + 1) steps, sums the window
+// exactly.
 template <bool RING>
 __global__ void __launch_bounds__(128) demod_sep_kernel(DevParams p, int m_lo, int nbins, int n_blk, int Rs, int refresh,
                                  const float2* __restrict__ z, const DemodTiming* __restrict__ recs, int n_list,
@@ -433,22 +433,16 @@ __global__ void __launch_bounds__(128) demod_sep_kernel(DevParams p, int m_lo, i
     sep_zero(W);
     sep_zero(P);
     int steps = 0;
-    // software pipeline: the bins of SFT i + 1 and the record of SFT i + 2 load while SFT i
-    // is summed
-    SepRec rc = load_rec(rt);
-    SftIn cur;
-    rec_fetch(cur, rc, df, kh, kl, act, m_lo, nbins, n_blk, z);
-    SepRec rn = n_list > 1 ? load_rec(rt + 1) : rc;
-    int lcur = __float_as_int(rc.t1.w) >> 2;
-    for (int i = 0; i < n_list; ++i) {
-        SftIn nxt{};
-        if (i + 1 < n_list) rec_fetch(nxt, rn, df, kh, kl, act, m_lo, nbins, n_blk, z);
-        const SepRec r = rc;
-        rc = rn;
-        if (i + 2 < n_list) rn = load_rec(rt + i + 2);
-        const SftIn q = cur;
-        cur = nxt;
-        const int l = __float_as_int(r.t1.w) >> 2;
+    int lcur = 0;
+    // SFT i: Rc its record, Fc its fetched inputs; Rn the record of SFT i + 1, Fn receives
+    // SFT i + 1's inputs.  The bins of SFT i + 1 and the record of SFT i + 2 (into Rc once
+    // read) load while SFT i is summed; two calls per iteration with the roles swapped keep
+    // the pipeline in place without register copies.
+    auto step = [&](SepRec& Rc, SftIn& Fc, const SepRec& Rn, SftIn& Fn, int i) {
+        if (i + 1 < n_list) rec_fetch(Fn, Rn, df, kh, kl, act, m_lo, nbins, n_blk, z);
+        const float4 wk = make_float4(Rc.t1.y, Rc.t1.z, 1.f, 0.f);
+        const int l = __float_as_int(Rc.t1.w) >> 2;
+        if (i + 2 < n_list) Rc = load_rec(rt + i + 2);
         if (l != lcur) {                               // block lcur is complete: the window of block l
             if (Rs > 0) {
                 if (RING) {
@@ -492,9 +486,8 @@ __global__ void __launch_bounds__(128) demod_sep_kernel(DevParams p, int m_lo, i
             sep_zero(P);
             lcur = l;
         }
-        const float4 wk = make_float4(r.t1.y, r.t1.z, 1.f, 0.f);
         float xi2;
-        const float2 y = sft_y(q, xi2);
+        const float2 y = sft_y(Fc, xi2);
         const float sax = W.ayx + P.ayx, say = W.ayy + P.ayy, sbx = W.byx + P.byx, sby = W.byy + P.byy;
         const float gx = fmaf(wk.x, sax, wk.y * sbx), gy = fmaf(wk.x, say, wk.y * sby);
         const float pr = 0.2f * fmaf(y.x, gx, y.y * gy);          // 2 Re(conj(y) g) / 10
@@ -503,7 +496,18 @@ __global__ void __launch_bounds__(128) demod_sep_kernel(DevParams p, int m_lo, i
         kahan_add(raw, rawc, pr);
         kahan_add(den, denc, 0.01f * xi2 * nq);
         sep_add_sft(P, y, xi2, wk);
+    };
+    SepRec ra = load_rec(rt);
+    SepRec rb = n_list > 1 ? load_rec(rt + 1) : ra;
+    SftIn fa, fb;
+    rec_fetch(fa, ra, df, kh, kl, act, m_lo, nbins, n_blk, z);
+    lcur = __float_as_int(ra.t1.w) >> 2;
+    int i = 0;
+    for (; i + 1 < n_list; i += 2) {
+        step(ra, fa, rb, fb, i);
+        step(rb, fb, ra, fa, i + 1);
     }
+    if (i < n_list) step(ra, fa, rb, fb, i);
     if (act) rho[(size_t)t * p.N_f + k] = den > 0.f ? raw / sqrtf(2.f * den) : 0.f;
 }
 
@@ -649,9 +653,9 @@ extern "C" cc_status crosscorr_demod_search(cc_plan* plan, const cc_template* t_
     };
     while (nthr > 32 && ring_bytes(nthr) > DM_RING_BUDGET) nthr /= 2;
     if (ring_bytes(nthr) > DM_RING_BUDGET) return fail(CC_ERR_UNSUPPORTED, "T_max / T_sft too large for the pair ring");
-    // exact window recomputation every `refresh` blocks: each R_s + 1 with the ring (a sum
-    // over the ring), 4 (R_s + 1) without (a recomputation from the bins)
-    const int refresh = sep_ring ? Rs + 1 : 4 * (Rs + 1);
+    // exact window sum (over the ring, or recomputed from the bins) after 4 (R_s + 1)
+    // single-block steps: the FP32 rounding of the running sums cannot drift further
+    const int refresh = 4 * (Rs + 1);
     // timing records for a batch of templates: every (X, l) for the pair loop, the list of
     // locked SFTs for the separable form
     const int n_list = plan->demod_nlist;
