@@ -433,7 +433,11 @@ __global__ void __launch_bounds__(128) demod_sep_kernel(DevParams p, int m_lo, i
     sep_zero(W);
     sep_zero(P);
     int steps = 0;
-    int lcur = 0;
+    int lcur = 0, scur = 0;                            // block lcur and its ring slot lcur mod (R_s + 1)
+    // the pair and normalisation terms go to plain FP32 partial sums that join the
+    // compensated totals at most every 64 SFTs (at a block change)
+    float raw_p = 0.f, den_p = 0.f;
+    int nacc = 0;
     // SFT i: Rc its record, Fc its fetched inputs; Rn the record of SFT i + 1, Fn receives
     // SFT i + 1's inputs.  The bins of SFT i + 1 and the record of SFT i + 2 (into Rc once
     // read) load while SFT i is summed; two calls per iteration with the roles swapped keep
@@ -447,20 +451,23 @@ __global__ void __launch_bounds__(128) demod_sep_kernel(DevParams p, int m_lo, i
             if (Rs > 0) {
                 if (RING) {
                     const bool step1 = l == lcur + 1 && ++steps < refresh;
-                    const int so = l % (Rs + 1);          // s_(l - R_s - 1) = s_(lcur - R_s) on a single step
+                    ring_put(scur, P);
                     if (step1) {
-                        const SepSums old = ring_get(so);
+                        scur = scur == Rs ? 0 : scur + 1;       // slot of l: s_(l - R_s - 1) = s_(lcur - R_s)
+                        const SepSums old = ring_get(scur);
                         sep_axpy(W, P, 1.f);
                         sep_axpy(W, old, -1.f);
-                        ring_put(lcur % (Rs + 1), P);
                     } else {
-                        ring_put(lcur % (Rs + 1), P);
                         const SepSums zero{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                         const int nz = min(l - lcur - 1, Rs + 1);   // empty blocks lcur + 1 .. l - 1
-                        for (int j = 1; j <= nz; ++j) ring_put((lcur + j) % (Rs + 1), zero);
+                        for (int j = 1; j <= nz; ++j) {
+                            scur = scur == Rs ? 0 : scur + 1;
+                            ring_put(scur, zero);
+                        }
+                        scur = l % (Rs + 1);
                         sep_zero(W);
                         for (int j = 0; j <= Rs; ++j)
-                            if (j != so) sep_axpy(W, ring_get(j), 1.f);
+                            if (j != scur) sep_axpy(W, ring_get(j), 1.f);
                         steps = 0;
                     }
                 } else if (l - lcur > Rs) {            // every block of the new window is empty
@@ -485,6 +492,12 @@ __global__ void __launch_bounds__(128) demod_sep_kernel(DevParams p, int m_lo, i
             }
             sep_zero(P);
             lcur = l;
+            if (steps == 0 || nacc >= 64) {
+                kahan_add(raw, rawc, raw_p);
+                kahan_add(den, denc, den_p);
+                raw_p = den_p = 0.f;
+                nacc = 0;
+            }
         }
         float xi2;
         const float2 y = sft_y(Fc, xi2);
@@ -493,8 +506,9 @@ __global__ void __launch_bounds__(128) demod_sep_kernel(DevParams p, int m_lo, i
         const float pr = 0.2f * fmaf(y.x, gx, y.y * gy);          // 2 Re(conj(y) g) / 10
         const float nq = fmaf(wk.x * wk.x, W.uaa + P.uaa,
                               fmaf(2.f * wk.x * wk.y, W.uab + P.uab, wk.y * wk.y * (W.ubb + P.ubb)));
-        kahan_add(raw, rawc, pr);
-        kahan_add(den, denc, 0.01f * xi2 * nq);
+        raw_p += pr;
+        den_p = fmaf(0.01f * xi2, nq, den_p);
+        ++nacc;
         sep_add_sft(P, y, xi2, wk);
     };
     SepRec ra = load_rec(rt);
@@ -502,12 +516,15 @@ __global__ void __launch_bounds__(128) demod_sep_kernel(DevParams p, int m_lo, i
     SftIn fa, fb;
     rec_fetch(fa, ra, df, kh, kl, act, m_lo, nbins, n_blk, z);
     lcur = __float_as_int(ra.t1.w) >> 2;
+    scur = lcur % (Rs + 1);
     int i = 0;
     for (; i + 1 < n_list; i += 2) {
         step(ra, fa, rb, fb, i);
         step(rb, fb, ra, fa, i + 1);
     }
     if (i < n_list) step(ra, fa, rb, fb, i);
+    kahan_add(raw, rawc, raw_p);
+    kahan_add(den, denc, den_p);
     if (act) rho[(size_t)t * p.N_f + k] = den > 0.f ? raw / sqrtf(2.f * den) : 0.f;
 }
 
