@@ -99,10 +99,11 @@ def measure_fp32_peak(stream=None) -> float:
     return v.value
 
 
-def sfts_to_series(band, block_sft, T_sft: float, f_h: float, stream=None):
+def sfts_to_series(band, block_sft, T_sft: float, f_h: float, out=None, stream=None):
     """Heterodyned, downsampled series [n_blocks * N'] (CUDA complex64) from SFT bands
     band [n_sft, N'] (CUDA complex64) and block_sft [n_blocks] (CUDA int64, -1 = gap):
-    the input preparation of Appendix B, in the CUDA library."""
+    the input preparation of Appendix B, in the CUDA library.  ``out``: an optional
+    preallocated contiguous complex64 tensor of n_blocks * N' elements."""
     import torch
     lib = _lib.load()
     _check_tensor("band", band, torch.complex64)
@@ -110,7 +111,13 @@ def sfts_to_series(band, block_sft, T_sft: float, f_h: float, stream=None):
     if band.dim() != 2:
         raise ValueError("band must be [n_sft, N']")
     n_blocks, n_prime = block_sft.numel(), band.shape[1]
-    x = torch.empty(n_blocks * n_prime, dtype=torch.complex64, device=band.device)
+    if out is None:
+        x = torch.empty(n_blocks * n_prime, dtype=torch.complex64, device=band.device)
+    else:
+        _check_tensor("out", out, torch.complex64)
+        if out.numel() != n_blocks * n_prime:
+            raise ValueError("out must hold n_blocks * N' elements")
+        x = out
     check("crosscorr_sfts_to_series", lib.crosscorr_sfts_to_series(
         _dptr(band), _dptr(block_sft), n_blocks, n_prime, float(T_sft), float(f_h), _dptr(x),
         _stream_handle(stream)))

@@ -5,6 +5,9 @@
 // prime factors 2, 3 and 5 only takes a mixed-radix FFT; any other N' the direct DFT.
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <utility>
 #include <vector>
 
 #include "common.cuh"
@@ -114,11 +117,8 @@ __device__ __forceinline__ void dft_small(float2 (&v)[5], int R) {
     }
 }
 
-// `groups` T_sft blocks per CTA, one group of blockDim.x / groups threads each;
-// twf: forward twiddles exp(-2 pi i e / N').  WARP: each group is one warp and its passes
-// synchronise the warp alone; otherwise the CTA's barriers order every group's passes.
-// A gap block's group writes zeros and idles through the passes.
-template <bool WARP>
+// N' above 1536: one T_sft block per CTA (groups = 1), the CTA's barriers ordering the
+// passes; twf: forward twiddles exp(-2 pi i e / N').  A gap block writes zeros.
 __global__ void __launch_bounds__(SS_THREADS)
 sft_fft_kernel(const float2* __restrict__ band, const int64_t* __restrict__ block_sft, int64_t n_blocks,
                int n_prime, double T_sft, double f_h, const float2* __restrict__ twf, Radices rad, int groups,
@@ -142,10 +142,7 @@ sft_fft_kernel(const float2* __restrict__ band, const int64_t* __restrict__ bloc
             src[m] = make_float2(z.x, -z.y);   // conjugated band
         }
     }
-    auto sync = [] {
-        if constexpr (WARP) __syncwarp();
-        else __syncthreads();
-    };
+    auto sync = [] { __syncthreads(); };
     sync();
     for (int p = 0; p < rad.n; ++p) {
         const int R = rad.r[p], ns = rad.ns[p], nb = n_prime / R, tstep = n_prime / (ns * R);
@@ -191,6 +188,164 @@ sft_fft_kernel(const float2* __restrict__ band, const int64_t* __restrict__ bloc
     }
 }
 
+__device__ __forceinline__ void cp_async8(float2* dst, const float2* src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// forward DFT of radix R (compile time) in place on v[0 .. R-1]
+template <int R>
+__device__ __forceinline__ void dft_r(float2 (&v)[R]) {
+    if constexpr (R == 2) {
+        const float2 a = v[0];
+        v[0] = f2add(a, v[1]);
+        v[1] = f2sub(a, v[1]);
+    } else if constexpr (R == 3) {
+        const float2 s = f2add(v[1], v[2]), d = f2sub(v[1], v[2]);
+        const float2 t = f2sub(v[0], f2scale(s, 0.5f)), u = f2negi(f2scale(d, kC3));
+        v[0] = f2add(v[0], s);
+        v[1] = f2add(t, u);
+        v[2] = f2sub(t, u);
+    } else if constexpr (R == 4) {
+        const float2 s0 = f2add(v[0], v[2]), d0 = f2sub(v[0], v[2]);
+        const float2 s1 = f2add(v[1], v[3]), d1 = f2negi(f2sub(v[1], v[3]));
+        v[0] = f2add(s0, s1);
+        v[2] = f2sub(s0, s1);
+        v[1] = f2add(d0, d1);
+        v[3] = f2sub(d0, d1);
+    } else {
+        static_assert(R == 5, "radix 2, 3, 4 or 5");
+        const float2 a14 = f2add(v[1], v[4]), d14 = f2sub(v[1], v[4]);
+        const float2 a23 = f2add(v[2], v[3]), d23 = f2sub(v[2], v[3]);
+        const float2 p1 = make_float2(v[0].x + kC51 * a14.x + kC52 * a23.x, v[0].y + kC51 * a14.y + kC52 * a23.y);
+        const float2 p2 = make_float2(v[0].x + kC52 * a14.x + kC51 * a23.x, v[0].y + kC52 * a14.y + kC51 * a23.y);
+        const float2 q1 = f2negi(make_float2(kS51 * d14.x + kS52 * d23.x, kS51 * d14.y + kS52 * d23.y));
+        const float2 q2 = f2negi(make_float2(kS52 * d14.x - kS51 * d23.x, kS52 * d14.y - kS51 * d23.y));
+        v[0] = f2add(v[0], f2add(a14, a23));
+        v[1] = f2add(p1, q1);
+        v[4] = f2sub(p1, q1);
+        v[2] = f2add(p2, q2);
+        v[3] = f2sub(p2, q2);
+    }
+}
+
+// One Stockham pass of radix R over N' points by one warp (lanes stride the butterflies);
+// CONJ conjugates the inputs (the first pass, reading the staged band).
+template <int R, bool CONJ>
+__device__ __forceinline__ void warp_pass_r(const float2* src, float2* dst, const float2* twf, int n_prime, int ns,
+                                            uint32_t nsm, int nss, int lane) {
+    const int nb = n_prime / R, tstep = n_prime / (ns * R);
+    for (int j = lane; j < nb; j += 32) {
+        const int k = ns == 1 ? 0 : j - (int)(((uint64_t)(uint32_t)j * nsm) >> nss) * ns;   // j mod ns
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            v[r] = src[j + r * nb];
+            if (CONJ) v[r].y = -v[r].y;
+        }
+        if (ns > 1) {
+            const int tk = k * tstep;
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                const float2 w = twf[tk * r];
+                v[r] = make_float2(v[r].x * w.x - v[r].y * w.y, v[r].x * w.y + v[r].y * w.x);
+            }
+        }
+        dft_r<R>(v);
+        float2* d = dst + (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) d[r * ns] = v[r];
+    }
+}
+
+template <bool CONJ>
+__device__ __forceinline__ void warp_pass(const float2* src, float2* dst, const float2* twf, int n_prime, int R,
+                                          int ns, uint32_t nsm, int nss, int lane) {
+    switch (R) {   // the same for the whole warp
+        case 2: warp_pass_r<2, CONJ>(src, dst, twf, n_prime, ns, nsm, nss, lane); break;
+        case 3: warp_pass_r<3, CONJ>(src, dst, twf, n_prime, ns, nsm, nss, lane); break;
+        case 4: warp_pass_r<4, CONJ>(src, dst, twf, n_prime, ns, nsm, nss, lane); break;
+        default: warp_pass_r<5, CONJ>(src, dst, twf, n_prime, ns, nsm, nss, lane); break;
+    }
+}
+
+// N' up to 1536: persistent warps, each taking blocks b = w, w + W, ... (W warps in the
+// grid).  Per warp three N'-point shared buffers: the next locked SFT's bins are staged by
+// cp.async while the current one runs its passes, so its HBM latency overlaps the
+// transform; the forward twiddles exp(-2 pi i e / N') are formed once per CTA (FP64).
+// Only warp-level synchronisation after the one CTA barrier of the twiddle table.
+__global__ void __launch_bounds__(SS_THREADS)
+sft_fft_warp_kernel(const float2* __restrict__ band, const int64_t* __restrict__ block_sft, int64_t n_blocks,
+                    int n_prime, double T_sft, double f_h, Radices rad, float2* __restrict__ x) {
+    extern __shared__ __align__(16) float2 sw[];
+    float2* twf = sw;                                  // [N' rounded up to even]
+    const int groups = blockDim.x >> 5, g = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2* stage = sw + ((n_prime + 1) & ~1) + (size_t)g * 3 * n_prime;
+    float2* bufA = stage + n_prime;
+    float2* bufB = bufA + n_prime;
+    for (int e = threadIdx.x; e < n_prime; e += blockDim.x) {
+        double sn, cs;
+        sincospi(-2.0 * (double)e / (double)n_prime, &sn, &cs);
+        twf[e] = make_float2((float)cs, (float)sn);
+    }
+    __syncthreads();
+    const int64_t W = (int64_t)gridDim.x * groups;
+    int64_t b = (int64_t)blockIdx.x * groups + g;
+    int64_t s = b < n_blocks ? __ldg(block_sft + b) : -1;
+    if (s >= 0) {
+        const float2* zs = band + s * (int64_t)n_prime;
+        for (int m = lane; m < n_prime; m += 32) cp_async8(stage + m, zs + m);
+    }
+    cp_async_commit();
+    const float scale = (float)(1.0 / T_sft);
+    for (; b < n_blocks; b += W) {
+        const int64_t bn = b + W;
+        const int64_t sn = bn < n_blocks ? __ldg(block_sft + bn) : -1;
+        float2* xo = x + b * (int64_t)n_prime;
+        if (s >= 0) {
+            cp_async_wait_all();
+            __syncwarp();
+            warp_pass<true>(stage, bufA, twf, n_prime, rad.r[0], rad.ns[0], rad.nsm[0], rad.nss[0], lane);
+            __syncwarp();                              // the stage is free: every lane has read it
+        }
+        if (sn >= 0) {
+            const float2* zs = band + sn * (int64_t)n_prime;
+            for (int m = lane; m < n_prime; m += 32) cp_async8(stage + m, zs + m);
+            cp_async_commit();
+        }
+        if (s >= 0) {
+            float2* src = bufA;
+            float2* dst = bufB;
+            for (int p = 1; p < rad.n; ++p) {
+                __syncwarp();
+                warp_pass<false>(src, dst, twf, n_prime, rad.r[p], rad.ns[p], rad.nsm[p], rad.nss[p], lane);
+                float2* t = src;
+                src = dst;
+                dst = t;
+            }
+            __syncwarp();
+            // SFT-start phase in FP64, reduced to cycles; output (-1)^j conj(X_j) / T_sft times it
+            const double cyc = f_h * ((double)b * T_sft);
+            const float c = (float)(cyc - floor(cyc));
+            float sn2, cs;
+            sincospif(2.0f * c, &sn2, &cs);
+            const float2 rot = make_float2(cs, -sn2);
+            for (int j = lane; j < n_prime; j += 32) {
+                const float sg = (j & 1) ? -scale : scale;
+                const float2 a = make_float2(src[j].x * sg, -src[j].y * sg);
+                xo[j] = make_float2(fmaf(a.x, rot.x, -a.y * rot.y), fmaf(a.x, rot.y, a.y * rot.x));
+            }
+            __syncwarp();                              // bufA / bufB reads done before the next pass 0
+        } else {
+            for (int j = lane; j < n_prime; j += 32) xo[j] = make_float2(0.f, 0.f);
+        }
+        s = sn;
+    }
+    cp_async_wait_all();
+}
+
 // N' as radices 4, 2, 3, 5 (fours first); false if another prime divides it.
 bool factor_radices(int64_t n, Radices* rad) {
     rad->n = 0;
@@ -226,15 +381,55 @@ extern "C" cc_status crosscorr_sfts_to_series(const void* band_dev, const int64_
     Radices rad;
     // the FFT holds two N'-point buffers in shared memory (up to 12800 points)
     const bool fft = n_prime <= 12800 && factor_radices(n_prime, &rad) && rad.n > 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    if (fft && n_prime <= 1536) {
+        // persistent warps: three N'-point buffers per warp plus the CTA's twiddle table,
+        // as many warps per CTA (at most 8) as fit in 72 KB; one wave of CTAs
+        const size_t per = 3 * sizeof(float2) * n_prime, tw_b = sizeof(float2) * ((n_prime + 1) & ~1);
+        const int groups = (int)std::max<int64_t>(1, std::min<int64_t>(SS_THREADS / 32, (72 * 1024 - tw_b) / per));
+        const size_t smem = tw_b + per * groups;
+        // the launch shape per (device, N'): the smem attribute and the occupancy query run
+        // once, so that repeated calls (and a stream capture of them) only launch
+        static std::mutex mu;
+        static std::map<std::pair<int, int64_t>, std::pair<int, int>> shapes;   // -> (occupancy, SMs)
+        int dev = 0, occ = 0, sms = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e, "sfts_to_series device");
+        {
+            std::lock_guard<std::mutex> lock(mu);
+            auto it = shapes.find({dev, n_prime});
+            if (it != shapes.end()) {
+                occ = it->second.first;
+                sms = it->second.second;
+            } else {
+                if (smem > 48 * 1024 &&
+                    (e = cudaFuncSetAttribute(sft_fft_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem)) != cudaSuccess)
+                    return cuda_fail(e, "sfts_to_series smem attribute");
+                if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sft_fft_warp_kernel, 32 * groups,
+                                                                        smem)) != cudaSuccess ||
+                    (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+                    return cuda_fail(e, "sfts_to_series occupancy");
+                shapes[{dev, n_prime}] = {occ, sms};
+            }
+        }
+        const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>((n_blocks + groups - 1) / groups,
+                                                                    (int64_t)std::max(1, occ) * sms));
+        sft_fft_warp_kernel<<<(unsigned)ctas, 32 * groups, smem, st>>>((const float2*)band_dev, block_sft_dev,
+                                                                       n_blocks, (int)n_prime, T_sft, f_h, rad,
+                                                                       (float2*)x_dev);
+        count_launch();
+        e = cudaGetLastError();
+        return e == cudaSuccess ? CC_OK : cuda_fail(e, "sft_fft_warp_kernel launch");
+    }
     // twiddles: exp(+2 pi i j / N') for the direct DFT, exp(-2 pi i j / N') for the FFT
     std::vector<float2> tw(n_prime);
     for (int64_t j = 0; j < n_prime; ++j) {
         const double a = 2.0 * M_PI * (double)j / (double)n_prime;
         tw[j] = make_float2((float)cos(a), (float)(fft ? -sin(a) : sin(a)));
     }
-    cudaStream_t st = (cudaStream_t)stream;
     float2* tw_dev = nullptr;
-    cudaError_t e = cudaMallocAsync((void**)&tw_dev, sizeof(float2) * n_prime, st);
+    e = cudaMallocAsync((void**)&tw_dev, sizeof(float2) * n_prime, st);
     if (e != cudaSuccess) return cuda_fail(e, "sfts_to_series twiddles");
     if ((e = cudaMemcpyAsync(tw_dev, tw.data(), sizeof(float2) * n_prime, cudaMemcpyHostToDevice, st)) !=
         cudaSuccess) {
@@ -242,26 +437,21 @@ extern "C" cc_status crosscorr_sfts_to_series(const void* band_dev, const int64_
         return cuda_fail(e, "sfts_to_series twiddles");
     }
     if (fft) {
-        // two N'-point buffers per block.  Up to 1536 points: one warp per block, as many
-        // blocks per CTA as fit in 48 KB (at most 8); larger N': one block per CTA, a group
-        // of up to 256 threads (a quarter of the widest pass's butterflies)
-        const size_t per = 2 * sizeof(float2) * n_prime;
-        const bool warp = n_prime <= 1536;
+        // one block per CTA, a group of up to 256 threads (a quarter of the widest pass's
+        // butterflies), two N'-point buffers
+        const size_t smem = 2 * sizeof(float2) * n_prime;
         int rmin = 5;
         for (int i = 0; i < rad.n; ++i) rmin = std::min(rmin, rad.r[i]);
-        const int gs = warp ? 32 : (int)std::min<int64_t>(SS_THREADS, std::max<int64_t>(32, ((n_prime / rmin / 4 + 31) / 32) * 32));
-        const int groups = warp ? (int)std::max<int64_t>(1, std::min<int64_t>(SS_THREADS / 32, (48 * 1024) / per)) : 1;
-        const size_t smem = per * groups;
-        auto kern = warp ? sft_fft_kernel<true> : sft_fft_kernel<false>;
+        const int gs = (int)std::min<int64_t>(SS_THREADS, std::max<int64_t>(32, ((n_prime / rmin / 4 + 31) / 32) * 32));
         if (smem > 48 * 1024 &&
-            (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) {
+            (e = cudaFuncSetAttribute(sft_fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+                cudaSuccess) {
             cudaFreeAsync(tw_dev, st);
             return cuda_fail(e, "sfts_to_series smem attribute");
         }
-        const int64_t ctas = (n_blocks + groups - 1) / groups;
-        kern<<<(unsigned)ctas, gs * groups, smem, st>>>((const float2*)band_dev, block_sft_dev, n_blocks,
-                                                        (int)n_prime, T_sft, f_h, tw_dev, rad, groups,
-                                                        (float2*)x_dev);
+        sft_fft_kernel<<<(unsigned)n_blocks, gs, smem, st>>>((const float2*)band_dev, block_sft_dev, n_blocks,
+                                                            (int)n_prime, T_sft, f_h, tw_dev, rad, 1,
+                                                            (float2*)x_dev);
     } else {
         const size_t smem = sizeof(float2) * n_prime;
         if (smem > 48 * 1024 &&
