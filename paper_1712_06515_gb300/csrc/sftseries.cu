@@ -70,6 +70,8 @@ struct Radices {
     int ns[SS_MAX_PASSES];        // product of the earlier radices
     uint32_t nsm[SS_MAX_PASSES];  // floor(j / ns) = (j nsm) >> nss (magic_for)
     int nss[SS_MAX_PASSES];
+    int nb[SS_MAX_PASSES];        // butterflies N' / R
+    int tstep[SS_MAX_PASSES];     // twiddle stride N' / (ns R)
 };
 
 constexpr float kC3 = 0.866025403784438647f;    // sin(2 pi / 3)
@@ -234,9 +236,8 @@ __device__ __forceinline__ void dft_r(float2 (&v)[R]) {
 // One Stockham pass of radix R over N' points by one warp (lanes stride the butterflies);
 // CONJ conjugates the inputs (the first pass, reading the staged band).
 template <int R, bool CONJ>
-__device__ __forceinline__ void warp_pass_r(const float2* src, float2* dst, const float2* twf, int n_prime, int ns,
-                                            uint32_t nsm, int nss, int lane) {
-    const int nb = n_prime / R, tstep = n_prime / (ns * R);
+__device__ __forceinline__ void warp_pass_r(const float2* src, float2* dst, const float2* twf, int nb, int tstep,
+                                            int ns, uint32_t nsm, int nss, int lane) {
     for (int j = lane; j < nb; j += 32) {
         const int k = ns == 1 ? 0 : j - (int)(((uint64_t)(uint32_t)j * nsm) >> nss) * ns;   // j mod ns
         float2 v[R];
@@ -261,27 +262,31 @@ __device__ __forceinline__ void warp_pass_r(const float2* src, float2* dst, cons
 }
 
 template <bool CONJ>
-__device__ __forceinline__ void warp_pass(const float2* src, float2* dst, const float2* twf, int n_prime, int R,
-                                          int ns, uint32_t nsm, int nss, int lane) {
-    switch (R) {   // the same for the whole warp
-        case 2: warp_pass_r<2, CONJ>(src, dst, twf, n_prime, ns, nsm, nss, lane); break;
-        case 3: warp_pass_r<3, CONJ>(src, dst, twf, n_prime, ns, nsm, nss, lane); break;
-        case 4: warp_pass_r<4, CONJ>(src, dst, twf, n_prime, ns, nsm, nss, lane); break;
-        default: warp_pass_r<5, CONJ>(src, dst, twf, n_prime, ns, nsm, nss, lane); break;
+__device__ __forceinline__ void warp_pass(const float2* src, float2* dst, const float2* twf, const Radices& rad,
+                                          int p, int lane) {
+    const int nb = rad.nb[p], tstep = rad.tstep[p], ns = rad.ns[p], nss = rad.nss[p];
+    const uint32_t nsm = rad.nsm[p];
+    switch (rad.r[p]) {   // the same for the whole warp
+        case 2: warp_pass_r<2, CONJ>(src, dst, twf, nb, tstep, ns, nsm, nss, lane); break;
+        case 3: warp_pass_r<3, CONJ>(src, dst, twf, nb, tstep, ns, nsm, nss, lane); break;
+        case 4: warp_pass_r<4, CONJ>(src, dst, twf, nb, tstep, ns, nsm, nss, lane); break;
+        default: warp_pass_r<5, CONJ>(src, dst, twf, nb, tstep, ns, nsm, nss, lane); break;
     }
 }
 
-// N' up to 1536: persistent warps, each taking blocks b = w, w + W, ... (W warps in the
-// grid).  Per warp three N'-point shared buffers: the next locked SFT's bins are staged by
-// cp.async while the current one runs its passes, so its HBM latency overlaps the
-// transform; the forward twiddles exp(-2 pi i e / N') are formed once per CTA (FP64).
-// Only warp-level synchronisation after the one CTA barrier of the twiddle table.
+// N' up to 1536: persistent warps, each taking its next T_sft block from a global counter
+// (locked SFTs and gaps fall unevenly on a fixed stride; the counter balances them).  Per
+// warp three N'-point shared buffers: the next locked SFT's bins are staged by cp.async
+// while the current one runs its passes, so its HBM latency overlaps the transform; the
+// forward twiddles exp(-2 pi i e / N') are formed once per CTA (FP64).  Only warp-level
+// synchronisation after the one CTA barrier of the twiddle table.
 __global__ void __launch_bounds__(SS_THREADS)
 sft_fft_warp_kernel(const float2* __restrict__ band, const int64_t* __restrict__ block_sft, int64_t n_blocks,
-                    int n_prime, double T_sft, double f_h, Radices rad, float2* __restrict__ x) {
+                    int n_prime, double T_sft, double f_h, Radices rad, unsigned int* __restrict__ next_block,
+                    float2* __restrict__ x) {
     extern __shared__ __align__(16) float2 sw[];
     float2* twf = sw;                                  // [N' rounded up to even]
-    const int groups = blockDim.x >> 5, g = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float2* stage = sw + ((n_prime + 1) & ~1) + (size_t)g * 3 * n_prime;
     float2* bufA = stage + n_prime;
     float2* bufB = bufA + n_prime;
@@ -291,8 +296,12 @@ sft_fft_warp_kernel(const float2* __restrict__ band, const int64_t* __restrict__
         twf[e] = make_float2((float)cs, (float)sn);
     }
     __syncthreads();
-    const int64_t W = (int64_t)gridDim.x * groups;
-    int64_t b = (int64_t)blockIdx.x * groups + g;
+    auto grab = [&]() -> int64_t {
+        unsigned int v = 0;
+        if (lane == 0) v = atomicAdd(next_block, 1u);
+        return (int64_t)__shfl_sync(0xffffffffu, v, 0);
+    };
+    int64_t b = grab();
     int64_t s = b < n_blocks ? __ldg(block_sft + b) : -1;
     if (s >= 0) {
         const float2* zs = band + s * (int64_t)n_prime;
@@ -300,14 +309,14 @@ sft_fft_warp_kernel(const float2* __restrict__ band, const int64_t* __restrict__
     }
     cp_async_commit();
     const float scale = (float)(1.0 / T_sft);
-    for (; b < n_blocks; b += W) {
-        const int64_t bn = b + W;
+    while (b < n_blocks) {
+        const int64_t bn = grab();
         const int64_t sn = bn < n_blocks ? __ldg(block_sft + bn) : -1;
         float2* xo = x + b * (int64_t)n_prime;
         if (s >= 0) {
             cp_async_wait_all();
             __syncwarp();
-            warp_pass<true>(stage, bufA, twf, n_prime, rad.r[0], rad.ns[0], rad.nsm[0], rad.nss[0], lane);
+            warp_pass<true>(stage, bufA, twf, rad, 0, lane);
             __syncwarp();                              // the stage is free: every lane has read it
         }
         if (sn >= 0) {
@@ -320,7 +329,7 @@ sft_fft_warp_kernel(const float2* __restrict__ band, const int64_t* __restrict__
             float2* dst = bufB;
             for (int p = 1; p < rad.n; ++p) {
                 __syncwarp();
-                warp_pass<false>(src, dst, twf, n_prime, rad.r[p], rad.ns[p], rad.nsm[p], rad.nss[p], lane);
+                warp_pass<false>(src, dst, twf, rad, p, lane);
                 float2* t = src;
                 src = dst;
                 dst = t;
@@ -342,6 +351,7 @@ sft_fft_warp_kernel(const float2* __restrict__ band, const int64_t* __restrict__
             for (int j = lane; j < n_prime; j += 32) xo[j] = make_float2(0.f, 0.f);
         }
         s = sn;
+        b = bn;
     }
     cp_async_wait_all();
 }
@@ -356,6 +366,8 @@ bool factor_radices(int64_t n, Radices* rad) {
             if (rad->n == SS_MAX_PASSES) return false;
             rad->ns[rad->n] = ns;
             magic_for((uint32_t)ns, &rad->nsm[rad->n], &rad->nss[rad->n]);
+            rad->nb[rad->n] = (int)(n / R);
+            rad->tstep[rad->n] = (int)(n / ((int64_t)ns * R));
             rad->r[rad->n++] = R;
             ns *= R;
             m /= R;
@@ -415,11 +427,20 @@ extern "C" cc_status crosscorr_sfts_to_series(const void* band_dev, const int64_
         }
         const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>((n_blocks + groups - 1) / groups,
                                                                     (int64_t)std::max(1, occ) * sms));
+        // the block counter: stream-ordered, zeroed before and freed after the kernel
+        unsigned int* ctr = nullptr;
+        if ((e = cudaMallocAsync((void**)&ctr, sizeof(unsigned int), st)) != cudaSuccess)
+            return cuda_fail(e, "sfts_to_series block counter");
+        if ((e = cudaMemsetAsync(ctr, 0, sizeof(unsigned int), st)) != cudaSuccess) {
+            cudaFreeAsync(ctr, st);
+            return cuda_fail(e, "sfts_to_series block counter");
+        }
         sft_fft_warp_kernel<<<(unsigned)ctas, 32 * groups, smem, st>>>((const float2*)band_dev, block_sft_dev,
                                                                        n_blocks, (int)n_prime, T_sft, f_h, rad,
-                                                                       (float2*)x_dev);
+                                                                       ctr, (float2*)x_dev);
         count_launch();
         e = cudaGetLastError();
+        cudaFreeAsync(ctr, st);
         return e == cudaSuccess ? CC_OK : cuda_fail(e, "sft_fft_warp_kernel launch");
     }
     // twiddles: exp(+2 pi i j / N') for the direct DFT, exp(-2 pi i j / N') for the FFT
