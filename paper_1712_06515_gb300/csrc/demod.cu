@@ -38,7 +38,9 @@ struct DemodTiming {   // per (template, detector, SFT block): 32 bytes
 };
 
 // DFT bins m_lo .. m_lo + nbins - 1 of one T_sft block of detector X, normalised to unit
-// variance; zero for gaps.  Also the block's filter weights (a^, b^, locked).
+// variance, each times (-1)^m: the two-bin interpolation's alternating sign
+// (-1)^m0 (s0 z_m0 - s1 z_(m0+1)) is then s0 z'_m0 + s1 z'_(m0+1).  Zero for gaps.  Also the
+// block's filter weights (a^, b^, locked).
 __global__ void __launch_bounds__(SFT_THREADS)
 sft_kernel(DevParams p, int nsft, int m_lo, int nbins, int n_blk, const float2* __restrict__ tw,
            float2* __restrict__ z, float4* __restrict__ wts) {
@@ -86,7 +88,8 @@ sft_kernel(DevParams p, int nsft, int m_lo, int nbins, int n_blk, const float2* 
             idx += step;
             idx -= idx >= nsft ? nsft : 0;
         }
-        zo[i] = make_float2(acc.x * norm, acc.y * norm);
+        const float sn = (m & 1) ? -norm : norm;         // stored times (-1)^m (see below)
+        zo[i] = make_float2(acc.x * sn, acc.y * sn);
     }
 }
 
@@ -160,15 +163,22 @@ __global__ void demod_timing_list_kernel(DevParams p, const cc_template* __restr
                                          const float4* __restrict__ wts, DemodTiming* __restrict__ out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t t = blockIdx.y;
-    if (i >= n_list) return;
-    const int key = __ldg(list + i);
-    const int l = key >> 2, X = key & 3;
-    DemodTiming r = demod_timing(p, tm[t], nsft, l, X, df0, dK);
-    const float4 wk = __ldg(wts + (size_t)X * n_blk + l);
-    r.pad0 = wk.x;
-    r.pad1 = wk.y;
-    r.pad2 = __int_as_float(key);
-    out[(size_t)t * n_list + i] = r;
+    if (i >= n_list + 2) return;
+    DemodTiming r;
+    if (i >= n_list) {                                 // padding: no bins (x far below the band)
+        r.A0 = -1.0e9f;
+        r.A1 = r.C0 = r.C1 = r.C128 = r.pad0 = r.pad1 = 0.f;
+        r.pad2 = __int_as_float(__ldg(list + n_list - 1));
+    } else {
+        const int key = __ldg(list + i);
+        const int l = key >> 2, X = key & 3;
+        r = demod_timing(p, tm[t], nsft, l, X, df0, dK);
+        const float4 wk = __ldg(wts + (size_t)X * n_blk + l);
+        r.pad0 = wk.x * 0.316227766016837933f;         // a^ / sqrt(10)
+        r.pad1 = wk.y * 0.316227766016837933f;
+        r.pad2 = __int_as_float(key);
+    }
+    out[(size_t)t * (n_list + 2) + i] = r;
 }
 
 // One thread per (template, output bin): the pair loop over time-ordered SFTs.  The ring
@@ -224,9 +234,8 @@ __global__ void demod_pair_kernel(DevParams p, int nsft, int m_lo, int nbins, in
             float2 y = make_float2(0.f, 0.f);
             if (act && idx >= 0 && idx + 1 < nbins) {
                 const float2* zk = z + ((size_t)X * n_blk + l) * nbins + idx;
-                const float2 z0 = __ldg(zk), z1 = __ldg(zk + 1);
-                const float sg = (m0 & 1) ? -1.f : 1.f;
-                const float2 u = make_float2(sg * (s0 * z0.x - s1 * z1.x), sg * (s0 * z0.y - s1 * z1.y));
+                const float2 z0 = __ldg(zk), z1 = __ldg(zk + 1);   // bins times (-1)^m
+                const float2 u = make_float2(fmaf(s0, z0.x, s1 * z1.x), fmaf(s0, z0.y, s1 * z1.y));
                 float cyc = fmaf(kl, tr.C1, fmaf(kh, tr.C128, tr.C0));
                 cyc -= floorf(cyc);
                 float sn, cs;
@@ -302,12 +311,11 @@ __device__ __forceinline__ void sep_add_sft(SepSums& a, float2 y, float xi2, flo
     a.ubb = fmaf(xb, wk.y, a.ubb);
 }
 
-// One SFT's inputs for the separable kernel, fetched ahead of its arithmetic: the signal
-// bin position (floor m0 and kappa = m0 - x), the heterodyne phase in cycles, and the two
-// bins m0, m0 + 1 (zero when out of the stored band).
+// One SFT's inputs for the separable kernel, fetched ahead of its arithmetic: kappa =
+// floor(x) - x of the signal bin position, the heterodyne phase in cycles reduced to
+// [-1/2, 1/2], and the two stored bins floor(x), floor(x) + 1 (zero when out of the band).
 struct SftIn {
     float k0, cyc;
-    int m0;
     float2 z0, z1;
 };
 
@@ -339,11 +347,9 @@ __device__ __forceinline__ float2 sft_y(const SftIn& q, float& xi2) {
     const float other = -__fdividef(r * sv, far);
     const float s0 = near0 ? sv : other, s1 = near0 ? other : sv;
     xi2 = s0 * s0 + s1 * s1;
-    const float sg = (q.m0 & 1) ? -1.f : 1.f;
-    const float2 u = make_float2(sg * (s0 * q.z0.x - s1 * q.z1.x), sg * (s0 * q.z0.y - s1 * q.z1.y));
-    const float c = q.cyc >= 0.5f ? q.cyc - 1.f : q.cyc;
+    const float2 u = make_float2(fmaf(s0, q.z0.x, s1 * q.z1.x), fmaf(s0, q.z0.y, s1 * q.z1.y));
     float sn, cs;
-    __sincosf(6.28318530717958648f * c, &sn, &cs);
+    __sincosf(6.28318530717958648f * q.cyc, &sn, &cs);
     return make_float2(fmaf(u.x, cs, u.y * sn), fmaf(u.y, cs, -u.x * sn));
 }
 
@@ -358,18 +364,17 @@ __device__ __forceinline__ SepRec load_rec(const DemodTiming* __restrict__ r) {
     return SepRec{__ldg(q), __ldg(q + 1)};
 }
 
-__device__ __forceinline__ void rec_fetch(SftIn& q, const SepRec& r, float df, float kh, float kl, bool act, int m_lo,
+__device__ __forceinline__ void rec_fetch(SftIn& q, const SepRec& r, float df, float kh, float kl, int m_lo,
                                           int nbins, int n_blk, const float2* __restrict__ z) {
     const int key = __float_as_int(r.t1.w);
     const float x = fmaf(df, r.t0.y, r.t0.x);
     const float fm = floorf(x);
     q.k0 = fm - x;
-    q.m0 = (int)fm;
-    const int idx = q.m0 - m_lo;
+    const int idx = (int)fm - m_lo;
     const float cyc = fmaf(kl, r.t0.w, fmaf(kh, r.t1.x, r.t0.z));
-    q.cyc = cyc - floorf(cyc);
+    q.cyc = cyc - rintf(cyc);
     q.z0 = q.z1 = make_float2(0.f, 0.f);
-    if (act && idx >= 0 && idx + 1 < nbins) {
+    if (idx >= 0 && idx + 1 < nbins) {
         const float2* zr = z + ((size_t)(key & 3) * n_blk + (key >> 2)) * nbins + idx;
         q.z0 = __ldg(zr);
         q.z1 = __ldg(zr + 1);
@@ -377,10 +382,14 @@ __device__ __forceinline__ void rec_fetch(SftIn& q, const SepRec& r, float df, f
 }
 
 // One thread per (template, output bin) walks the list of locked SFTs in time order (gaps
-// never enter the loop).  The SFT records of one template are shared by its CTAs.  Block
+// never enter the loop).  The SFT records of one template are shared by its CTAs; their
+// filter weights come scaled by 1/sqrt(10), so Gamma_KL = a^'_K a^'_L + b^'_K b^'_L and the
+// factors 1/10 and 1/100 drop out (the pair sum is then half the statistic's raw sum).
+// V holds the sums over SFT K's partners so far (window W plus the current block); block
 // sums go to the window when the block index changes: one step adds s_l and subtracts
 // s_(l - R_s); a jump over empty blocks, and every 4 (R_s + 1) steps, sums the window
-// exactly.
+// exactly.  The record list carries two padding records (no bins) past its end so that
+// the pipeline's loads need no guards.
 template <bool RING>
 __global__ void __launch_bounds__(128) demod_sep_kernel(DevParams p, int m_lo, int nbins, int n_blk, int Rs, int refresh,
                                  const float2* __restrict__ z, const DemodTiming* __restrict__ recs, int n_list,
@@ -391,15 +400,16 @@ __global__ void __launch_bounds__(128) demod_sep_kernel(DevParams p, int m_lo, i
     const int64_t t = t_base + blockIdx.y;
     const int k = blockIdx.x * nthr + tid;
     const bool act = k < (int)p.N_f;
-    const DemodTiming* rt = recs + (size_t)(t - t_base) * n_list;
+    const DemodTiming* rt = recs + (size_t)(t - t_base) * (n_list + 2);
     if (n_list == 0) {                                 // no locked SFT
         if (act) rho[(size_t)t * p.N_f + k] = 0.f;
         return;
     }
     if (RING)
         for (int j = 0; j < (Rs + 1) * 7; ++j) sring[(size_t)j * nthr + tid] = 0.f;
-    const float df = act ? (float)__ldg(dfreq + k) : 0.f;
-    const int64_t kb = act ? __ldg(kbar + k) : 0;
+    // threads past the last bin compute bin 0's statistic and store nothing
+    const float df = (float)__ldg(dfreq + (act ? k : 0));
+    const int64_t kb = __ldg(kbar + (act ? k : 0));
     const float kh = (float)(kb >> 7), kl = (float)(kb & 127);
     auto ring_get = [&](int slot) {
         const float* r = sring + (size_t)slot * 7 * nthr + tid;
@@ -422,16 +432,16 @@ __global__ void __launch_bounds__(128) demod_sep_kernel(DevParams p, int m_lo, i
         for (int i = __ldg(boff + j); i < e; ++i) {
             const SepRec r = load_rec(rt + i);
             SftIn q;
-            rec_fetch(q, r, df, kh, kl, act, m_lo, nbins, n_blk, z);
+            rec_fetch(q, r, df, kh, kl, m_lo, nbins, n_blk, z);
             float xi2;
             const float2 y = sft_y(q, xi2);
             sep_add_sft(sj, y, xi2, make_float4(r.t1.y, r.t1.z, 1.f, 0.f));
         }
     };
     float raw = 0.f, rawc = 0.f, den = 0.f, denc = 0.f;
-    SepSums W, P;
+    SepSums W, V;
     sep_zero(W);
-    sep_zero(P);
+    sep_zero(V);
     int steps = 0;
     int lcur = 0, scur = 0;                            // block lcur and its ring slot lcur mod (R_s + 1)
     // the pair and normalisation terms go to plain FP32 partial sums that join the
@@ -443,19 +453,21 @@ __global__ void __launch_bounds__(128) demod_sep_kernel(DevParams p, int m_lo, i
     // read) load while SFT i is summed; two calls per iteration with the roles swapped keep
     // the pipeline in place without register copies.
     auto step = [&](SepRec& Rc, SftIn& Fc, const SepRec& Rn, SftIn& Fn, int i) {
-        if (i + 1 < n_list) rec_fetch(Fn, Rn, df, kh, kl, act, m_lo, nbins, n_blk, z);
+        rec_fetch(Fn, Rn, df, kh, kl, m_lo, nbins, n_blk, z);
         const float4 wk = make_float4(Rc.t1.y, Rc.t1.z, 1.f, 0.f);
         const int l = __float_as_int(Rc.t1.w) >> 2;
-        if (i + 2 < n_list) Rc = load_rec(rt + i + 2);
+        Rc = load_rec(rt + i + 2);
         if (l != lcur) {                               // block lcur is complete: the window of block l
             if (Rs > 0) {
                 if (RING) {
                     const bool step1 = l == lcur + 1 && ++steps < refresh;
-                    ring_put(scur, P);
+                    SepSums Pb = V;                    // block lcur's sums
+                    sep_axpy(Pb, W, -1.f);
+                    ring_put(scur, Pb);
                     if (step1) {
                         scur = scur == Rs ? 0 : scur + 1;       // slot of l: s_(l - R_s - 1) = s_(lcur - R_s)
                         const SepSums old = ring_get(scur);
-                        sep_axpy(W, P, 1.f);
+                        W = V;
                         sep_axpy(W, old, -1.f);
                     } else {
                         const SepSums zero{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -474,23 +486,25 @@ __global__ void __launch_bounds__(128) demod_sep_kernel(DevParams p, int m_lo, i
                     sep_zero(W);
                     steps = 0;
                 } else if (++steps < refresh) {        // blocks lcur - R_s .. l - R_s - 1 leave
-                    sep_axpy(W, P, 1.f);
+                    W = V;
                     for (int j = max(0, lcur - Rs); j < l - Rs; ++j) {
                         SepSums old;
                         block_sums(j, old);
                         sep_axpy(W, old, -1.f);
                     }
                 } else {
-                    W = P;                             // blocks l - R_s .. lcur (those after are empty)
+                    SepSums Wn = V;                    // blocks l - R_s .. lcur (those after are empty)
+                    sep_axpy(Wn, W, -1.f);
                     for (int j = max(0, l - Rs); j < lcur; ++j) {
                         SepSums sj;
                         block_sums(j, sj);
-                        sep_axpy(W, sj, 1.f);
+                        sep_axpy(Wn, sj, 1.f);
                     }
+                    W = Wn;
                     steps = 0;
                 }
             }
-            sep_zero(P);
+            V = W;
             lcur = l;
             if (steps == 0 || nacc >= 64) {
                 kahan_add(raw, rawc, raw_p);
@@ -501,20 +515,17 @@ __global__ void __launch_bounds__(128) demod_sep_kernel(DevParams p, int m_lo, i
         }
         float xi2;
         const float2 y = sft_y(Fc, xi2);
-        const float sax = W.ayx + P.ayx, say = W.ayy + P.ayy, sbx = W.byx + P.byx, sby = W.byy + P.byy;
-        const float gx = fmaf(wk.x, sax, wk.y * sbx), gy = fmaf(wk.x, say, wk.y * sby);
-        const float pr = 0.2f * fmaf(y.x, gx, y.y * gy);          // 2 Re(conj(y) g) / 10
-        const float nq = fmaf(wk.x * wk.x, W.uaa + P.uaa,
-                              fmaf(2.f * wk.x * wk.y, W.uab + P.uab, wk.y * wk.y * (W.ubb + P.ubb)));
-        raw_p += pr;
-        den_p = fmaf(0.01f * xi2, nq, den_p);
+        const float gx = fmaf(wk.x, V.ayx, wk.y * V.byx), gy = fmaf(wk.x, V.ayy, wk.y * V.byy);
+        raw_p = fmaf(y.x, gx, fmaf(y.y, gy, raw_p));                 // Re(conj(y) g)
+        const float nq = fmaf(wk.x * wk.x, V.uaa, fmaf(2.f * wk.x * wk.y, V.uab, wk.y * wk.y * V.ubb));
+        den_p = fmaf(xi2, nq, den_p);
         ++nacc;
-        sep_add_sft(P, y, xi2, wk);
+        sep_add_sft(V, y, xi2, wk);
     };
     SepRec ra = load_rec(rt);
-    SepRec rb = n_list > 1 ? load_rec(rt + 1) : ra;
+    SepRec rb = load_rec(rt + 1);
     SftIn fa, fb;
-    rec_fetch(fa, ra, df, kh, kl, act, m_lo, nbins, n_blk, z);
+    rec_fetch(fa, ra, df, kh, kl, m_lo, nbins, n_blk, z);
     lcur = __float_as_int(ra.t1.w) >> 2;
     scur = lcur % (Rs + 1);
     int i = 0;
@@ -525,7 +536,8 @@ __global__ void __launch_bounds__(128) demod_sep_kernel(DevParams p, int m_lo, i
     if (i < n_list) step(ra, fa, rb, fb, i);
     kahan_add(raw, rawc, raw_p);
     kahan_add(den, denc, den_p);
-    if (act) rho[(size_t)t * p.N_f + k] = den > 0.f ? raw / sqrtf(2.f * den) : 0.f;
+    // rho = (2 raw) / sqrt(2 den)
+    if (act) rho[(size_t)t * p.N_f + k] = den > 0.f ? 1.41421356237309505f * raw * rsqrtf(den) : 0.f;
 }
 
 }  // namespace
@@ -676,7 +688,7 @@ extern "C" cc_status crosscorr_demod_search(cc_plan* plan, const cc_template* t_
     // timing records for a batch of templates: every (X, l) for the pair loop, the list of
     // locked SFTs for the separable form
     const int n_list = plan->demod_nlist;
-    const size_t per_t = sizeof(DemodTiming) * (sep ? (size_t)std::max(1, n_list) : (size_t)p.Q * n_blk);
+    const size_t per_t = sizeof(DemodTiming) * (sep ? (size_t)n_list + 2 : (size_t)p.Q * n_blk);
     const int64_t batch = std::max<int64_t>(1, std::min<int64_t>({n_t, (int64_t)((size_t)2 << 30) / (int64_t)per_t, 65535}));
     cc_status s = ensure_workspace(plan, per_t * batch);
     if (s != CC_OK) return s;
@@ -694,7 +706,7 @@ extern "C" cc_status crosscorr_demod_search(cc_plan* plan, const cc_template* t_
             demod_timing_kernel<<<dim3((unsigned)((n_blk + 127) / 128), (unsigned)p.Q, (unsigned)nb), 128, 0, st>>>(
                 p, t_dev + t0, nsft, n_blk, df0, dK, (DemodTiming*)plan->ws);
         else if (n_list > 0)
-            demod_timing_list_kernel<<<dim3((unsigned)((n_list + 127) / 128), (unsigned)nb), 128, 0, st>>>(
+            demod_timing_list_kernel<<<dim3((unsigned)((n_list + 2 + 127) / 128), (unsigned)nb), 128, 0, st>>>(
                 p, t_dev + t0, nsft, n_blk, df0, dK, (const int*)plan->demod_list, n_list,
                 (const float4*)plan->demod_w, (DemodTiming*)plan->ws);
         if (!sep || n_list > 0) count_launch();
