@@ -147,17 +147,9 @@ __device__ DemodTiming demod_timing(const DevParams& p, const cc_template& T, in
     return r;
 }
 
-__global__ void demod_timing_kernel(DevParams p, const cc_template* __restrict__ tm, int nsft, int n_blk,
-                                    double df0, double dK, DemodTiming* __restrict__ out) {
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
-    const int X = blockIdx.y;
-    const int64_t t = blockIdx.z;
-    if (l >= n_blk) return;
-    out[((size_t)t * p.Q + X) * n_blk + l] = demod_timing(p, tm[t], nsft, l, X, df0, dK);
-}
-
-// The separable kernel's records: one per locked SFT of the time-ordered list, the timing
-// of demod_timing with the SFT's filter weights and list key (4 l + X) in the spare words.
+// The search kernels' records: one per locked SFT of the time-ordered list, the timing of
+// demod_timing with the SFT's filter weights (divided by sqrt(10)) and list key (4 l + X) in
+// the spare words; two padding records (no bins) follow the list.
 __global__ void demod_timing_list_kernel(DevParams p, const cc_template* __restrict__ tm, int nsft, int n_blk,
                                          double df0, double dK, const int* __restrict__ list, int n_list,
                                          const float4* __restrict__ wts, DemodTiming* __restrict__ out) {
@@ -179,96 +171,6 @@ __global__ void demod_timing_list_kernel(DevParams p, const cc_template* __restr
         r.pad2 = __int_as_float(key);
     }
     out[(size_t)t * (n_list + 2) + i] = r;
-}
-
-// One thread per (template, output bin): the pair loop over time-ordered SFTs.  The ring
-// holds the last (R_s + 1) blocks' y and Xi^2 per thread (thread-private columns of
-// shared memory) and the blocks' filter weights (shared by the CTA).
-__global__ void demod_pair_kernel(DevParams p, int nsft, int m_lo, int nbins, int n_blk, int Rs,
-                                  const float2* __restrict__ z, const float4* __restrict__ wts,
-                                  const DemodTiming* __restrict__ tq, const double* __restrict__ dfreq,
-                                  const int64_t* __restrict__ kbar, int64_t t_base, float* __restrict__ rho) {
-    extern __shared__ __align__(16) unsigned char sm[];
-    const int nthr = blockDim.x, tid = threadIdx.x;
-    const int Q = p.Q;
-    const int W = (Rs + 1) * Q;                        // ring slots: block l at slots (l mod (Rs+1)) Q + X
-    float2* ry = (float2*)sm;                          // [W][nthr]
-    float* rx = (float*)(ry + (size_t)W * nthr);       // [W][nthr] Xi^2
-    float2* rab = (float2*)(rx + (size_t)W * nthr);    // [W] (a^, b^)
-    int* rblk = (int*)(rab + W);                       // [W] block index held, -1 empty
-    const int64_t t = t_base + blockIdx.y;
-    const int k = blockIdx.x * nthr + tid;
-    const bool act = k < (int)p.N_f;
-    for (int j = tid; j < W; j += nthr) rblk[j] = -1;
-    const float df = act ? (float)__ldg(dfreq + k) : 0.f;
-    const int64_t kb = act ? __ldg(kbar + k) : 0;
-    const float kh = (float)(kb >> 7), kl = (float)(kb & 127);
-    float raw = 0.f, rawc = 0.f, den = 0.f, denc = 0.f;
-    __syncthreads();
-    for (int l = 0; l < n_blk; ++l) {
-        const int base = (l % (Rs + 1)) * Q;
-        for (int X = 0; X < Q; ++X) {
-            const float4 wk = __ldg(wts + (size_t)X * n_blk + l);
-            const int slot = base + X;
-            if (wk.z == 0.f) {                          // gap: no SFT (uniform across the CTA)
-                __syncthreads();
-                if (tid == 0) rblk[slot] = -1;
-                __syncthreads();
-                continue;
-            }
-            const DemodTiming tr = tq[((size_t)(t - t_base) * Q + X) * n_blk + l];
-            const float x = fmaf(df, tr.A1, tr.A0);
-            const float fm = floorf(x);
-            const float k0 = fm - x;                   // kappa of bin floor(x), in (-1, 0]
-            float s0, s1;
-            if (k0 == 0.f) {
-                s0 = 1.f;
-                s1 = 0.f;
-            } else {
-                const float sp = sinpif(k0) * 0.318309886183790672f;   // sin(pi kappa)/pi
-                s0 = __fdividef(sp, k0);
-                s1 = -__fdividef(sp, k0 + 1.f);        // sin(pi (kappa + 1)) = -sin(pi kappa)
-            }
-            const int m0 = (int)fm;
-            const int idx = m0 - m_lo;
-            float2 y = make_float2(0.f, 0.f);
-            if (act && idx >= 0 && idx + 1 < nbins) {
-                const float2* zk = z + ((size_t)X * n_blk + l) * nbins + idx;
-                const float2 z0 = __ldg(zk), z1 = __ldg(zk + 1);   // bins times (-1)^m
-                const float2 u = make_float2(fmaf(s0, z0.x, s1 * z1.x), fmaf(s0, z0.y, s1 * z1.y));
-                float cyc = fmaf(kl, tr.C1, fmaf(kh, tr.C128, tr.C0));
-                cyc -= floorf(cyc);
-                float sn, cs;
-                sincospif(2.0f * cyc, &sn, &cs);
-                y = make_float2(fmaf(u.x, cs, u.y * sn), fmaf(u.y, cs, -u.x * sn));   // u exp(-2 pi i cyc)
-            }
-            const float xi2 = s0 * s0 + s1 * s1;
-            // partners: the blocks l - Rs .. l - 1 (every detector) and block l's earlier detectors
-            float pr = 0.f, pd = 0.f;
-            for (int j = 0; j < W; ++j) {
-                const int bj = rblk[j];
-                if (bj < 0 || l - bj > Rs) continue;
-                if (bj == l && j - base >= X) continue;
-                const float2 ab = rab[j];
-                const float g = 0.1f * fmaf(wk.x, ab.x, wk.y * ab.y);
-                const float2 yl = ry[(size_t)j * nthr + tid];
-                pr = fmaf(g, 2.f * fmaf(y.x, yl.x, y.y * yl.y), pr);
-                const float q = g * g * rx[(size_t)j * nthr + tid];
-                pd = fmaf(xi2, q, pd);
-            }
-            kahan_add(raw, rawc, pr);
-            kahan_add(den, denc, pd);
-            __syncthreads();                            // every thread is done with the old slot
-            ry[(size_t)slot * nthr + tid] = y;
-            rx[(size_t)slot * nthr + tid] = xi2;
-            if (tid == 0) {
-                rab[slot] = make_float2(wk.x, wk.y);
-                rblk[slot] = l;
-            }
-            __syncthreads();
-        }
-    }
-    if (act) rho[(size_t)t * p.N_f + k] = den > 0.f ? raw / sqrtf(2.f * den) : 0.f;
 }
 
 // The same statistic in separable form.  The geometric filter Gamma_KL = (a^_K a^_L +
@@ -540,6 +442,90 @@ __global__ void __launch_bounds__(128) demod_sep_kernel(DevParams p, int m_lo, i
     if (act) rho[(size_t)t * p.N_f + k] = den > 0.f ? 1.41421356237309505f * raw * rsqrtf(den) : 0.f;
 }
 
+// The method's pair loop: one thread per (template, output bin) over the locked SFTs in
+// time order (the separable kernel's records and pipelined loads).  A ring of R_s + 1
+// blocks holds, per slot (block mod (R_s + 1), detector), the thread's y and Xi^2
+// (thread-private columns of shared memory) and the SFT's prescaled filter weights
+// (shared).  A slot that is not a partner of the current SFT -- a block outside the
+// window, a gap, a later detector of the current block -- has zero weights, so the
+// partner loop is one fixed-length sum without branches: Gamma_KL = a^'_K a^'_L + b^'_K b^'_L
+// per slot, 12 flops per pair as in the paper's loop.  Before the first SFT of a block the
+// slots of that block (and of any skipped block) are cleared.
+__global__ void __launch_bounds__(256) demod_pair_kernel(DevParams p, int m_lo, int nbins, int n_blk, int Rs,
+                                                         const float2* __restrict__ z,
+                                                         const DemodTiming* __restrict__ recs, int n_list,
+                                                         const double* __restrict__ dfreq,
+                                                         const int64_t* __restrict__ kbar, int64_t t_base,
+                                                         float* __restrict__ rho) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int nthr = blockDim.x, tid = threadIdx.x;
+    const int Q = p.Q, W = (Rs + 1) * Q;
+    float2* ry = (float2*)sm;                          // [W][nthr] y
+    float* rx = (float*)(ry + (size_t)W * nthr);       // [W][nthr] Xi^2
+    float2* rab = (float2*)(rx + (size_t)W * nthr);    // [W] (a^', b^'), zero: not a partner
+    const int64_t t = t_base + blockIdx.y;
+    const int k = blockIdx.x * nthr + tid;
+    const bool act = k < (int)p.N_f;
+    const DemodTiming* rt = recs + (size_t)(t - t_base) * (n_list + 2);
+    for (int j = 0; j < W; ++j) {
+        ry[(size_t)j * nthr + tid] = make_float2(0.f, 0.f);
+        rx[(size_t)j * nthr + tid] = 0.f;
+    }
+    for (int j = tid; j < W; j += nthr) rab[j] = make_float2(0.f, 0.f);
+    if (n_list == 0) {
+        if (act) rho[(size_t)t * p.N_f + k] = 0.f;
+        return;
+    }
+    __syncthreads();
+    const float df = (float)__ldg(dfreq + (act ? k : 0));
+    const int64_t kb = __ldg(kbar + (act ? k : 0));
+    const float kh = (float)(kb >> 7), kl = (float)(kb & 127);
+    float raw = 0.f, rawc = 0.f, den = 0.f, denc = 0.f;
+    auto step = [&](SepRec& Rc, SftIn& Fc, const SepRec& Rn, SftIn& Fn, int i) {
+        rec_fetch(Fn, Rn, df, kh, kl, m_lo, nbins, n_blk, z);
+        const float a = Rc.t1.y, b = Rc.t1.z;
+        const int key = __float_as_int(Rc.t1.w);
+        const int l = key >> 2, X = key & 3;
+        const int ln = __float_as_int(Rn.t1.w) >> 2;    // block of SFT i + 1 (padding: the last block)
+        Rc = load_rec(rt + i + 2);
+        float xi2;
+        const float2 y = sft_y(Fc, xi2);
+        float pr = 0.f, pq = 0.f;
+        for (int j = 0; j < W; ++j) {
+            const float2 ab = rab[j];
+            const float g = fmaf(a, ab.x, b * ab.y);
+            const float2 yl = ry[(size_t)j * nthr + tid];
+            pr = fmaf(g, fmaf(y.x, yl.x, y.y * yl.y), pr);
+            pq = fmaf(g * g, rx[(size_t)j * nthr + tid], pq);
+        }
+        kahan_add(raw, rawc, pr);
+        kahan_add(den, denc, xi2 * pq);
+        __syncthreads();                               // every thread is done with the ring
+        const int slot = (l % (Rs + 1)) * Q + X;
+        ry[(size_t)slot * nthr + tid] = y;
+        rx[(size_t)slot * nthr + tid] = xi2;
+        if (tid == 0) {
+            rab[slot] = make_float2(a, b);
+            // SFT i + 1 opens block ln: clear the slots of blocks l + 1 .. ln (at most all)
+            for (int bb = l + 1; bb <= ln && bb <= l + Rs + 1; ++bb)
+                for (int x2 = 0; x2 < Q; ++x2) rab[(bb % (Rs + 1)) * Q + x2] = make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+    };
+    SepRec ra = load_rec(rt);
+    SepRec rb = load_rec(rt + 1);
+    SftIn fa, fb;
+    rec_fetch(fa, ra, df, kh, kl, m_lo, nbins, n_blk, z);
+    int i = 0;
+    for (; i + 1 < n_list; i += 2) {
+        step(ra, fa, rb, fb, i);
+        step(rb, fb, ra, fa, i + 1);
+    }
+    if (i < n_list) step(ra, fa, rb, fb, i);
+    // rho = (2 raw) / sqrt(2 den)
+    if (act) rho[(size_t)t * p.N_f + k] = den > 0.f ? 1.41421356237309505f * raw * rsqrtf(den) : 0.f;
+}
+
 }  // namespace
 }  // namespace cc
 
@@ -673,22 +659,21 @@ extern "C" cc_status crosscorr_demod_search(cc_plan* plan, const cc_template* t_
     const int Rs = (int)std::floor(plan->cfg.T_max / Tsft + 1e-9);
     const int W = (Rs + 1) * p.Q;
     const bool sep = plan->demod_form == CC_DEMOD_SEPARABLE;
+    const int n_list = plan->demod_nlist;
     // separable form: 128 threads, the ring of block sums while it stays within DM_SEP_RING
     const bool sep_ring = sep && (size_t)(Rs + 1) * 7 * 128 * sizeof(float) <= DM_SEP_RING;
     int nthr = sep ? 128 : 256;
     auto ring_bytes = [&](int nt) {
         return sep ? (sep_ring ? (size_t)(Rs + 1) * 7 * nt * sizeof(float) : 0)
-                   : (size_t)W * nt * 12 + (size_t)W * 12 + 64;
+                   : (size_t)W * nt * 12 + (size_t)W * 8;
     };
     while (nthr > 32 && ring_bytes(nthr) > DM_RING_BUDGET) nthr /= 2;
     if (ring_bytes(nthr) > DM_RING_BUDGET) return fail(CC_ERR_UNSUPPORTED, "T_max / T_sft too large for the pair ring");
     // exact window sum (over the ring, or recomputed from the bins) after 4 (R_s + 1)
     // single-block steps: the FP32 rounding of the running sums cannot drift further
     const int refresh = 4 * (Rs + 1);
-    // timing records for a batch of templates: every (X, l) for the pair loop, the list of
-    // locked SFTs for the separable form
-    const int n_list = plan->demod_nlist;
-    const size_t per_t = sizeof(DemodTiming) * (sep ? (size_t)n_list + 2 : (size_t)p.Q * n_blk);
+    // timing records for a batch of templates: the list of locked SFTs plus two padding
+    const size_t per_t = sizeof(DemodTiming) * ((size_t)n_list + 2);
     const int64_t batch = std::max<int64_t>(1, std::min<int64_t>({n_t, (int64_t)((size_t)2 << 30) / (int64_t)per_t, 65535}));
     cc_status s = ensure_workspace(plan, per_t * batch);
     if (s != CC_OK) return s;
@@ -702,14 +687,12 @@ extern "C" cc_status crosscorr_demod_search(cc_plan* plan, const cc_template* t_
     const double df0 = plan->f_r - 0.5 / plan->cfg.dt, dK = 1.0 / plan->T_FFT;
     for (int64_t t0 = 0; t0 < n_t; t0 += batch) {
         const int64_t nb = std::min(batch, n_t - t0);
-        if (!sep)
-            demod_timing_kernel<<<dim3((unsigned)((n_blk + 127) / 128), (unsigned)p.Q, (unsigned)nb), 128, 0, st>>>(
-                p, t_dev + t0, nsft, n_blk, df0, dK, (DemodTiming*)plan->ws);
-        else if (n_list > 0)
+        if (n_list > 0) {
             demod_timing_list_kernel<<<dim3((unsigned)((n_list + 2 + 127) / 128), (unsigned)nb), 128, 0, st>>>(
                 p, t_dev + t0, nsft, n_blk, df0, dK, (const int*)plan->demod_list, n_list,
                 (const float4*)plan->demod_w, (DemodTiming*)plan->ws);
-        if (!sep || n_list > 0) count_launch();
+            count_launch();
+        }
         cudaEvent_t ev0, ev1;   // diagnostic timing of the pair loop (crosscorr_plan_set_kernel_timing)
         timing_pair(plan, &ev0, &ev1);
         if (ev0) cudaEventRecord(ev0, st);
@@ -721,8 +704,8 @@ extern "C" cc_status crosscorr_demod_search(cc_plan* plan, const cc_template* t_
                 (const int64_t*)plan->demod_kbar, t0, rho_dev);
         else
             demod_pair_kernel<<<grid, nthr, smem, st>>>(
-                p, nsft, plan->demod_m_lo, plan->demod_nbins, n_blk, Rs, (const float2*)plan->demod_z,
-                (const float4*)plan->demod_w, (const DemodTiming*)plan->ws, (const double*)plan->demod_df,
+                p, plan->demod_m_lo, plan->demod_nbins, n_blk, Rs, (const float2*)plan->demod_z,
+                (const DemodTiming*)plan->ws, n_list, (const double*)plan->demod_df,
                 (const int64_t*)plan->demod_kbar, t0, rho_dev);
         count_launch();
         if (ev1) cudaEventRecord(ev1, st);
