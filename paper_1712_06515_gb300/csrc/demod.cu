@@ -448,9 +448,11 @@ __global__ void __launch_bounds__(128) demod_sep_kernel(DevParams p, int m_lo, i
 // (thread-private columns of shared memory) and the SFT's prescaled filter weights
 // (shared).  A slot that is not a partner of the current SFT -- a block outside the
 // window, a gap, a later detector of the current block -- has zero weights, so the
-// partner loop is one fixed-length sum without branches: Gamma_KL = a^'_K a^'_L + b^'_K b^'_L
-// per slot, 12 flops per pair as in the paper's loop.  Before the first SFT of a block the
-// slots of that block (and of any skipped block) are cleared.
+// partner loop is one fixed-length sum without branches.  The filter weights
+// Gamma_KL = a^'_K a^'_L + b^'_K b^'_L of the next SFT against every slot are formed once
+// per CTA (slot j by thread j mod blockDim) while the ring is updated, so the loop reads
+// one shared value per slot.  Before the first SFT of a block the slots of that block
+// (and of any skipped block) are cleared.
 __global__ void __launch_bounds__(256) demod_pair_kernel(DevParams p, int m_lo, int nbins, int n_blk, int Rs,
                                                          const float2* __restrict__ z,
                                                          const DemodTiming* __restrict__ recs, int n_list,
@@ -463,6 +465,7 @@ __global__ void __launch_bounds__(256) demod_pair_kernel(DevParams p, int m_lo, 
     float2* ry = (float2*)sm;                          // [W][nthr] y
     float* rx = (float*)(ry + (size_t)W * nthr);       // [W][nthr] Xi^2
     float2* rab = (float2*)(rx + (size_t)W * nthr);    // [W] (a^', b^'), zero: not a partner
+    float* sg = (float*)(rab + W);                     // [W] Gamma of the current SFT per slot
     const int64_t t = t_base + blockIdx.y;
     const int k = blockIdx.x * nthr + tid;
     const bool act = k < (int)p.N_f;
@@ -471,7 +474,10 @@ __global__ void __launch_bounds__(256) demod_pair_kernel(DevParams p, int m_lo, 
         ry[(size_t)j * nthr + tid] = make_float2(0.f, 0.f);
         rx[(size_t)j * nthr + tid] = 0.f;
     }
-    for (int j = tid; j < W; j += nthr) rab[j] = make_float2(0.f, 0.f);
+    for (int j = tid; j < W; j += nthr) {
+        rab[j] = make_float2(0.f, 0.f);
+        sg[j] = 0.f;                                   // the first SFT has no partner
+    }
     if (n_list == 0) {
         if (act) rho[(size_t)t * p.N_f + k] = 0.f;
         return;
@@ -492,8 +498,7 @@ __global__ void __launch_bounds__(256) demod_pair_kernel(DevParams p, int m_lo, 
         const float2 y = sft_y(Fc, xi2);
         float pr = 0.f, pq = 0.f;
         for (int j = 0; j < W; ++j) {
-            const float2 ab = rab[j];
-            const float g = fmaf(a, ab.x, b * ab.y);
+            const float g = sg[j];
             const float2 yl = ry[(size_t)j * nthr + tid];
             pr = fmaf(g, fmaf(y.x, yl.x, y.y * yl.y), pr);
             pq = fmaf(g * g, rx[(size_t)j * nthr + tid], pq);
@@ -501,14 +506,23 @@ __global__ void __launch_bounds__(256) demod_pair_kernel(DevParams p, int m_lo, 
         kahan_add(raw, rawc, pr);
         kahan_add(den, denc, xi2 * pq);
         __syncthreads();                               // every thread is done with the ring
-        const int slot = (l % (Rs + 1)) * Q + X;
+        const int bl = l % (Rs + 1), slot = bl * Q + X;
         ry[(size_t)slot * nthr + tid] = y;
         rx[(size_t)slot * nthr + tid] = xi2;
-        if (tid == 0) {
-            rab[slot] = make_float2(a, b);
-            // SFT i + 1 opens block ln: clear the slots of blocks l + 1 .. ln (at most all)
-            for (int bb = l + 1; bb <= ln && bb <= l + Rs + 1; ++bb)
-                for (int x2 = 0; x2 < Q; ++x2) rab[(bb % (Rs + 1)) * Q + x2] = make_float2(0.f, 0.f);
+        // the ring's weights after SFT i (its own slot set; SFT i + 1 opening block ln
+        // clears the slots of blocks l + 1 .. ln, all of them after R_s + 1 blocks) and
+        // Gamma of SFT i + 1 against each slot
+        const float an = Rn.t1.y, bn = Rn.t1.z;
+        const int jump = ln - l;
+        for (int j = tid; j < W; j += nthr) {
+            float2 ab = j == slot ? make_float2(a, b) : rab[j];
+            if (jump > 0) {
+                const int d = j / Q - bl;                 // block-slot distance after l, 0 .. R_s
+                const int dd = d <= 0 ? d + Rs + 1 : d;   // 1 .. R_s + 1
+                if (dd <= jump) ab = make_float2(0.f, 0.f);
+            }
+            rab[j] = ab;
+            sg[j] = fmaf(an, ab.x, bn * ab.y);
         }
         __syncthreads();
     };
@@ -665,7 +679,7 @@ extern "C" cc_status crosscorr_demod_search(cc_plan* plan, const cc_template* t_
     int nthr = sep ? 128 : 256;
     auto ring_bytes = [&](int nt) {
         return sep ? (sep_ring ? (size_t)(Rs + 1) * 7 * nt * sizeof(float) : 0)
-                   : (size_t)W * nt * 12 + (size_t)W * 8;
+                   : (size_t)W * nt * 12 + (size_t)W * 12;
     };
     while (nthr > 32 && ring_bytes(nthr) > DM_RING_BUDGET) nthr /= 2;
     if (ring_bytes(nthr) > DM_RING_BUDGET) return fail(CC_ERR_UNSUPPORTED, "T_max / T_sft too large for the pair ring");
