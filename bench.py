@@ -865,8 +865,7 @@ def run_multiband(args):
         c = algorithmic_costs(p.info, p.Q, tm.shape[0], cfg.D, learned)
         flops += c["total_flops"]
     achieved = flops * args.steps / elapsed / 1e12
-    clk_max = float((clk or {}).get("sm_max_mhz") or 2070.0)
-    peak = SM_COUNT * FP32_LANES * 2 * clk_max * 1e6 / 1e12
+    peak, peak_kind = fp32_peak(cc, clk)
     # e2e: every band's series and templates copied in from pinned memory, rho copied out
     x_host = [x.cpu().pin_memory() for (_, _, x, _) in bands]
     t_host = [t.cpu().pin_memory() for (_, _, _, t) in bands]
@@ -902,7 +901,7 @@ def run_multiband(args):
                    "l2": "inputs: 32 bands x 2 x 6.9 MB series (442 MB, larger than L2)"},
         "roofline": {"bound": "alu", "kernel": "graph (all kernels of all bands)", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                     "peak_kind": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 flop x {clk_max:g} MHz"},
+                     "peak_kind": peak_kind},
         "clocks": clk,
         # graph replays launch the kernels recorded at capture
         "gpu_launches": int(lib.crosscorr_kernel_launches() - n0) + mb.kernels_per_run * args.steps,
@@ -982,8 +981,7 @@ def run_demod(args):
         # normalisation terms and the running sums of its block, and 14 per SFT for the
         # window update (28 per block of two detectors): no per-pair term
         flops_tb = (30.0 + 53.0 + 14.0) * locked
-    clk_max = float((clk or {}).get("sm_max_mhz") or 2070.0)
-    peak = SM_COUNT * FP32_LANES * 2 * clk_max * 1e6 / 1e12
+    peak, peak_kind = fp32_peak(cc, clk)
     achieved = flops_tb * units / (pair_ms / 1e3) / 1e12 if pair_ms > 0 else None
     out = {
         "metric": METRIC, "value": units / elapsed, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
@@ -995,8 +993,7 @@ def run_demod(args):
         "roofline": {"bound": "alu", "kernel": "demod_sep_kernel" if separable else "demod_pair_kernel",
                      "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak if achieved else None, "traffic": None,
-                     "peak_kind": f"derived: {SM_COUNT} SMs x {FP32_LANES} FP32 lanes x 2 flop x {clk_max:g} MHz",
-                     "flops_per_template_bin": flops_tb, "kernel_ms_per_launch": pair_ms / max(1, pair_launches),
+                     "peak_kind": peak_kind, "flops_per_template_bin": flops_tb, "kernel_ms_per_launch": pair_ms / max(1, pair_launches),
                      "kernel_launches": pair_launches,
                      "kernel_share_of_step": pair_ms / (1e3 * elapsed) if elapsed > 0 else None},
         "clocks": clk, "gpu_launches": int(lib.crosscorr_kernel_launches() - n0),
