@@ -74,11 +74,11 @@ struct DevParams {
     const float2* twc;               // [C][N_s]: exp(-2 pi i ((b0 + c) s mod N_FFT) / N_FFT)
     const float2* twk;               // [C4][272]: coset twiddles of the 4096-point kernel's passes (plan.cu)
     int C4;                          // cosets of the 4096-point decomposition (N_FFT / 4096; 0 if N_FFT < 4096)
+    int wait_test;                   // crosscorr_plan_set_wait_test: skip each CTA's first bulk copy
     const int* coset4_off;           // [C4+1], and the bin lists of that decomposition
     const int* coset4_k;
     const int* coset4_m;
     unsigned* err;                   // device error word: bit 0 set by a kernel whose bounded wait ran out
-    int wait_test;                   // crosscorr_plan_set_wait_test: skip each CTA's first bulk copy
     const float* ltaps;              // [LEARNED_NODES][LEARNED_TAPS] learned taps (null until set)
     float ham[MAX_TAPS];             // Hamming window, 2D+1 taps
 };

@@ -62,12 +62,13 @@ __host__ __device__ inline int resample_window_len(const DevParams& p) {
 // detector times all fall in gaps is skipped: its norms are written as zero and its
 // a_r, b_r are written as zero (`write_inactive`, the staged stage: every weight there is
 // zero) or left unwritten (the two-pass search reads a segment only when its norms are
-// nonzero).  Without `kn` every sample is computed.
+// nonzero).  Without `kn` every sample is computed.  The parameter block comes last: with
+// it first, the offsets of the small parameters after it moved with its size, and at some
+// sizes the two-pass variant compiled to 52 registers instead of 32 and ran 15 % slower.
 template <int DT, bool PRE>
 __global__ void __launch_bounds__(RS_THREADS)
-resample_kernel(DevParams p, const cc_template* __restrict__ tm, int64_t t_base, void* ab,
-                float4* __restrict__ norm, const KnotRec* __restrict__ kn, int64_t nkn, int use_window,
-                int write_inactive) {
+resample_kernel(const cc_template* __restrict__ tm, int64_t t_base, void* ab, float4* __restrict__ norm,
+                const KnotRec* __restrict__ kn, int64_t nkn, int use_window, int write_inactive, DevParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float red[32];
     __shared__ int active;
@@ -462,7 +463,7 @@ cc_status launch_resample(cc_plan* plan, const cc_template* t_dev, int64_t n_t, 
     for (int64_t t0 = 0; t0 < n_t; t0 += MAX_GRID_YZ) {
         const int64_t nt = std::min<int64_t>(MAX_GRID_YZ, n_t - t0);
         dim3 grid((unsigned)p.M, (unsigned)p.Q, (unsigned)nt);
-        kern<<<grid, RS_THREADS, sm, st>>>(p, t_dev, t0, ab, (float4*)norm, kn, nkn, use_window, write_inactive);
+        kern<<<grid, RS_THREADS, sm, st>>>(t_dev, t0, ab, (float4*)norm, kn, nkn, use_window, write_inactive, p);
         count_launch();
     }
     cudaError_t e = cudaGetLastError();
