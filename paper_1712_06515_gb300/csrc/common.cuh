@@ -421,11 +421,25 @@ __device__ __forceinline__ float2 phase_rot(float psi) {
     return make_float2(c, s);
 }
 
-// Windowed-sinc taps on xp[0 .. 2D] (sample j* - D first) at offset delta != 0: the sum
-// of xp[n] w_n sinc(delta - (n - D)), with sin(pi (delta - m)) = (-1)^m sin(pi delta).
+// sin(pi r) / (pi r) for |r| <= 1/2 from its Taylor series sum_n (-1)^n (pi r)^2n / (2n+1)!,
+// cut after n = 6: the first omitted term is below (pi/2)^14 / 15! = 4.2e-10.
+__device__ __forceinline__ float sinc_pi(float r) {
+    const float u = 9.86960440108935862f * r * r;   // (pi r)^2
+    float s = -1.f / 6227020800.f;                  // -1/13!
+    s = fmaf(s, u, 1.f / 39916800.f);               // 1/11!
+    s = fmaf(s, u, -1.f / 362880.f);                // -1/9!
+    s = fmaf(s, u, 1.f / 5040.f);                   // 1/7!
+    s = fmaf(s, u, -1.f / 120.f);                   // -1/5!
+    s = fmaf(s, u, 1.f / 6.f);                      // 1/3!
+    return fmaf(-s, u, 1.f);                        // 1 - u (1/3! - u/5! + ...)
+}
+
+// Windowed-sinc taps on xp[0 .. 2D] (sample j* - D first) at offset delta != 0 (|delta| <=
+// 1/2): the sum of xp[n] w_n sinc(delta - (n - D)), with sin(pi (delta - m)) =
+// (-1)^m sin(pi delta) and sin(pi delta) / pi = delta sinc_pi(delta).
 __device__ __forceinline__ float2 sinc_taps(const DevParams& p, const float2* __restrict__ xp, float delta) {
     const int D = p.D;
-    const float s = sinpif(delta) * 0.318309886183790672f;   // sin(pi delta)/pi
+    const float s = delta * sinc_pi(delta);                 // sin(pi delta)/pi
     float2 acc = make_float2(0.f, 0.f);
     for (int n = 0; n <= 2 * D; ++n) {
         const float dj = delta - (float)(n - D);              // (t - t_j)/dt
@@ -442,8 +456,9 @@ __device__ __forceinline__ float2 sinc_taps(const DevParams& p, const float2* __
 // signed window (-1)^k w_{D-+k}, so one reciprocal serves two taps.
 template <int D>
 __device__ __forceinline__ float2 sinc_taps_t(const DevParams& p, const float2* __restrict__ xp, float delta) {
-    const float s = sinpif(delta) * 0.318309886183790672f;
-    const float c0 = p.ham[D] * __fdividef(s, delta);
+    const float sc = sinc_pi(delta);
+    const float s = delta * sc;                              // sin(pi delta)/pi
+    const float c0 = p.ham[D] * sc;
     float2 acc = make_float2(c0 * xp[D].x, c0 * xp[D].y);
 #pragma unroll
     for (int k = 1; k <= D; ++k) {
@@ -468,7 +483,7 @@ __device__ __forceinline__ float2 interp_sinc(const DevParams& p, const float2* 
     const int D = p.D;
     const int j0 = jstar - D;
     if (j0 >= 0 && j0 + 2 * D < N) return sinc_taps(p, x + j0, delta);
-    const float s = sinpif(delta) * 0.318309886183790672f;
+    const float s = delta * sinc_pi(delta);                 // sin(pi delta)/pi
     float2 acc = make_float2(0.f, 0.f);
     for (int n = 0; n <= 2 * D; ++n) {
         const int j = j0 + n;

@@ -221,19 +221,6 @@ struct SftIn {
     float2 z0, z1;
 };
 
-// sin(pi r) / (pi r) for |r| <= 1/2 from its Taylor series sum_n (-1)^n (pi r)^2n / (2n+1)!,
-// cut after n = 6: the first omitted term is below (pi/2)^14 / 15! = 4.2e-10.
-__device__ __forceinline__ float sinc_pi_half(float r) {
-    const float u = 9.86960440108935862f * r * r;   // (pi r)^2
-    float s = -1.f / 6227020800.f;                  // -1/13!
-    s = fmaf(s, u, 1.f / 39916800.f);               // 1/11!
-    s = fmaf(s, u, -1.f / 362880.f);                // -1/9!
-    s = fmaf(s, u, 1.f / 5040.f);                   // 1/7!
-    s = fmaf(s, u, -1.f / 120.f);                   // -1/5!
-    s = fmaf(s, u, 1.f / 6.f);                      // 1/3!
-    return fmaf(-s, u, 1.f);                        // 1 - u (1/3! - u/5! + ...)
-}
-
 // The demodulated bin y (the two-bin sinc interpolation of the pair kernel, rotated by the
 // heterodyne phase) and the interpolation weight Xi^2.  The two sinc weights
 // s0 = sin(pi kappa) / (pi kappa), s1 = -sin(pi kappa) / (pi (kappa + 1)) take the series
@@ -245,7 +232,7 @@ __device__ __forceinline__ float2 sft_y(const SftIn& q, float& xi2) {
     const bool near0 = q.k0 >= -0.5f;                // kappa in [-1/2, 0]: series at kappa
     const float r = near0 ? q.k0 : q.k0 + 1.f;
     const float far = near0 ? q.k0 + 1.f : q.k0;
-    const float sv = sinc_pi_half(r);
+    const float sv = sinc_pi(r);
     const float other = -__fdividef(r * sv, far);
     const float s0 = near0 ? sv : other, s1 = near0 ? other : sv;
     xi2 = s0 * s0 + s1 * s1;
