@@ -111,6 +111,8 @@ def sfts_to_series(band, block_sft, T_sft: float, f_h: float, out=None, stream=N
     if band.dim() != 2:
         raise ValueError("band must be [n_sft, N']")
     n_blocks, n_prime = block_sft.numel(), band.shape[1]
+    if band.shape[0] == 0:      # every block a gap: the library still takes a valid band pointer
+        band = torch.zeros((1, n_prime), dtype=torch.complex64, device=band.device)
     if out is None:
         x = torch.empty(n_blocks * n_prime, dtype=torch.complex64, device=band.device)
     else:

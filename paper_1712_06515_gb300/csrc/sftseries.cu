@@ -16,6 +16,7 @@ namespace cc {
 namespace {
 
 constexpr int SS_THREADS = 256;
+constexpr int SS_WARP_SMEM = 72 * 1024;   // shared-memory budget of a persistent-warp CTA
 
 // one CTA per T_sft block: the block's SFT (or zeros for a gap) -> N' output samples
 __global__ void __launch_bounds__(SS_THREADS)
@@ -399,7 +400,7 @@ extern "C" cc_status crosscorr_sfts_to_series(const void* band_dev, const int64_
         // persistent warps: three N'-point buffers per warp plus the CTA's twiddle table,
         // as many warps per CTA (at most 8) as fit in 72 KB; one wave of CTAs
         const size_t per = 3 * sizeof(float2) * n_prime, tw_b = sizeof(float2) * ((n_prime + 1) & ~1);
-        const int groups = (int)std::max<int64_t>(1, std::min<int64_t>(SS_THREADS / 32, (72 * 1024 - tw_b) / per));
+        const int groups = (int)std::max<int64_t>(1, std::min<int64_t>(SS_THREADS / 32, (SS_WARP_SMEM - tw_b) / per));
         const size_t smem = tw_b + per * groups;
         // the launch shape per (device, N'): the smem attribute and the occupancy query run
         // once, so that repeated calls (and a stream capture of them) only launch
@@ -414,9 +415,10 @@ extern "C" cc_status crosscorr_sfts_to_series(const void* band_dev, const int64_
                 occ = it->second.first;
                 sms = it->second.second;
             } else {
-                if (smem > 48 * 1024 &&
-                    (e = cudaFuncSetAttribute(sft_fft_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)smem)) != cudaSuccess)
+                // the attribute is the kernel's, shared by every N': set to the largest shape
+                // (72 KB, or one group of three 1536-point buffers and the table: 49 KB)
+                if ((e = cudaFuncSetAttribute(sft_fft_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              SS_WARP_SMEM)) != cudaSuccess)
                     return cuda_fail(e, "sfts_to_series smem attribute");
                 if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sft_fft_warp_kernel, 32 * groups,
                                                                         smem)) != cudaSuccess ||

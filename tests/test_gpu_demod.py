@@ -76,6 +76,38 @@ def test_demod_o1_band_30_days_injected_template(separable):
     assert int(got[0].argmax()) == int(ref[0].argmax())
 
 
+@pytest.fixture(scope="module")
+def o1_band_120d():
+    ds = synth.o1_band(n_ap=1, n_tasc=1, days=120)
+    return ds, demod.sfts(ds)
+
+
+@pytest.mark.parametrize("separable", [False, True], ids=["pairs", "separable"])
+def test_demod_o1_band_full_size_sampled_bins(o1_band_120d, separable):
+    """The workload `bench.py --method demod` times: 120 days, 33134 locked SFTs, 12356 bins.
+    The injected template and a neighbour on the GPU (every bin) against the oracle at 24
+    evenly spaced bins and the five bins around the GPU's peak.  The oracle's largest value
+    among those five sits at the GPU's peak."""
+    from oracle import make_plan
+    ds, sft_list = o1_band_120d
+    inj = ds.injection
+    tm = np.array([[inj.a_p, inj.T_asc, inj.P], [inj.a_p + 0.02, inj.T_asc + 60.0, inj.P]])
+    got = gpu_demod(ds, tm, separable=separable)
+    freq = make_plan(ds.cfg).freq
+    n_f = len(freq)
+    assert got.shape == (2, n_f)
+    for t in range(2):
+        k = int(np.argmax(got[t]))
+        near = list(range(max(0, k - 2), min(n_f, k + 3)))
+        idx = np.array(sorted(set(np.linspace(0, n_f - 1, 24).astype(int).tolist()) | set(near)))
+        ref = demod.demod_rho(ds, tm[t], freqs=freq[idx], sft_list=sft_list)
+        err = float(np.abs(got[t][idx] - ref).max())
+        lim = 1e-4 * max(1.0, float(np.abs(ref).max()))
+        assert err <= lim, f"template {t}: max |drho| = {err:.3e} > {lim:.3e}"
+        ref_near = ref[np.searchsorted(idx, near)]
+        assert near[int(np.argmax(ref_near))] == k
+
+
 def test_demod_forms_agree_to_rounding():
     """Pair loop and separable form on the same plan: the same rho up to FP32 rounding
     (a bound ten times tighter than the oracle bar), including gaps and a ragged end."""
