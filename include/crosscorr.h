@@ -303,9 +303,12 @@ cc_status crosscorr_plan_set_tuning(cc_plan* plan, const cc_tuning* tuning);
  *
  * crosscorr_demod_prepare computes the SFT bins a signal of the band can reach for
  * Doppler factors |dtau/dt - 1| <= doppler_max (0 selects 5e-4) from x_dev (Q device
- * pointers to complex64[N_t], as for crosscorr_search) into plan-owned device memory,
- * asynchronously on `stream`; crosscorr_demod_search then writes rho to
- * rho_dev[n_t][N_f] (device) for device templates t_dev[n_t], asynchronously. */
+ * pointers to complex64[N_t], as for crosscorr_search) into plan-owned device memory, and
+ * the time-ordered list of locked SFTs the search walks; it synchronises `stream` once
+ * (the lock flags come back to the host to build that list).  crosscorr_demod_search
+ * then writes rho to rho_dev[n_t][N_f] (device) for device templates t_dev[n_t],
+ * asynchronously on `stream`, with per-template SFT records (32 bytes per locked SFT) in
+ * the plan workspace, grown on demand. */
 cc_status crosscorr_demod_prepare(cc_plan* plan, const void* const* x_dev, int32_t n_bin, double doppler_max,
                                   void* stream);
 cc_status crosscorr_demod_search(cc_plan* plan, const cc_template* t_dev, int64_t n_t, float* rho_dev,
