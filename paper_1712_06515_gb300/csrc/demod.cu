@@ -7,13 +7,17 @@
 //     the bins a signal in the band can reach (direct DFT with an exact integer twiddle
 //     index), normalised to unit variance, and per SFT the filter weights
 //     a^ = sqrt(2 T_sft / S) a(t_K), b^ likewise (S = 2 sigma^2 dt);
-//   crosscorr_demod_search: per template an FP64 pass gives, per SFT, the signal's bin
-//     position and phase as linear functions of the output bin; one thread per
-//     (template, output bin) then walks the SFTs in time order, forms
+//   crosscorr_demod_search: per template an FP64 pass gives, per locked SFT (a list in
+//     time order built by the prepare call), the signal's bin position and phase as
+//     linear functions of the output bin; one thread per (template, output bin) then
+//     walks the SFTs in time order, forms
 //     y_K = sum_m (-1)^m sinc(kappa_Km) z_Km exp(-i Phi_K) (= Xi_K z_K exp(-i Phi_K)) and
-//     sums Gamma_KL 2 Re(conj(y_K) y_L) over every earlier SFT L within T_max (the pair
-//     loop of the method, each unordered pair once), with the normalisation
-//     sum (Xi_K Xi_L Gamma_KL)^2 alongside; rho = raw / sqrt(2 den).
+//     sums Gamma_KL 2 Re(conj(y_K) y_L) over every earlier SFT L within T_max, with the
+//     normalisation sum (Xi_K Xi_L Gamma_KL)^2 alongside; rho = raw / sqrt(2 den).  Two
+//     forms of that sum: the method's pair loop (demod_pair_kernel, one term per pair,
+//     each unordered pair once) and the separable form (demod_sep_kernel: Gamma_KL is a
+//     sum of products of a K factor and an L factor, so running sums over the partners
+//     give the same value in O(1) per SFT).
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -30,11 +34,11 @@ constexpr int DM_MAX_SFT_SAMPLES = 16384;   // T_sft / dt staged in shared memor
 constexpr size_t DM_RING_BUDGET = 160 * 1024;
 constexpr size_t DM_SEP_RING = 40 * 1024;   // separable form: block-sum ring per CTA (R_s <= 10)
 
-struct DemodTiming {   // per (template, detector, SFT block): 32 bytes
+struct DemodTiming {   // per (template, locked SFT): 32 bytes
     float A0, A1;       // signal bin position x = A0 + df A1 (df = f - f_h of the output bin)
     float C0, C1;       // heterodyned phase (cycles) = C0 + kbar C1 with kbar = 128 kh + kl:
-    float C128, pad0;   //   C0 + kh C128 + kl C1 (mod 1)
-    float pad1, pad2;
+    float C128, pad0;   //   C0 + kh C128 + kl C1 (mod 1); pad0, pad1: the SFT's a^, b^
+    float pad1, pad2;   //   divided by sqrt(10); pad2: its list key 4 l + X (int bits)
 };
 
 // DFT bins m_lo .. m_lo + nbins - 1 of one T_sft block of detector X, normalised to unit
