@@ -140,6 +140,7 @@ struct cc_plan {
     int search_path = CC_PATH_AUTO;           // crosscorr_plan_set_path
     cc_tuning tuning = {0, 0, 0};             // crosscorr_plan_set_tuning
     int kbar_span4 = 0;                       // largest transform position of a bin, 4096-point cosets
+    int* segfft_ctr = nullptr;                // [C4] unit counters of the staged segment FFT (plan-owned)
     bool ws_external = false;                 // ws is caller memory (crosscorr_plan_set_workspace)
     // diagnostic event pairs around fused-kernel launches (crosscorr_plan_set_kernel_timing)
     bool kernel_timing = false;

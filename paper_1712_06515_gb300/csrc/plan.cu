@@ -469,6 +469,15 @@ cc_status crosscorr_plan(const cc_config* cfg, const cc_detector* dets, cc_plan*
         dp.coset4_m = dp.coset_m;
     }
     p->kbar_span4 = C4 > 0 ? (int)((p->kbar.back() - p->k0) / C4) : 0;
+    if (C4 > 0) {
+        void* ctr = nullptr;
+        if (cudaMalloc(&ctr, sizeof(int) * C4) != cudaSuccess) {
+            crosscorr_plan_destroy(p);
+            return fail(CC_ERR_OOM, "unit counters");
+        }
+        p->dev_allocs.push_back(ctr);
+        p->segfft_ctr = (int*)ctr;
+    }
     dp.log2L = log2L;
     dp.nsft = (int)nsft;
     cc::magic_for((uint32_t)nsft, &dp.nsft_m, &dp.nsft_s);

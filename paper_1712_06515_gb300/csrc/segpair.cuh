@@ -29,5 +29,9 @@ cc_status launch_segpair_tma(cc_plan* plan, const SegPairLayout& lay, int64_t n_
 bool segpair_tma_folded(const cc_plan* plan);
 size_t segpair_tma_fold_bytes(const cc_plan* plan);
 cc_status launch_fold(cc_plan* plan, int64_t n_t, const void* ab, const float4* norm, void* z, cudaStream_t st);
+// The staged segment-FFT stage by the same kernel (spectra written instead of pair sums):
+// whether the plan fits it, and one launch writing F [n_t][Q][M][2][N_f] (counters: [C4]).
+bool segfft_tma_supported(const cc_plan* plan);
+cc_status launch_segfft_tma(cc_plan* plan, int64_t n_t, const void* ab, float2* F, int* counters, cudaStream_t st);
 
 }  // namespace cc

@@ -112,10 +112,13 @@ struct TmaWork {
 // segments (N_s > L) the fold kernel's Z [n_t][Q][2][M][C][L] in the same type; norm:
 // [n_t][Q][M] (hat-A, hat-B, hat-C, 0), raw: [n_t][2 * n_chunks][N_f] partial pair
 // sums, counters: [C] unit counters (zero at launch).
-template <bool BF16>
+// SPECTRA (the staged segment-FFT stage): no pair sums; every (detector, segment)
+// transform of the unit's chunk is written, with its segment-start phase W_N^(k seg0), to
+// Fs[n_t][Q][M][2][N_f] at the coset's bins (norm unused: every segment is transformed).
+template <bool BF16, bool SPECTRA>
 __global__ void __launch_bounds__(TT_THREADS, 2)
 segpair_tma_kernel(DevParams p, TmaWork q, const void* __restrict__ ab, const float4* __restrict__ norm,
-                   float* __restrict__ raw, int* __restrict__ counters) {
+                   float* __restrict__ raw, int* __restrict__ counters, float2* __restrict__ Fs) {
     extern __shared__ __align__(128) unsigned char sm[];
     constexpr int L = TT_L;
     constexpr int NSL = 256;    // butterflies of each pass = threads
@@ -164,7 +167,7 @@ segpair_tma_kernel(DevParams p, TmaWork q, const void* __restrict__ ab, const fl
         const int rem = u % (2 * q.n_chunks), w = rem / q.n_chunks, chunk = rem % q.n_chunks;
         const int64_t Ka = (int64_t)chunk * q.chunk_len;
         const int64_t Kb = imin64(M, Ka + q.chunk_len);
-        const int64_t Kl = imax64(0, Ka - R);
+        const int64_t Kl = SPECTRA ? Ka : imax64(0, Ka - R);
         const uint64_t bc = ((uint64_t)p.b0 + (uint64_t)c) & mask;
         const float2* __restrict__ twk = p.twk + (size_t)c * 272;
         // pair phase of this thread's bins: theta = W_N^(-(bc + C tid) N_s)
@@ -177,13 +180,16 @@ segpair_tma_kernel(DevParams p, TmaWork q, const void* __restrict__ ab, const fl
         // W_N^(ct r3), formed from these four powers
         const float2 b1 = twiddle_N(ct & mask, N), b2 = twiddle_N((2 * ct) & mask, N);
         const float2 b4 = twiddle_N((4 * ct) & mask, N), b8 = twiddle_N((8 * ct) & mask, N);
-        const float4* __restrict__ nt = norm + (size_t)t * Q * M;
+        const float4* __restrict__ nt = SPECTRA ? nullptr : norm + (size_t)t * Q * M;
         // element offset of (template t, detector X, weight w) row
         const size_t abt = (size_t)t * Q * 2 * N_tau + (size_t)w * N_tau;
         auto active = [&](int64_t K, int X) {
+            if constexpr (SPECTRA) return true;
             const float4 n = nt[(size_t)X * M + K];
             return n.x + n.y > 0.f;
         };
+        // SPECTRA: the coset's bins of output row (X, K)
+        const int o4 = __ldg(p.coset4_off + c), nb4 = __ldg(p.coset4_off + c + 1) - o4;
         // the transform after (K, X) in unit order (detector 0, then detector Q-1, of each
         // segment; inactive ones skipped); X = -1 starts at segment K
         auto next_after = [&](int64_t K, int X, int64_t& nK, int& nX) -> bool {
@@ -234,10 +240,18 @@ segpair_tma_kernel(DevParams p, TmaWork q, const void* __restrict__ ab, const fl
         for (int64_t K = Kl; K < Kb; ++K) {
             const bool a0 = active(K, 0), al = active(K, Q - 1);
             float2 v[16];
+            // SPECTRA: the segment-start phase W_N^(k seg0) of bin k = bc + C m, m = tid + 256 r:
+            // ph0 = W_N^((bc + C tid) seg0), stepped by W_N^(256 C seg0)
+            float2 ph0 = make_float2(1.f, 0.f), phs = make_float2(1.f, 0.f);
+            if constexpr (SPECTRA) {
+                const uint64_t s0 = (uint64_t)(K * N_s) & mask;
+                ph0 = twiddle_N(((ct & mask) * s0) & mask, N);
+                phs = twiddle_N(((256 * (uint64_t)C) * s0) & mask, N);
+            }
 #pragma unroll 1
             for (int pass = 0; pass < 2; ++pass) {
                 const int X = pass == 0 ? 0 : Q - 1;
-                if (pass == 0 ? !(Q > 1 && a0) : !al) continue;
+                if (pass == 0 ? !(Q > 1 && a0) : !al) continue;   // (SPECTRA: every transform is active)
                 // (K, X) is the staged transform
                 const bool ok = mbar_wait(bar, phase);
                 phase ^= 1;
@@ -312,12 +326,25 @@ segpair_tma_kernel(DevParams p, TmaWork q, const void* __restrict__ ab, const fl
                     v[15] = cmul(v[15], cmul(b12, b3));
                     dft16_lo8(v);
                 }
-                if (pass == 0) {
+                if constexpr (SPECTRA) {
+                    // the transform with its segment-start phase to H, then the coset's bins to F
+                    float2 ph = ph0;
+#pragma unroll
+                    for (int r = 0; r < SLP; ++r) {
+                        if (tid + NSL * r <= q.mmax) H[r * NSL + tid] = cmul(v[r], ph);
+                        ph = cmul(ph, phs);
+                    }
+                    __syncthreads();
+                    float2* Fo = Fs + ((((size_t)t * Q + X) * M + K) * 2 + w) * p.N_f;
+                    for (int i = tid; i < nb4; i += TT_THREADS) Fo[__ldg(p.coset4_k + o4 + i)] = H[__ldg(p.coset4_m + o4 + i)];
+                    __syncthreads();                   // H is rewritten by the next transform
+                } else if (pass == 0) {
 #pragma unroll
                     for (int r = 0; r < SLP; ++r)
                         if (tid + NSL * r <= q.mmax) H[r * NSL + tid] = v[r];   // read back by this thread only
                 }
             }
+            if constexpr (SPECTRA) continue;
             // pair terms of segment K (F = 0 for a detector with no weight in it); prevP
             // holds the previous segment's detector sum times theta of its bin
             const bool acc_on = K >= Ka;
@@ -342,6 +369,7 @@ segpair_tma_kernel(DevParams p, TmaWork q, const void* __restrict__ ab, const fl
                 if (R > 0 && !psi_one) th = cmul(th, psi);
             }
         }
+        if constexpr (SPECTRA) continue;
         // partial sums of this (template, weight, chunk) row for the coset's bins, staged
         // through Y (the last transform's reads of Y ended before its second barrier)
         __syncthreads();
@@ -490,13 +518,14 @@ bool tma_layout(const cc_plan* plan, TmaWork* q, size_t* bytes) {
     return o <= 113 * 1024;   // two CTAs per SM
 }
 
-template <bool BF16>
+template <bool BF16, bool SPECTRA>
 int occupancy(size_t smem) {
     int n = 0;
-    if (cudaFuncSetAttribute(segpair_tma_kernel<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
+    if (cudaFuncSetAttribute(segpair_tma_kernel<BF16, SPECTRA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
         return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, segpair_tma_kernel<BF16>, TT_THREADS, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, segpair_tma_kernel<BF16, SPECTRA>, TT_THREADS, smem) !=
+        cudaSuccess)
         return 0;
     return n;
 }
@@ -576,7 +605,7 @@ cc_status launch_segpair_tma(cc_plan* plan, const SegPairLayout& lay, int64_t n_
     q.units = n_t * 2 * lay.n_chunks;
     if (q.units > 0x7fffffff) return fail(CC_ERR_UNSUPPORTED, "too many work units in one launch");
     const bool bf16 = p.store == CC_STORE_BF16;
-    const int occ = bf16 ? occupancy<true>(bytes) : occupancy<false>(bytes);
+    const int occ = bf16 ? occupancy<true, false>(bytes) : occupancy<false, false>(bytes);
     if (occ < 1) return fail(CC_ERR_UNSUPPORTED, "segpair_tma kernel does not fit an SM");
     int dev = 0, sms = 152;
     cudaError_t e = cudaGetDevice(&dev);
@@ -586,13 +615,64 @@ cc_status launch_segpair_tma(cc_plan* plan, const SegPairLayout& lay, int64_t n_
     if ((e = cudaMemsetAsync(counters, 0, sizeof(int) * p.C4, st)) != cudaSuccess)
         return cuda_fail(e, "unit counters");
     if (bf16)
-        segpair_tma_kernel<true><<<(unsigned)grid, TT_THREADS, bytes, st>>>(p, q, ab, norm, raw, counters);
+        segpair_tma_kernel<true, false><<<(unsigned)grid, TT_THREADS, bytes, st>>>(p, q, ab, norm, raw, counters,
+                                                                                  nullptr);
     else
-        segpair_tma_kernel<false><<<(unsigned)grid, TT_THREADS, bytes, st>>>(p, q, ab, norm, raw, counters);
+        segpair_tma_kernel<false, false><<<(unsigned)grid, TT_THREADS, bytes, st>>>(p, q, ab, norm, raw, counters,
+                                                                                   nullptr);
     count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "segpair_tma launch");
     return CC_OK;
+}
+
+// The staged segment-FFT stage by the persistent kernel: whole segments (N_s <= 4096, even;
+// a multiple of 4 with BF16 storage) on 4096-point cosets (the plan's own, or zero-padded
+// when the plan is tuned to transform_len 4096), Q <= 2, output bins in the lower half of
+// each coset transform.
+bool segfft_tma_supported(const cc_plan* plan) {
+    const DevParams& p = plan->dp;
+    const bool padded = p.L < TT_L && plan->tuning.transform_len == TT_L && p.C4 > 0;
+    if ((p.L != TT_L && !padded) || p.Q > 2 || p.N_s > TT_L || plan->N_f < 1) return false;
+    if (p.N_s % (p.store == CC_STORE_BF16 ? 4 : 2)) return false;
+    TmaWork q;
+    size_t bytes;
+    if (!tma_layout(plan, &q, &bytes)) return false;
+    return 2 * q.mmax < TT_L;
+}
+
+cc_status launch_segfft_tma(cc_plan* plan, int64_t n_t, const void* ab, float2* F, int* counters, cudaStream_t st) {
+    const DevParams& p = plan->dp;
+    TmaWork q;
+    size_t bytes;
+    if (!tma_layout(plan, &q, &bytes)) return fail(CC_ERR_UNSUPPORTED, "segpair_tma layout");
+    const bool bf16 = p.store == CC_STORE_BF16;
+    const int occ = bf16 ? occupancy<true, true>(bytes) : occupancy<false, true>(bytes);
+    if (occ < 1) return fail(CC_ERR_UNSUPPORTED, "segpair_tma kernel does not fit an SM");
+    int dev = 0, sms = 152;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "device attributes");
+    // chunks of segments: about 24 units per persistent CTA
+    const int64_t ctas_per_coset = std::max<int64_t>(1, (int64_t)occ * sms / p.C4);
+    const int64_t n_chunks = std::max<int64_t>(1, std::min<int64_t>({(24 * ctas_per_coset + 2 * n_t - 1) / (2 * n_t),
+                                                                     p.M, 32767}));
+    q.n_chunks = (int)n_chunks;
+    q.chunk_len = (p.M + n_chunks - 1) / n_chunks;
+    q.units = n_t * 2 * n_chunks;
+    if (q.units > 0x7fffffff) return fail(CC_ERR_UNSUPPORTED, "too many work units in one launch");
+    const int64_t grid = std::min<int64_t>((int64_t)occ * sms, q.units * p.C4);
+    if ((e = cudaMemsetAsync(counters, 0, sizeof(int) * p.C4, st)) != cudaSuccess)
+        return cuda_fail(e, "unit counters");
+    if (bf16)
+        segpair_tma_kernel<true, true><<<(unsigned)grid, TT_THREADS, bytes, st>>>(p, q, ab, nullptr, nullptr,
+                                                                                 counters, F);
+    else
+        segpair_tma_kernel<false, true><<<(unsigned)grid, TT_THREADS, bytes, st>>>(p, q, ab, nullptr, nullptr,
+                                                                                  counters, F);
+    count_launch();
+    e = cudaGetLastError();
+    return e == cudaSuccess ? CC_OK : cuda_fail(e, "segment FFT (persistent) launch");
 }
 
 }  // namespace cc

@@ -6,6 +6,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "segpair.cuh"
 #include "fft_reg.cuh"
 
 namespace cc {
@@ -501,6 +502,9 @@ static const void* segfft_t_ptr() { return (const void*)segfft_kernel_t<LT>; }
 
 cc_status launch_segfft(cc_plan* plan, const void* ab, int64_t n_t, void* F, cudaStream_t st) {
     const DevParams& p = plan->dp;
+    // 4096-point cosets of whole segments: the persistent, TMA-staged kernel in spectra mode
+    if (plan->segfft_ctr && segfft_tma_supported(plan))
+        return launch_segfft_tma(plan, n_t, ab, (float2*)F, plan->segfft_ctr, st);
     const void* kt = p.L == 64 ? segfft_t_ptr<64>() : p.L == 128 ? segfft_t_ptr<128>() : p.L == 256 ? segfft_t_ptr<256>()
                    : p.L == 512 ? segfft_t_ptr<512>() : p.L == 1024 ? segfft_t_ptr<1024>()
                    : p.L == 2048 ? segfft_t_ptr<2048>() : p.L == 4096 ? segfft_t_ptr<4096>() : nullptr;

@@ -199,3 +199,34 @@ def test_bounded_wait_runs_out_reports_timeout_and_context_survives():
         again = plan.search(x, tm).cpu().numpy()
         plan.check()
     assert np.array_equal(again, good)
+
+
+@pytest.mark.parametrize("name,padded", [("R1", False), ("R1_Q1", False), ("R1_Ns3000", False),
+                                         ("L2048", True)])
+def test_staged_segment_fft_on_4096_cosets(name, padded):
+    """The staged segment-FFT stage on 4096-point cosets (the persistent kernel writing
+    spectra instead of pair sums, every segment transformed): random series in, every
+    spectrum bin against the oracle's zero-padded FP64 FFT route."""
+    kw = dict(BASE)
+    kw.update(CASES.get(name, PADDED.get(name, {})))
+    ds = synth.tiny(seed=53, n_templates=2, **kw)
+    p = oracle.make_plan(ds.cfg)
+    assert ds.cfg.n_samples == p.M * p.N_s
+    Q = ds.cfg.n_det
+    rng = np.random.default_rng(7)
+    a0 = rng.standard_normal((2, Q, 2, p.M * p.N_s)) + 1j * rng.standard_normal((2, Q, 2, p.M * p.N_s))
+    r = np.arange(p.M * p.N_s)
+    rot = np.exp(-2j * np.pi * ((p.f_r * r * p.dt) % 1.0))
+    Fref = np.zeros((2, Q, p.M, 2, p.N_f), np.complex128)
+    for t in range(2):
+        for q in range(Q):
+            for w in range(2):
+                Fref[t, q, :, w] = oracle.spectra_fft(a0[t, q, w], p)
+    with cc.CrossCorrPlan(ds.cfg, ds.dets) as plan:
+        assert (plan.info["L"] == 4096) != padded
+        if padded:
+            plan.set_tuning(transform_len=4096)
+        ab = torch.from_numpy((a0 * rot).astype(np.complex64)).to(DEV)
+        F = plan.segment_fft(ab, 2).cpu().numpy()
+    err = np.abs(F - Fref).max()
+    assert err <= 1e-5 * np.abs(Fref).max(), err
