@@ -230,3 +230,21 @@ def test_staged_segment_fft_on_4096_cosets(name, padded):
         F = plan.segment_fft(ab, 2).cpu().numpy()
     err = np.abs(F - Fref).max()
     assert err <= 1e-5 * np.abs(Fref).max(), err
+
+
+def test_staged_search_bf16_on_4096_cosets():
+    """The staged path with BF16 storage on 4096-point cosets (the spectra mode reading
+    bf16 pairs): against the oracle at the BF16 bar and against the two-pass path with the
+    same storage to a tighter bound."""
+    ds = case("R1")
+    ref = oracle.rho(ds)
+    with cc.CrossCorrPlan(ds.cfg, ds.dets, store=cc.STORE_BF16) as plan:
+        x = torch.from_numpy(ds.x64).to(DEV)
+        tm = torch.from_numpy(ds.templates).to(DEV)
+        plan.set_path(cc.PATH_STAGED)
+        staged = plan.search(x, tm).cpu().numpy().astype(np.float64)
+        plan.set_path(cc.PATH_TWO_PASS)
+        two_pass = plan.search(x, tm).cpu().numpy().astype(np.float64)
+        plan.check()
+    assert_close(staged, ref, 1e-2)
+    assert_close(staged, two_pass, 3e-3)
