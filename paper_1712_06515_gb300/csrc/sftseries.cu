@@ -357,24 +357,100 @@ sft_fft_warp_kernel(const float2* __restrict__ band, const int64_t* __restrict__
     cp_async_wait_all();
 }
 
+// The per-pass constants of a radix order r[0 .. n-1] of N'.
+void set_passes(int64_t N, const int* r, int n, Radices* rad) {
+    rad->n = n;
+    int ns = 1;
+    for (int i = 0; i < n; ++i) {
+        const int R = r[i];
+        rad->ns[i] = ns;
+        magic_for((uint32_t)ns, &rad->nsm[i], &rad->nss[i]);
+        rad->nb[i] = (int)(N / R);
+        rad->tstep[i] = (int)(N / ((int64_t)ns * R));
+        rad->r[i] = R;
+        ns *= R;
+    }
+}
+
 // N' as radices 4, 2, 3, 5 (fours first); false if another prime divides it.
 bool factor_radices(int64_t n, Radices* rad) {
-    rad->n = 0;
+    int r[SS_MAX_PASSES], k = 0;
     int64_t m = n;
-    int ns = 1;
     for (int R : {4, 2, 3, 5}) {
         while (m % R == 0) {
-            if (rad->n == SS_MAX_PASSES) return false;
-            rad->ns[rad->n] = ns;
-            magic_for((uint32_t)ns, &rad->nsm[rad->n], &rad->nss[rad->n]);
-            rad->nb[rad->n] = (int)(n / R);
-            rad->tstep[rad->n] = (int)(n / ((int64_t)ns * R));
-            rad->r[rad->n++] = R;
-            ns *= R;
+            if (k == SS_MAX_PASSES) return false;
+            r[k++] = R;
             m /= R;
         }
     }
-    return m == 1;
+    if (m != 1) return false;
+    set_passes(n, r, k, rad);
+    return true;
+}
+
+// Shared-memory wavefronts of one warp access to 8-byte elements at `idx` (32 banks of
+// 4 bytes, 128-byte rows): the largest number of distinct rows any bank is asked for.
+int warp_wavefronts(const int* idx, int nl) {
+    int rows[32][64], cnt[32] = {0};
+    int worst = 0;
+    for (int l = 0; l < nl; ++l)
+        for (int h = 0; h < 2; ++h) {
+            const int w = 8 * idx[l] + 4 * h, b = (w / 4) % 32, row = w / 128;
+            bool seen = false;
+            for (int i = 0; i < cnt[b]; ++i) seen |= rows[b][i] == row;
+            if (!seen) {
+                rows[b][cnt[b]++] = row;
+                worst = std::max(worst, cnt[b]);
+            }
+        }
+    return worst;
+}
+
+// Shared-memory wavefronts of the warp kernel's passes in a radix order: the R strided
+// reads src[j + r nb], the R writes dst[(j - k) R + k + r NS] and the twiddle reads.
+int64_t order_wavefronts(int64_t N, const int* r, int n) {
+    int64_t total = 0;
+    int ns = 1, idx[32];
+    for (int p = 0; p < n; ++p) {
+        const int R = r[p], nb = (int)(N / R), tstep = (int)(N / ((int64_t)ns * R));
+        for (int j0 = 0; j0 < nb; j0 += 32) {
+            const int nl = std::min(32, nb - j0);
+            for (int q = 0; q < R; ++q) {
+                for (int l = 0; l < nl; ++l) idx[l] = j0 + l + q * nb;
+                total += warp_wavefronts(idx, nl);
+                for (int l = 0; l < nl; ++l) {
+                    const int j = j0 + l, k = j % ns;
+                    idx[l] = (j - k) * R + k + q * ns;
+                }
+                total += warp_wavefronts(idx, nl);
+                if (ns > 1 && q > 0) {
+                    for (int l = 0; l < nl; ++l) idx[l] = ((j0 + l) % ns) * q * tstep;
+                    total += warp_wavefronts(idx, nl);
+                }
+            }
+        }
+        ns *= R;
+    }
+    return total;
+}
+
+// The warp kernel's radix order: of every distinct order of the factors, the one with the
+// fewest shared-memory wavefronts (early passes write with stride R, and a radix whose
+// stride shares no factor with the banks writes without conflicts).
+void order_for_banks(int64_t N, Radices* rad) {
+    int r[SS_MAX_PASSES], best[SS_MAX_PASSES];
+    const int n = rad->n;
+    for (int i = 0; i < n; ++i) r[i] = rad->r[i];
+    std::sort(r, r + n);
+    int64_t best_w = -1;
+    do {
+        const int64_t w = order_wavefronts(N, r, n);
+        if (best_w < 0 || w < best_w) {
+            best_w = w;
+            std::copy(r, r + n, best);
+        }
+    } while (std::next_permutation(r, r + n));
+    set_passes(N, best, n, rad);
 }
 
 }  // namespace
@@ -405,16 +481,22 @@ extern "C" cc_status crosscorr_sfts_to_series(const void* band_dev, const int64_
         // the launch shape per (device, N'): the smem attribute and the occupancy query run
         // once, so that repeated calls (and a stream capture of them) only launch
         static std::mutex mu;
-        static std::map<std::pair<int, int64_t>, std::pair<int, int>> shapes;   // -> (occupancy, SMs)
+        struct Shape {
+            int occ, sms;
+            Radices rad;
+        };
+        static std::map<std::pair<int, int64_t>, Shape> shapes;
         int dev = 0, occ = 0, sms = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e, "sfts_to_series device");
         {
             std::lock_guard<std::mutex> lock(mu);
             auto it = shapes.find({dev, n_prime});
             if (it != shapes.end()) {
-                occ = it->second.first;
-                sms = it->second.second;
+                occ = it->second.occ;
+                sms = it->second.sms;
+                rad = it->second.rad;
             } else {
+                order_for_banks(n_prime, &rad);
                 // the attribute is the kernel's, shared by every N': set to the largest shape
                 // (72 KB, or one group of three 1536-point buffers and the table: 49 KB)
                 if ((e = cudaFuncSetAttribute(sft_fft_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -424,7 +506,7 @@ extern "C" cc_status crosscorr_sfts_to_series(const void* band_dev, const int64_
                                                                         smem)) != cudaSuccess ||
                     (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
                     return cuda_fail(e, "sfts_to_series occupancy");
-                shapes[{dev, n_prime}] = {occ, sms};
+                shapes[{dev, n_prime}] = Shape{occ, sms, rad};
             }
         }
         const int64_t ctas = std::max<int64_t>(1, std::min<int64_t>((n_blocks + groups - 1) / groups,
