@@ -680,6 +680,26 @@ extern "C" cc_status crosscorr_demod_search(cc_plan* plan, const cc_template* t_
     // timing records for a batch of templates: the list of locked SFTs plus two padding
     const size_t per_t = sizeof(DemodTiming) * ((size_t)n_list + 2);
     const int64_t batch = std::max<int64_t>(1, std::min<int64_t>({n_t, (int64_t)((size_t)2 << 30) / (int64_t)per_t, 65535}));
+    if (sep) {
+        // CTA size of the separable kernel (every thread does the same work, issue-bound):
+        // the fewest resident-thread slots over whole waves of the first batch,
+        // ceil(CTAs / (resident CTAs x SMs)) x resident threads per SM
+        int dev = 0, sms = 152;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const void* kern = sep_ring ? (const void*)demod_sep_kernel<true> : (const void*)demod_sep_kernel<false>;
+        int64_t best = -1;
+        for (int nt : {128, 96, 64}) {
+            int occ = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, nt, ring_bytes(nt)) != cudaSuccess || occ < 1)
+                continue;
+            const int64_t ctas = (plan->N_f + nt - 1) / nt * std::min(batch, n_t);
+            const int64_t est = (ctas + (int64_t)occ * sms - 1) / ((int64_t)occ * sms) * occ * nt;
+            if (best < 0 || est < best) {
+                best = est;
+                nthr = nt;
+            }
+        }
+    }
     cc_status s = ensure_workspace(plan, per_t * batch);
     if (s != CC_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
