@@ -204,7 +204,9 @@ cc_status crosscorr_resample(cc_plan* plan, const void* const* x_dev, const cc_t
  *   F[(((t*Q + X)*M + K)*2 + w)*N_f + k] = sum_{r in segment K} w_r exp(-2 pi i (k-bar_k - N_FFT/2) r / N_FFT)
  * i.e. the zero-padded N_FFT-point transform at the selected bins with the
  * segment-start phase Phi_in included.  ab_dev as written by stage 1; F_dev:
- * device complex64[n_t][Q][M][2][N_f]. */
+ * device complex64[n_t][Q][M][2][N_f].  Asynchronous on `stream`; on 4096-point cosets
+ * (Q <= 2, whole segments) it uses a plan-owned unit counter, so two calls on one plan
+ * must not run concurrently on different streams (as for every call on a plan). */
 cc_status crosscorr_segment_fft(cc_plan* plan, const void* ab_dev, int64_t n_t, void* F_dev,
                                 void* stream);
 
