@@ -257,6 +257,7 @@ segpair_tma_kernel(DevParams p, TmaWork q, const void* __restrict__ ab, const fl
                 phase ^= 1;
                 // first radix-16 pass: sample s = tid + 256 r of the segment (zero beyond
                 // N_s) times the coset factor W_N^(256 bc r)
+                bool nz = false;   // SPECTRA: a nonzero sample in this thread's share
                 {
 #pragma unroll
                     for (int r = 0; r < 16; ++r) {
@@ -266,6 +267,7 @@ segpair_tma_kernel(DevParams p, TmaWork q, const void* __restrict__ ab, const fl
                             v[r] = in ? __bfloat1622float2(((const __nv_bfloat162*)stage)[s]) : make_float2(0.f, 0.f);
                         else
                             v[r] = in ? ((const float2*)stage)[s] : make_float2(0.f, 0.f);
+                        if constexpr (SPECTRA) nz |= v[r].x != 0.f || v[r].y != 0.f;
                     }
 #pragma unroll
                     for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], __ldg(twk + r));
@@ -287,6 +289,15 @@ segpair_tma_kernel(DevParams p, TmaWork q, const void* __restrict__ ab, const fl
                     return;
                 }
                 if (more && tid == 0) issue(nK, nX);
+                if constexpr (SPECTRA) {
+                    // a row of zeros (a gapped segment, written as zeros by the resampling
+                    // stage): zero spectra, no transform
+                    if (!__syncthreads_or(nz)) {
+                        float2* Fo = Fs + ((((size_t)t * Q + X) * M + K) * 2 + w) * p.N_f;
+                        for (int i = tid; i < nb4; i += TT_THREADS) Fo[__ldg(p.coset4_k + o4 + i)] = make_float2(0.f, 0.f);
+                        continue;
+                    }
+                }
                 // second pass (NS = 16): Y -> Z, twiddles W_L^(16 k r) W_N^(16 bc r) from the
                 // table (the thread factor of the first pass's source threads)
                 {

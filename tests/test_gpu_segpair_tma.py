@@ -205,8 +205,9 @@ def test_bounded_wait_runs_out_reports_timeout_and_context_survives():
                                          ("L2048", True)])
 def test_staged_segment_fft_on_4096_cosets(name, padded):
     """The staged segment-FFT stage on 4096-point cosets (the persistent kernel writing
-    spectra instead of pair sums, every segment transformed): random series in, every
-    spectrum bin against the oracle's zero-padded FP64 FFT route."""
+    spectra instead of pair sums; all-zero segments written as zeros without a transform):
+    random series with some zero segments in, every spectrum bin against the oracle's
+    zero-padded FP64 FFT route."""
     kw = dict(BASE)
     kw.update(CASES.get(name, PADDED.get(name, {})))
     ds = synth.tiny(seed=53, n_templates=2, **kw)
@@ -215,6 +216,8 @@ def test_staged_segment_fft_on_4096_cosets(name, padded):
     Q = ds.cfg.n_det
     rng = np.random.default_rng(7)
     a0 = rng.standard_normal((2, Q, 2, p.M * p.N_s)) + 1j * rng.standard_normal((2, Q, 2, p.M * p.N_s))
+    for K in range(0, p.M, 3):   # some all-zero segments (as the resampling stage writes gaps)
+        a0[K % 2, K % Q, (K // 3) % 2, K * p.N_s:(K + 1) * p.N_s] = 0
     r = np.arange(p.M * p.N_s)
     rot = np.exp(-2j * np.pi * ((p.f_r * r * p.dt) % 1.0))
     Fref = np.zeros((2, Q, p.M, 2, p.N_f), np.complex128)
