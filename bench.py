@@ -38,7 +38,7 @@ GRID_TEMPLATES = 8000
 # an ncu capture of one launch on 8 templates (its summary is kept with the profiles;
 # the reads of a_r, b_r grow with the templates of a launch).  None once the kernel
 # changes.
-SEGPAIR_DRAM_BYTES_PER_TEMPLATE = (1.789992e9 + 47.0528e6) / 8
+SEGPAIR_DRAM_BYTES_PER_TEMPLATE = (1.790227e9 + 46.770432e6) / 8
 SM_COUNT = 152
 FP32_LANES = 128
 # days of the 120-day band in the bounded CPU samples (both CPU legs use the same sample)
