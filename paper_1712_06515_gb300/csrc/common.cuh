@@ -311,8 +311,10 @@ __device__ __forceinline__ Orbit make_orbit(const DevParams& p, const cc_templat
 // E = M + e sin M converges quadratically to FP64 precision well within them for e < 0.95).
 // SSB part: t = u - Delta(t), u = tau + b, iterated on Delta from Delta(u) (contraction
 // |Delta'| <= 1e-4).  Both work on the small quantities b and Delta so d = Delta - b
-// keeps FP64 precision.
-__device__ __forceinline__ double knot_delay(const DevParams& p, int X, const Orbit& o, double tau) {
+// keeps FP64 precision.  The binary part depends on the source time only, so a caller
+// with several detectors computes it once (knot_binary) and the SSB part per detector
+// (knot_ssb); knot_delay is the two together.
+__device__ __forceinline__ double knot_binary(const Orbit& o, double tau) {
     double b;
     if (o.e == 0.0) {
         const double x0 = (tau - o.tasc_rel) * o.invP;        // orbital phase in cycles
@@ -343,6 +345,10 @@ __device__ __forceinline__ double knot_delay(const DevParams& p, int X, const Or
             b = o.a_p * (o.sinw * (cE - o.e) + o.cosw * o.sq * sE);
         }
     }
+    return b;
+}
+
+__device__ __forceinline__ double knot_ssb(const DevParams& p, int X, double tau, double b) {
     const double* tab = p.ssb[X];
     const double t0 = p.eph_t0[X], inv = p.inv_eph_dt[X];
     const int64_t n = p.n_eph[X];
@@ -351,6 +357,10 @@ __device__ __forceinline__ double knot_delay(const DevParams& p, int X, const Or
 #pragma unroll
     for (int it = 0; it < N_SSB_ITER; ++it) dl = table_lerp(tab, t0, inv, n, u - dl);
     return dl - b;
+}
+
+__device__ __forceinline__ double knot_delay(const DevParams& p, int X, const Orbit& o, double tau) {
+    return knot_ssb(p, X, tau, knot_binary(o, tau));
 }
 
 // Knot record from the delays at knots k-1, k, k+1, k+2 (seconds) of a knot at

@@ -96,27 +96,33 @@ bool fused_layout(const cc_plan* plan, int64_t n_t, FusedLayout* lay) {
 }
 
 // Knot records (FP64 delays at every KNOT-th source sample, four per record) for a batch
-// of templates: one thread per record, the block's 256 records plus three halo knots.
+// of templates: one thread per record of every detector, the block's 256 records plus
+// three halo knots.  The binary-orbit part of each delay is computed once for all
+// detectors (it depends on the source time only); the barycentric part per detector.
 __global__ void __launch_bounds__(256)
 knots_kernel(DevParams p, const cc_template* __restrict__ tm, int64_t t_base, int64_t nkn,
              KnotRec* __restrict__ out) {
-    __shared__ double dk[256 + 3];
+    __shared__ double dk[CC_MAX_DET][256 + 3];
     __shared__ Orbit orb_s;
-    const int X = blockIdx.y;
+    const int Q = p.Q;
     const int64_t tl = blockIdx.z, t = t_base + tl;
     const int64_t k0 = (int64_t)blockIdx.x * 256;
     // the orbit's FP64 set-up (a reciprocal, and trigonometry for e != 0) once per block
     if (threadIdx.x == 0) orb_s = make_orbit(p, tm[t]);
     __syncthreads();
     const Orbit orb = orb_s;
-    for (int i = threadIdx.x; i < 256 + 3; i += 256)
-        dk[i] = knot_delay(p, X, orb, (double)((k0 - 1 + i) * KNOT) * p.dt);
+    for (int i = threadIdx.x; i < 256 + 3; i += 256) {
+        const double tau = (double)((k0 - 1 + i) * KNOT) * p.dt;
+        const double b = knot_binary(orb, tau);
+        for (int X = 0; X < Q; ++X) dk[X][i] = knot_ssb(p, X, tau, b);
+    }
     __syncthreads();
     const int64_t k = k0 + threadIdx.x;
     if (k < nkn)
-        out[((size_t)tl * p.Q + X) * nkn + k] =
-            make_knot(p, dk[threadIdx.x], dk[threadIdx.x + 1], dk[threadIdx.x + 2], dk[threadIdx.x + 3],
-                      (double)(k * KNOT) * p.dt);
+        for (int X = 0; X < Q; ++X)
+            out[((size_t)tl * Q + X) * nkn + k] =
+                make_knot(p, dk[X][threadIdx.x], dk[X][threadIdx.x + 1], dk[X][threadIdx.x + 2],
+                          dk[X][threadIdx.x + 3], (double)(k * KNOT) * p.dt);
 }
 
 int64_t knot_rows(const cc_plan* plan) { return (plan->N_tau + KNOT - 1) / KNOT; }
@@ -127,7 +133,7 @@ cc_status launch_knots(cc_plan* plan, const cc_template* t_dev, int64_t n_t, Kno
     const int64_t nkn = knot_rows(plan);
     for (int64_t t0 = 0; t0 < n_t; t0 += 65535) {
         const int64_t nt = std::min<int64_t>(65535, n_t - t0);
-        dim3 gk((unsigned)((nkn + 255) / 256), (unsigned)p.Q, (unsigned)nt);
+        dim3 gk((unsigned)((nkn + 255) / 256), 1u, (unsigned)nt);
         knots_kernel<<<gk, 256, 0, st>>>(p, t_dev + t0, 0, nkn, kn + (size_t)t0 * p.Q * nkn);
         count_launch();
     }
@@ -176,7 +182,7 @@ cc_status launch_fused(cc_plan* plan, const cc_template* t_dev, int64_t n_t, flo
     for (int64_t tb = 0; tb < n_t; tb += step) {
         const int64_t nt = std::min(step, n_t - tb);
         if (pre) {
-            dim3 gk((unsigned)((nkn + 255) / 256), (unsigned)p.Q, (unsigned)nt);
+            dim3 gk((unsigned)((nkn + 255) / 256), 1u, (unsigned)nt);
             knots_kernel<<<gk, 256, 0, st>>>(p, t_dev, tb, nkn, kn_ws);
             count_launch();
         }
