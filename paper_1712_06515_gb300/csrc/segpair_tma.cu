@@ -32,6 +32,11 @@
 //     (the plan's twk table); the last pass computes only the 8 outputs m < L/2 that hold
 //     output bins.
 //
+// The same kernel with SPECTRA set serves the staged segment-FFT stage: it writes each
+// (detector, segment) transform, with its segment-start phase, to the coset's bins of F
+// instead of summing pairs, and writes zeros for an all-zero staged row without
+// transforming it.
+//
 // Waits on the mbarrier are bounded (about one second of clock): a wait that runs out
 // sets bit 0 of the plan's device error word, every thread of the CTA agrees on it at
 // the next barrier, the CTA waits (bounded again) for the copy still in flight and
