@@ -136,3 +136,50 @@ def test_equals_resampled_statistic_where_the_two_coincide():
     rr = oc.rho_template(ds, ds.templates[0], plan=plan_f, spectra="direct")
     assert rd[0] > 10.0
     assert abs(rd[0] / rr[0] - 1.0) < 2e-3, (rd[0], rr[0])
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(T_max=256.0, T_short=128.0), dict(n_det=3, duty=0.6)])
+def test_separable_rearrangement_equals_pair_loop(kw):
+    """The separable form the GPU offers beside the pair loop: with
+    Gamma_KL = (a^_K a^_L + b^_K b^_L) / 10, the pair sum of SFT K over its partners L is
+    2 Re(conj(y_K) (a^_K S_A + b^_K S_B)) / 10 (S_A = sum_L a^_L y_L, S_B likewise) and its
+    normalisation term Xi_K^2 (a^_K^2 U_AA + 2 a^_K b^_K U_AB + b^_K^2 U_BB) / 100
+    (U_AA = sum_L Xi_L^2 a^_L^2, ...).  Built here from the oracle's own pieces and summed
+    over the partner windows directly, it equals the oracle's pair loop to FP64 rounding."""
+    ds = synth.tiny(seed=19, n_templates=2, injection=INJ, **kw)
+    cfg = ds.cfg
+    plan = oracle.make_plan(cfg)
+    f = plan.freq
+    for tmpl in ds.templates:
+        a_p, tasc, P, e, omega = oracle.orbit(tmpl)
+        T, Y, XI, AH, BH = [], [], [], [], []
+        for det, (ks, tmid, z, sig) in zip(ds.dets, demod.sfts(ds)):
+            if len(ks) == 0:
+                continue
+            x, cyc = demod.signal_bins(det, cfg, a_p, tasc - cfg.t0, P, tmid, f, e, omega)
+            zK, xi = demod.sft_data_vector(z, x)
+            Y.append(xi * zK * np.exp(-2j * np.pi * cyc))
+            XI.append(xi)
+            scale = np.sqrt(2.0 * cfg.T_sft / (2.0 * sig * sig * cfg.dt))
+            AH.append(scale * demod._lerp(det.ab_t0, det.ab_dt, det.a_tab, tmid))
+            BH.append(scale * demod._lerp(det.ab_t0, det.ab_dt, det.b_tab, tmid))
+            T.append(tmid)
+        T = np.concatenate(T)
+        order = np.argsort(T, kind="stable")
+        T, Y, XI = T[order], np.concatenate(Y)[order], np.concatenate(XI)[order]
+        AH, BH = np.concatenate(AH)[order], np.concatenate(BH)[order]
+        raw = np.zeros(len(f))
+        den = np.zeros(len(f))
+        for K in range(len(T)):
+            part = (np.arange(len(T)) < K) & (T[K] - T <= cfg.T_max + 1e-9)   # earlier SFTs in the window
+            SA = (AH[part, None] * Y[part]).sum(axis=0)
+            SB = (BH[part, None] * Y[part]).sum(axis=0)
+            x2 = XI[part] ** 2
+            UAA = (x2 * AH[part, None] ** 2).sum(axis=0)
+            UAB = (x2 * (AH[part] * BH[part])[:, None]).sum(axis=0)
+            UBB = (x2 * BH[part, None] ** 2).sum(axis=0)
+            raw += 0.2 * np.real(np.conj(Y[K]) * (AH[K] * SA + BH[K] * SB))
+            den += XI[K] ** 2 * (AH[K] ** 2 * UAA + 2.0 * AH[K] * BH[K] * UAB + BH[K] ** 2 * UBB) / 100.0
+        sep = np.where(den > 0, raw / np.sqrt(2.0 * den), 0.0)
+        ref = demod.demod_rho(ds, tmpl)
+        np.testing.assert_allclose(sep, ref, rtol=0, atol=1e-9 * max(1.0, np.abs(ref).max()))
